@@ -1,0 +1,141 @@
+"""CPU oracle for RECEIPT tip decomposition -- test infrastructure only.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package. It shares no code with the CUDA
+library in ``paper_2010_08695_gb300`` and imports nothing from it.
+
+The arithmetic lives in ``oracle.c`` (plain C, compiled here with gcc and
+OpenMP for the per-vertex counting loop only):
+
+* ``count_2hop``   -- butterflies per vertex by their definition
+  (sum over same-side x' of C(common neighbours, 2)), both sides;
+* ``count_vp``     -- Algorithm 1 (pvBcnt), an independent cross-check;
+* ``count_vertex`` -- the same definition for a list of vertices;
+* ``bup``          -- Algorithm 2: sequential bottom-up peeling, with a
+  monotone radix heap and the literal clamp of the support update.
+
+All functions take original-id edge lists ``(eu, ev)`` and return arrays
+indexed by original id.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+import time
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liboracle.so`` next to the source (gcc, -O2, OpenMP)."""
+    with _lock:
+        if (not force and os.path.exists(_LIB)
+                and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+            return _LIB
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-D_POSIX_C_SOURCE=199309L", "-fopenmp",
+               "-shared", "-fPIC", "-o", tmp, _SRC]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+        return _LIB
+
+
+class BupStats(ctypes.Structure):
+    _fields_ = [("wedges", ctypes.c_uint64), ("peeled", ctypes.c_int64),
+                ("seconds_count", ctypes.c_double), ("seconds_peel", ctypes.c_double),
+                ("complete", ctypes.c_int64)]
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+        u64p = ctypes.c_void_p
+        lib.oracle_count_2hop.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                          i32p, i32p, u64p, u64p]
+        lib.oracle_count_vp.argtypes = lib.oracle_count_2hop.argtypes
+        lib.oracle_count_vertex.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                            i32p, i32p, ctypes.c_int, i32p, ctypes.c_int64,
+                                            u64p]
+        lib.oracle_bup.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, i32p, i32p,
+                                   ctypes.c_int, u64p, ctypes.c_uint64,
+                                   ctypes.POINTER(BupStats)]
+        lib.oracle_num_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _prep(eu, ev):
+    eu = np.ascontiguousarray(eu, dtype=np.int32)
+    ev = np.ascontiguousarray(ev, dtype=np.int32)
+    if eu.shape != ev.shape:
+        raise ValueError("eu and ev differ in length")
+    return eu, ev
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(rc):
+    if rc != 0:
+        raise RuntimeError({1: "invalid input", 2: "out of memory"}.get(rc, f"rc={rc}"))
+
+
+def count_2hop(eu, ev, nu, nv):
+    """Per-vertex butterfly counts ``(cnt_u, cnt_v)`` by their definition."""
+    eu, ev = _prep(eu, ev)
+    cu = np.zeros(nu, np.uint64)
+    cv = np.zeros(nv, np.uint64)
+    _check(_load().oracle_count_2hop(nu, nv, len(eu), eu, ev, _ptr(cu), _ptr(cv)))
+    return cu, cv
+
+
+def count_vp(eu, ev, nu, nv):
+    """Per-vertex butterfly counts ``(cnt_u, cnt_v)`` by Algorithm 1."""
+    eu, ev = _prep(eu, ev)
+    cu = np.zeros(nu, np.uint64)
+    cv = np.zeros(nv, np.uint64)
+    _check(_load().oracle_count_vp(nu, nv, len(eu), eu, ev, _ptr(cu), _ptr(cv)))
+    return cu, cv
+
+
+def count_vertex(eu, ev, nu, nv, side, xs):
+    """Butterflies of the listed vertices of ``side`` (0 = U, 1 = V)."""
+    eu, ev = _prep(eu, ev)
+    xs = np.ascontiguousarray(xs, dtype=np.int32)
+    out = np.zeros(len(xs), np.uint64)
+    _check(_load().oracle_count_vertex(nu, nv, len(eu), eu, ev, int(side), xs, len(xs),
+                                       _ptr(out)))
+    return out
+
+
+def bup(eu, ev, nu, nv, side, max_wedges: int = 0):
+    """Tip numbers of ``side`` by sequential bottom-up peeling.
+
+    Returns ``(tips, stats)``; ``stats`` holds wedges traversed, vertices
+    peeled, seconds of the initial count and of the peel, and whether the
+    peel ran to completion (``max_wedges`` > 0 bounds it)."""
+    eu, ev = _prep(eu, ev)
+    n = nu if side == 0 else nv
+    tips = np.zeros(n, np.uint64)
+    st = BupStats()
+    _check(_load().oracle_bup(nu, nv, len(eu), eu, ev, int(side), _ptr(tips),
+                              int(max_wedges), ctypes.byref(st)))
+    return tips, {"wedges": int(st.wedges), "peeled": int(st.peeled),
+                  "seconds_count": st.seconds_count, "seconds_peel": st.seconds_peel,
+                  "complete": bool(st.complete)}
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())

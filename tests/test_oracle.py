@@ -1,0 +1,176 @@
+"""Pins of the CPU oracle to facts other than itself: brute-force enumeration
+(butterflies as 2x2 bicliques; tip numbers as a maximum over vertex subsets,
+Definition 1), closed forms on complete bipartite graphs, invariants (the sum
+of per-vertex counts on each side is twice the number of butterflies; forests
+hold no butterfly; tip number <= butterfly count), disjoint unions and the
+U/V transposition."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import bruteforce as bf
+
+
+def _rand_graphs(n, max_u=8, max_v=7, seed=0):
+    rng = np.random.default_rng(seed)
+    for g in range(n):
+        nu = int(rng.integers(1, max_u + 1))
+        nv = int(rng.integers(1, max_v + 1))
+        p = float(rng.uniform(0.2, 0.9))
+        eu, ev = synth.random_small(nu, nv, p, int(rng.integers(1 << 30)))
+        yield eu, ev, nu, nv
+
+
+def test_counts_match_biclique_enumeration():
+    for eu, ev, nu, nv in _rand_graphs(150, seed=1):
+        cu, cv = oracle.count_2hop(eu, ev, nu, nv)
+        bu, bv = bf.counts(eu, ev, nu, nv)
+        assert cu.tolist() == bu
+        assert cv.tolist() == bv
+
+
+def test_vertex_priority_count_matches_enumeration():
+    for eu, ev, nu, nv in _rand_graphs(150, seed=2):
+        cu, cv = oracle.count_vp(eu, ev, nu, nv)
+        bu, bv = bf.counts(eu, ev, nu, nv)
+        assert cu.tolist() == bu
+        assert cv.tolist() == bv
+
+
+def test_sum_is_twice_butterflies():
+    for eu, ev, nu, nv in _rand_graphs(60, max_u=9, max_v=9, seed=3):
+        nb = len(bf.butterflies(eu, ev))
+        cu, cv = oracle.count_2hop(eu, ev, nu, nv)
+        assert int(cu.sum()) == 2 * nb
+        assert int(cv.sum()) == 2 * nb
+
+
+def test_tip_numbers_match_subset_definition():
+    for side in (0, 1):
+        for eu, ev, nu, nv in _rand_graphs(200, max_u=8, max_v=8, seed=10 + side):
+            tips, st = oracle.bup(eu, ev, nu, nv, side)
+            assert st["complete"]
+            assert tips.tolist() == bf.tip_numbers(eu, ev, nu, nv, side)
+
+
+@pytest.mark.parametrize("a,b", [(1, 1), (2, 2), (3, 5), (7, 4), (12, 9), (40, 3)])
+def test_complete_bipartite_closed_form(a, b):
+    eu, ev = synth.complete_bipartite(a, b)
+    cu, cv = oracle.count_2hop(eu, ev, a, b)
+    assert (cu == (a - 1) * (b * (b - 1) // 2)).all()
+    assert (cv == (b - 1) * (a * (a - 1) // 2)).all()
+    tu, _ = oracle.bup(eu, ev, a, b, 0)
+    tv, _ = oracle.bup(eu, ev, a, b, 1)
+    assert (tu == (a - 1) * (b * (b - 1) // 2)).all()
+    assert (tv == (b - 1) * (a * (a - 1) // 2)).all()
+    vu, vv = oracle.count_vp(eu, ev, a, b)
+    assert (vu == cu).all() and (vv == cv).all()
+
+
+def test_complete_bipartite_with_pendants():
+    a, b = 6, 5
+    eu, ev = synth.complete_bipartite(a, b)
+    # pendant U vertices a..a+3 hang off V vertex 0; pendant V vertices b..b+2 off U 0
+    eu = np.concatenate([eu, np.arange(a, a + 4, dtype=np.int32), np.zeros(3, np.int32)])
+    ev = np.concatenate([ev, np.zeros(4, np.int32), np.arange(b, b + 3, dtype=np.int32)])
+    nu, nv = a + 4, b + 3
+    tu, _ = oracle.bup(eu, ev, nu, nv, 0)
+    core = (a - 1) * (b * (b - 1) // 2)
+    assert (tu[:a] == core).all() and (tu[a:] == 0).all()
+
+
+def test_forests_have_no_butterflies():
+    rng = np.random.default_rng(5)
+    for _ in range(30):
+        nu, nv = int(rng.integers(1, 40)), int(rng.integers(1, 40))
+        # random forest: each new vertex attaches to at most one earlier vertex
+        eu, ev = [], []
+        for v in range(1, nv):
+            eu.append(int(rng.integers(nu)))
+            ev.append(v)
+        # make it a forest: every V vertex has degree 1
+        eu, ev = np.array(eu, np.int32), np.array(ev, np.int32)
+        cu, cv = oracle.count_2hop(eu, ev, nu, nv)
+        assert cu.sum() == 0 and cv.sum() == 0
+        t, _ = oracle.bup(eu, ev, nu, nv, 0)
+        assert t.sum() == 0
+    # a star
+    eu = np.zeros(50, np.int32)
+    ev = np.arange(50, dtype=np.int32)
+    assert oracle.count_2hop(eu, ev, 1, 50)[1].sum() == 0
+
+
+def test_disjoint_union_is_union_of_parts():
+    rng = np.random.default_rng(7)
+    parts = []
+    for g in range(5):
+        nu, nv = int(rng.integers(5, 60)), int(rng.integers(5, 40))
+        m = int(rng.integers(1, nu * nv // 2 + 1))
+        eu, ev = synth.er(nu, nv, m, int(rng.integers(1 << 30)))
+        parts.append((eu, ev, nu, nv))
+    ou = ov = 0
+    EU, EV = [], []
+    for eu, ev, nu, nv in parts:
+        EU.append(eu + ou)
+        EV.append(ev + ov)
+        ou += nu
+        ov += nv
+    EU, EV = np.concatenate(EU), np.concatenate(EV)
+    for side in (0, 1):
+        whole, _ = oracle.bup(EU, EV, ou, ov, side)
+        pieces = np.concatenate([oracle.bup(eu, ev, nu, nv, side)[0]
+                                 for eu, ev, nu, nv in parts])
+        assert (whole == pieces).all()
+
+
+def test_transpose_symmetry():
+    for seed in range(5):
+        eu, ev = synth.er(80, 30, 700, seed)
+        a, _ = oracle.bup(eu, ev, 80, 30, 1)
+        b, _ = oracle.bup(ev, eu, 30, 80, 0)
+        assert (a == b).all()
+        cu, cv = oracle.count_2hop(eu, ev, 80, 30)
+        tu, tv = oracle.count_2hop(ev, eu, 30, 80)
+        assert (cu == tv).all() and (cv == tu).all()
+
+
+def test_tip_bounded_by_count_and_counting_paths_agree():
+    eu, ev, nu, nv, _ = synth.config_graph(1)
+    cu, cv = oracle.count_2hop(eu, ev, nu, nv)
+    vu, vv = oracle.count_vp(eu, ev, nu, nv)
+    assert (cu == vu).all() and (cv == vv).all()
+    for side, c in ((0, cu), (1, cv)):
+        t, st = oracle.bup(eu, ev, nu, nv, side)
+        assert st["complete"] and (t <= c).all()
+    sample = np.array([0, 5, 17, 1999], np.int32)
+    assert (oracle.count_vertex(eu, ev, nu, nv, 0, sample) == cu[sample]).all()
+
+
+def test_chung_lu_counting_paths_agree():
+    eu, ev = synth.chung_lu(3000, 800, 30000, 2.2, 2.4, seed=9)
+    cu, cv = oracle.count_2hop(eu, ev, 3000, 800)
+    vu, vv = oracle.count_vp(eu, ev, 3000, 800)
+    assert (cu == vu).all() and (cv == vv).all()
+
+
+def test_duplicates_and_edge_cases():
+    eu = np.array([0, 0, 1, 1, 0, 1], np.int32)
+    ev = np.array([0, 1, 0, 1, 0, 1], np.int32)  # K_{2,2} with two repeats
+    cu, cv = oracle.count_2hop(eu, ev, 3, 2)
+    assert cu.tolist() == [1, 1, 0] and cv.tolist() == [1, 1]
+    t, _ = oracle.bup(eu, ev, 3, 2, 0)
+    assert t.tolist() == [1, 1, 0]
+    e = np.zeros(0, np.int32)
+    assert oracle.bup(e, e, 4, 3, 0)[0].tolist() == [0, 0, 0, 0]
+    assert oracle.bup(e, e, 0, 3, 0)[0].tolist() == []
+    with pytest.raises(RuntimeError):
+        oracle.count_2hop(np.array([5], np.int32), np.array([0], np.int32), 3, 2)
+
+
+def test_bounded_peel_sample():
+    eu, ev, nu, nv, _ = synth.config_graph(1)
+    full, st_full = oracle.bup(eu, ev, nu, nv, 0)
+    part, st = oracle.bup(eu, ev, nu, nv, 0, max_wedges=st_full["wedges"] // 3)
+    assert not st["complete"] and 0 < st["peeled"] < nu
+    assert st["wedges"] >= st_full["wedges"] // 3
