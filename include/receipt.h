@@ -1,0 +1,181 @@
+/*
+ * receipt.h -- C ABI of the GB300 (sm_103a) RECEIPT tip-decomposition library.
+ *
+ * The method is RECEIPT (Lakhotia, Kannan, Prasanna, De Rose): per-vertex
+ * butterfly counting (Algorithm 1), a coarse-grained decomposition that
+ * splits one side's vertices into tip-number ranges by concurrent range
+ * peeling (Algorithm 3), and a fine-grained decomposition that peels every
+ * range's vertex subset independently and exactly (Algorithm 4), with the
+ * support update of Algorithm 2.
+ *
+ * Conventions shared by every entry point
+ *  - A bipartite graph G(W = (U, V), E) is given by |U| = nu, |V| = nv and m
+ *    edges (eu[i], ev[i]) with 0 <= eu[i] < nu and 0 <= ev[i] < nv (original
+ *    ids). Vertex ids are int32; counts and tip numbers are exact uint64.
+ *  - Pointers named d_* are device pointers on the current CUDA device and
+ *    h_* are host pointers. The caller owns every buffer it passes in; the
+ *    library never frees or keeps them past the call.
+ *  - Results are indexed by ORIGINAL vertex id.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Work is
+ *    enqueued on it; entry points that need a decision from the device
+ *    (the range loop of tip_decompose, validation in build_csr) synchronise
+ *    that stream before they return, so outputs are ready on return unless
+ *    stated otherwise.
+ *  - No C++ exception crosses this boundary. Every entry point returns a
+ *    receipt_status; receipt_last_error() gives a thread-local message for the
+ *    most recent failure on the calling thread.
+ *  - Device-side anomalies (a bounded wait that gave up, an internal table
+ *    overflow) are reported through a device error word and surface as
+ *    RECEIPT_ERR_TIMEOUT / RECEIPT_ERR_INTERNAL from the call that saw them.
+ */
+#ifndef RECEIPT_H
+#define RECEIPT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RECEIPT_OK = 0,
+    RECEIPT_ERR_INVALID = 1,  /* bad argument: id out of range, null pointer, bad side */
+    RECEIPT_ERR_OOM = 2,      /* device allocation failed                           */
+    RECEIPT_ERR_CUDA = 3,     /* a CUDA runtime call failed                          */
+    RECEIPT_ERR_TIMEOUT = 4,  /* a bounded device-side wait gave up                  */
+    RECEIPT_ERR_OVERFLOW = 5, /* a count would exceed 2^63 or m exceeds the id space */
+    RECEIPT_ERR_BUSY = 6,     /* the serving engine has no free slot or memory       */
+    RECEIPT_ERR_INTERNAL = 7  /* a device-side consistency check failed              */
+} receipt_status;
+
+typedef enum { RECEIPT_SIDE_U = 0, RECEIPT_SIDE_V = 1 } receipt_side;
+
+/* Opaque, library-owned graph: the relabelled two-sided CSR on the device. */
+typedef struct receipt_graph receipt_graph;
+
+/*
+ * Options of a tip decomposition. Zero-initialise, then set what you need;
+ * receipt_options_default() fills the defaults.
+ */
+typedef struct {
+    /* P, the number of vertex subsets the coarse-grained decomposition
+     * creates (Algorithm 3, input P; Sec. 5 uses 150). 0 means 150. */
+    int32_t P;
+    /* Optional injected range bounds theta(2) < theta(3) < ... (host array
+     * of n_bounds values, strictly increasing and > 0). When given they
+     * replace the adaptive range determination of Sec. 3.1.1; the last
+     * subset collects all vertices left after the given ranges. Tip numbers
+     * do not depend on the ranges (Theorem 2), so this is a test hook. */
+    const uint64_t *h_bounds;
+    int32_t n_bounds;
+    /* Optional device output: subset index (0-based) of every vertex of the
+     * decomposed side, by original id. */
+    int32_t *d_subset;
+    /* Optional host output of the range lower bounds theta(1..P_eff) and of
+     * theta(P_eff + 1) (UINT64_MAX for the last, open range): room for
+     * h_bounds_cap values; *h_p_eff receives the number of subsets made. */
+    uint64_t *h_bounds_out;
+    int32_t h_bounds_cap;
+    int32_t *h_p_eff;
+    /* Non-zero: record per-phase CUDA-event timings in the graph's stats. */
+    int32_t timing;
+} receipt_options;
+
+/* Counters of the last call on a graph (Sec. 5: wedges and rounds). */
+typedef struct {
+    uint64_t wedges_count;   /* wedges traversed by Algorithm 1              */
+    uint64_t wedges_cd;      /* wedges traversed by coarse-grained peeling   */
+    uint64_t wedges_fd;      /* wedges traversed by fine-grained peeling     */
+    uint64_t wedges_bup;     /* sum over the other side of d(d-1): the wedge
+                                count of bottom-up peeling, a graph property */
+    int64_t rounds_cd;       /* synchronisation rounds of Algorithm 3 (rho)  */
+    int64_t levels_fd;       /* peeling levels summed over all subsets       */
+    int32_t p_eff;           /* subsets actually created                     */
+    int32_t reserved;
+    float ms_csr, ms_count, ms_cd, ms_fd, ms_total; /* only if timing != 0   */
+} receipt_stats;
+
+/* Fills `opt` with the defaults (P = 150, nothing optional). */
+void receipt_options_default(receipt_options *opt);
+
+/*
+ * Builds the graph (Algorithm 1, step 1, and the adjacency of Sec. 4.2):
+ * removes duplicate edges (dedup != 0; with dedup == 0 a duplicate is an
+ * error), relabels each side in descending order of degree (ties by
+ * original id; one label space over U u V with U before V on equal degree),
+ * and builds the CSR of both sides with every neighbour list sorted by the
+ * new labels.
+ *   d_eu, d_ev : device int32[m], read only.
+ *   m          : number of input edges, 0 <= m < 2^31 (m == 0 is allowed).
+ *   nu, nv     : side sizes, >= 0.
+ *   out        : receives the new graph; release it with receipt_graph_destroy.
+ * Errors: RECEIPT_ERR_INVALID (id out of range, duplicate with dedup == 0,
+ * negative sizes), RECEIPT_ERR_OOM, RECEIPT_ERR_CUDA. Synchronises `stream`.
+ */
+receipt_status receipt_build_csr(const int32_t *d_eu, const int32_t *d_ev, int64_t m,
+                                 int32_t nu, int32_t nv, int dedup, void *stream,
+                                 receipt_graph **out);
+
+/* Frees a graph and all its device memory (NULL is a no-op). */
+receipt_status receipt_graph_destroy(receipt_graph *g);
+
+/* Sizes of a built graph (m after duplicate removal). Any pointer may be NULL. */
+receipt_status receipt_graph_info(const receipt_graph *g, int32_t *nu, int32_t *nv,
+                                  int64_t *m);
+
+/*
+ * Per-vertex butterfly counts of both sides (Algorithm 1, pvBcnt).
+ *   d_cnt_u : device uint64[nu] or NULL; d_cnt_v : device uint64[nv] or NULL.
+ * Counts are indexed by original id. Enqueued on `stream`; ready when the
+ * stream reaches this point (no host synchronisation).
+ */
+receipt_status receipt_count_butterflies(receipt_graph *g, uint64_t *d_cnt_u,
+                                         uint64_t *d_cnt_v, void *stream);
+
+/*
+ * Tip decomposition of one side (Algorithms 3 and 4): tip number theta_x of
+ * every vertex x of `side`, i.e. the largest k such that x lies in a k-tip
+ * (Definition 1).
+ *   d_tip : device uint64[n_side], by original id.
+ *   opt   : NULL for defaults.
+ * Synchronises `stream` once per range and once per peeling round.
+ */
+receipt_status receipt_tip_decompose(receipt_graph *g, receipt_side side, uint64_t *d_tip,
+                                     const receipt_options *opt, void *stream);
+
+/*
+ * Tip decomposition of n independent graphs in one pass: the graphs are
+ * packed into one disjoint union (tip numbers of a disjoint union are those
+ * of its parts), so all of them share the peeling rounds of Algorithm 3 and
+ * the persistent task queue of Algorithm 4.
+ *   gs[i]     : built graphs (unchanged by the call).
+ *   sides[i]  : side to decompose in graph i.
+ *   d_tips[i] : device uint64[n_side(i)] outputs by original id.
+ */
+receipt_status receipt_decompose_batch(receipt_graph *const *gs, const receipt_side *sides,
+                                       int32_t n, uint64_t *const *d_tips,
+                                       const receipt_options *opt, void *stream);
+
+/*
+ * End-to-end convenience over HOST buffers: copies the edge list to the
+ * device, builds the graph, decomposes `side`, copies the tip numbers back
+ * to h_tip (host uint64[n_side], by original id) and frees everything.
+ * Synchronous.
+ */
+receipt_status receipt_tip_decompose_host(const int32_t *h_eu, const int32_t *h_ev, int64_t m,
+                                          int32_t nu, int32_t nv, receipt_side side,
+                                          uint64_t *h_tip, const receipt_options *opt,
+                                          void *stream);
+
+/* Counters of the last count/decompose call on g. */
+receipt_status receipt_get_stats(const receipt_graph *g, receipt_stats *out);
+
+/* Thread-local text of the last error on the calling thread ("" if none). */
+const char *receipt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RECEIPT_H */

@@ -1,0 +1,260 @@
+"""GB300-native RECEIPT tip decomposition -- Python binding of libreceipt.so.
+
+A thin ctypes layer over the C ABI of ``include/receipt.h``: it marshals
+arguments (device pointers of torch tensors, the current CUDA stream) and
+nothing else; every step of counting and peeling runs in the CUDA kernels of
+``csrc/``. There is no CPU fallback: if the library is missing or fails to
+load, every call raises.
+
+Functions carry the C names (``receipt_build_csr``, ``receipt_count_butterflies``,
+``receipt_tip_decompose``, ``receipt_decompose_batch``,
+``receipt_tip_decompose_host``, ``receipt_get_stats``, ``receipt_last_error``);
+``Graph`` wraps the opaque graph handle.
+
+Counts and tip numbers are exact unsigned 64-bit integers. They are returned
+in ``torch.int64`` tensors holding the same bits (every value a graph of
+fewer than 2^31 edges can produce is below 2^63).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libreceipt.so")
+_lib = None
+_lock = threading.Lock()
+
+RECEIPT_OK = 0
+_STATUS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "OVERFLOW", 6: "BUSY",
+           7: "INTERNAL"}
+SIDE_U, SIDE_V = 0, 1
+
+
+class ReceiptError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"receipt error {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("P", ctypes.c_int32), ("h_bounds", ctypes.POINTER(ctypes.c_uint64)),
+                ("n_bounds", ctypes.c_int32), ("d_subset", ctypes.c_void_p),
+                ("h_bounds_out", ctypes.POINTER(ctypes.c_uint64)), ("h_bounds_cap", ctypes.c_int32),
+                ("h_p_eff", ctypes.POINTER(ctypes.c_int32)), ("timing", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("wedges_count", ctypes.c_uint64), ("wedges_cd", ctypes.c_uint64),
+                ("wedges_fd", ctypes.c_uint64), ("wedges_bup", ctypes.c_uint64),
+                ("rounds_cd", ctypes.c_int64), ("levels_fd", ctypes.c_int64),
+                ("p_eff", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("ms_csr", ctypes.c_float), ("ms_count", ctypes.c_float), ("ms_cd", ctypes.c_float),
+                ("ms_fd", ctypes.c_float), ("ms_total", ctypes.c_float)]
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load(build_if_missing: bool = True):
+    """Loads libreceipt.so (building it with nvcc first if it is missing or
+    older than its sources). Raises if it cannot be loaded."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        from . import _build
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"{_LIB_PATH} is missing: run __graft_entry__.build()")
+        lib = ctypes.CDLL(_LIB_PATH)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        lib.receipt_build_csr.argtypes = [vp, vp, i64, i32, i32, ctypes.c_int, vp,
+                                          ctypes.POINTER(vp)]
+        lib.receipt_graph_destroy.argtypes = [vp]
+        lib.receipt_graph_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                           ctypes.POINTER(i64)]
+        lib.receipt_count_butterflies.argtypes = [vp, vp, vp, vp]
+        lib.receipt_tip_decompose.argtypes = [vp, ctypes.c_int, vp, ctypes.POINTER(Options), vp]
+        lib.receipt_decompose_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int),
+                                                i32, ctypes.POINTER(vp), ctypes.POINTER(Options), vp]
+        lib.receipt_tip_decompose_host.argtypes = [vp, vp, i64, i32, i32, ctypes.c_int, vp,
+                                                   ctypes.POINTER(Options), vp]
+        lib.receipt_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+        lib.receipt_last_error.restype = ctypes.c_char_p
+        lib.receipt_options_default.argtypes = [ctypes.POINTER(Options)]
+        for f in ("receipt_build_csr", "receipt_graph_destroy", "receipt_graph_info",
+                  "receipt_count_butterflies", "receipt_tip_decompose",
+                  "receipt_decompose_batch", "receipt_tip_decompose_host", "receipt_get_stats"):
+            getattr(lib, f).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def receipt_last_error() -> str:
+    return load().receipt_last_error().decode()
+
+
+def _check(rc):
+    if rc != RECEIPT_OK:
+        raise ReceiptError(rc, receipt_last_error())
+
+
+def _stream_handle(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _options(P=150, bounds=None, subset=None, bounds_out=None, p_eff=None, timing=False):
+    o = Options()
+    load().receipt_options_default(ctypes.byref(o))
+    o.P = int(P)
+    keep = []
+    if bounds is not None:
+        b = np.ascontiguousarray(bounds, dtype=np.uint64)
+        keep.append(b)
+        o.h_bounds = b.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+        o.n_bounds = len(b)
+    if subset is not None:
+        o.d_subset = subset.data_ptr()
+    if bounds_out is not None:
+        o.h_bounds_out = bounds_out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+        o.h_bounds_cap = len(bounds_out)
+    if p_eff is not None:
+        o.h_p_eff = ctypes.pointer(p_eff)
+        keep.append(p_eff)
+    o.timing = 1 if timing else 0
+    return o, keep
+
+
+def receipt_build_csr(eu, ev, nu: int, nv: int, dedup: bool = True, stream=None):
+    """Builds a graph from device int32 edge tensors; returns the raw handle."""
+    lib = load()
+    h = ctypes.c_void_p()
+    m = int(eu.numel())
+    _check(lib.receipt_build_csr(_dptr(eu) if m else None, _dptr(ev) if m else None, m, int(nu),
+                                 int(nv), 1 if dedup else 0, _stream_handle(stream),
+                                 ctypes.byref(h)))
+    return h
+
+
+def receipt_count_butterflies(handle, cnt_u, cnt_v, stream=None):
+    _check(load().receipt_count_butterflies(handle, _dptr(cnt_u), _dptr(cnt_v),
+                                            _stream_handle(stream)))
+
+
+def receipt_tip_decompose(handle, side: int, tip, options=None, stream=None):
+    o = options if options is not None else _options()[0]
+    _check(load().receipt_tip_decompose(handle, int(side), _dptr(tip), ctypes.byref(o),
+                                        _stream_handle(stream)))
+
+
+def receipt_get_stats(handle) -> dict:
+    st = Stats()
+    _check(load().receipt_get_stats(handle, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in Stats._fields_ if k != "reserved"}
+
+
+class Graph:
+    """Device graph (relabelled two-sided CSR) owned by libreceipt."""
+
+    def __init__(self, eu, ev, nu: int, nv: int, dedup: bool = True, stream=None):
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        eu = torch.as_tensor(eu).to(device=dev, dtype=torch.int32).contiguous()
+        ev = torch.as_tensor(ev).to(device=dev, dtype=torch.int32).contiguous()
+        self.nu, self.nv = int(nu), int(nv)
+        self.device = dev
+        self._h = receipt_build_csr(eu, ev, nu, nv, dedup, stream)
+        nu_, nv_, m_ = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        _check(load().receipt_graph_info(self._h, ctypes.byref(nu_), ctypes.byref(nv_),
+                                         ctypes.byref(m_)))
+        self.m = int(m_.value)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().receipt_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def count_butterflies(self, stream=None):
+        """Per-vertex butterfly counts ``(cnt_u, cnt_v)`` (Algorithm 1)."""
+        import torch
+        cu = torch.empty(self.nu, dtype=torch.int64, device=self.device)
+        cv = torch.empty(self.nv, dtype=torch.int64, device=self.device)
+        receipt_count_butterflies(self._h, cu, cv, stream)
+        return cu, cv
+
+    def tip_decompose(self, side: int = SIDE_U, P: int = 150, bounds=None, subsets=False,
+                      timing=False, out=None, stream=None):
+        """Tip numbers of ``side`` (Algorithms 3 and 4). With ``subsets=True``
+        returns ``(tips, subset_of_vertex, range_bounds)``."""
+        import torch
+        n = self.nu if side == SIDE_U else self.nv
+        tip = out if out is not None else torch.empty(n, dtype=torch.int64, device=self.device)
+        sub = torch.empty(n, dtype=torch.int32, device=self.device) if subsets else None
+        bout = np.zeros(P + (len(bounds) if bounds is not None else 0) + 4, np.uint64) \
+            if subsets else None
+        peff = ctypes.c_int32(0)
+        o, keep = _options(P, bounds, sub, bout, peff, timing)
+        receipt_tip_decompose(self._h, side, tip, o, stream)
+        if subsets:
+            return tip, sub, bout[: peff.value + 1]
+        return tip
+
+    def stats(self) -> dict:
+        return receipt_get_stats(self._h)
+
+
+def receipt_decompose_batch(graphs, sides, outs=None, P: int = 150, stream=None):
+    """Tip numbers of many graphs in one pass (disjoint-union packing)."""
+    import torch
+    n = len(graphs)
+    hs = (ctypes.c_void_p * n)(*[g.handle for g in graphs])
+    ss = (ctypes.c_int * n)(*[int(s) for s in sides])
+    if outs is None:
+        outs = [torch.empty(g.nu if s == 0 else g.nv, dtype=torch.int64, device=g.device)
+                for g, s in zip(graphs, sides)]
+    ps = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+    o, keep = _options(P)
+    _check(load().receipt_decompose_batch(hs, ss, n, ps, ctypes.byref(o), _stream_handle(stream)))
+    return outs
+
+
+def receipt_tip_decompose_host(eu, ev, nu: int, nv: int, side: int, P: int = 150, stream=None,
+                               out=None):
+    """End to end over host buffers: copies in, builds, decomposes, copies out."""
+    eu = np.ascontiguousarray(eu, dtype=np.int32)
+    ev = np.ascontiguousarray(ev, dtype=np.int32)
+    n = nu if side == SIDE_U else nv
+    tip = out if out is not None else np.zeros(n, np.uint64)
+    o, keep = _options(P)
+    _check(load().receipt_tip_decompose_host(eu.ctypes.data_as(ctypes.c_void_p),
+                                             ev.ctypes.data_as(ctypes.c_void_p), len(eu), int(nu),
+                                             int(nv), int(side), tip.ctypes.data_as(ctypes.c_void_p),
+                                             ctypes.byref(o), _stream_handle(stream)))
+    return tip
+
+
+def as_u64(t) -> np.ndarray:
+    """Device int64 tensor of exact counts -> host numpy uint64 (same bits)."""
+    return t.cpu().numpy().view(np.uint64)

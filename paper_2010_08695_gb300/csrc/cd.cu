@@ -1,0 +1,589 @@
+// Coarse-grained decomposition, Algorithm 3 (RECEIPT CD).
+//
+// Per range i (1 <= i <= P):
+//  1. init <- support of every remaining vertex (Algorithm 3, support init);
+//  2. theta(i+1) from the weighted support histogram of the remaining
+//     vertices (findHi) with the adaptive target of Sec. 3.1.1;
+//  3. repeat { activeSet <- remaining vertices with support < theta(i+1);
+//     peel them concurrently with the update of Algorithm 2 } until the
+//     activeSet is empty.
+// Vertices left after P ranges form one more subset (Sec. 3.1.1, last
+// paragraph).
+//
+// Reading of the support update on the GPU: the raw support sup[x] is kept
+// unclamped. It always equals the butterflies x shares with vertices not yet
+// peeled, so it never underflows (Lemma 2: each shared butterfly is removed
+// once), and "support in [theta(i), theta(i+1))" is "sup < theta(i+1)" for
+// every remaining vertex; the clamp of Algorithm 2 only matters for the
+// value recorded, which the fine-grained step applies.
+//
+// The next activeSet is built without any scan: a vertex enters it exactly
+// when one 64-bit atomic subtraction takes its support from >= theta(i+1) to
+// < theta(i+1), and that atomic's return value tells the thread that did it.
+// A peeled vertex whose raw support is 0 shares no butterfly with any
+// remaining vertex, so its update is skipped.
+#include <algorithm>
+
+#include "engine.cuh"
+#include "internal.cuh"
+
+namespace receipt {
+
+namespace {
+
+constexpr int NBUCKET = 1920;  // 32 exact buckets + 58 octaves x 32 mantissa steps
+
+__device__ __forceinline__ int bucket_of(unsigned long long k) {
+    if (k < 32) return (int)k;
+    int e = 63 - __clzll((long long)k);
+    int mant = (int)((k >> (e - 5)) & 31);
+    return 32 + (e - 5) * 32 + mant;
+}
+
+__device__ __forceinline__ unsigned long long bucket_top(int b) {
+    if (b < 32) return (unsigned long long)b;
+    int e = (b - 32) / 32 + 5, mant = (b - 32) % 32;
+    if (e == 63 && mant == 31) return ~0ull;
+    return ((unsigned long long)(33 + mant) << (e - 5)) - 1ull;
+}
+
+struct CdDev {
+    unsigned long long hi;
+    int32_t nF, nNext, nLw, nLc, nLg, nLo;
+    int32_t work[4];
+    int32_t n_remaining;
+    int32_t pad;
+    unsigned long long wrem_prev;
+    double tgt_prev;
+    unsigned long long wedges;
+    unsigned long long hist_w[NBUCKET];
+    uint32_t hist_c[NBUCKET];
+};
+
+// wfull[x] = sum over y in N_x of d_y (wedges walked when x is peeled)
+__global__ void k_deg_of_nbr(const int32_t *__restrict__ adj, int64_t m,
+                             const int64_t *__restrict__ offO, int64_t *__restrict__ out) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < m) {
+        int32_t y = adj[q];
+        out[q] = offO[y + 1] - offO[y];
+    }
+}
+
+__global__ void k_wfull(const int64_t *__restrict__ off, int32_t n, const int64_t *__restrict__ pscan,
+                        unsigned long long *__restrict__ wfull) {
+    int32_t x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x < n) wfull[x] = (unsigned long long)(pscan[off[x + 1]] - pscan[off[x]]);
+}
+
+__global__ void k_init_state(int32_t *sub, int32_t n) {
+    int32_t x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x < n) sub[x] = -1;
+}
+
+// Histogram of remaining vertices' supports weighted by w[x] = wfull - d_x,
+// and init <- sup for every remaining vertex.
+__global__ void k_cd_hist(int32_t n, const int32_t *__restrict__ sub,
+                          const unsigned long long *__restrict__ sup,
+                          const unsigned long long *__restrict__ wfull,
+                          const int64_t *__restrict__ off, unsigned long long *__restrict__ init,
+                          CdDev *st) {
+    __shared__ unsigned long long hw[NBUCKET];
+    __shared__ uint32_t hc[NBUCKET];
+    for (int b = threadIdx.x; b < NBUCKET; b += blockDim.x) {
+        hw[b] = 0;
+        hc[b] = 0;
+    }
+    __syncthreads();
+    for (int32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
+        if (sub[x] < 0) {
+            unsigned long long v = sup[x];
+            init[x] = v;
+            int b = bucket_of(v);
+            atomicAdd(&hc[b], 1u);
+            unsigned long long w = wfull[x] - (unsigned long long)(off[x + 1] - off[x]);
+            if (w) atomicAdd(&hw[b], w);
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < NBUCKET; b += blockDim.x) {
+        if (hc[b]) {
+            atomicAdd(&st->hist_c[b], hc[b]);
+            if (hw[b]) atomicAdd(&st->hist_w[b], hw[b]);
+        }
+    }
+}
+
+// findHi with the adaptive target (one block). range = 0-based index i-1,
+// P = subsets requested.
+__global__ void __launch_bounds__(1024) k_cd_select(CdDev *st, int range, int P) {
+    __shared__ unsigned long long tmpw[33];
+    __shared__ uint32_t tmpc[33];
+    __shared__ int s_pick, s_first, s_last;
+    constexpr int PER = (NBUCKET + 1023) / 1024;
+    unsigned long long w[PER];
+    uint32_t c[PER];
+    unsigned long long wsum = 0;
+    uint32_t csum = 0;
+    for (int j = 0; j < PER; j++) {
+        int b = threadIdx.x * PER + j;
+        w[j] = b < NBUCKET ? st->hist_w[b] : 0;
+        c[j] = b < NBUCKET ? st->hist_c[b] : 0;
+        wsum += w[j];
+        csum += c[j];
+    }
+    if (threadIdx.x == 0) {
+        s_pick = NBUCKET;
+        s_first = NBUCKET;
+        s_last = -1;
+    }
+    unsigned long long wtot;
+    uint32_t ctot;
+    unsigned long long wpre = block_exclusive_scan<unsigned long long>(wsum, tmpw, &wtot);
+    block_exclusive_scan<uint32_t>(csum, tmpc, &ctot);
+    // adaptive target: tgt_i = s_{i-1} * W_rem / (P - i + 1)
+    double s_prev = 1.0;
+    if (range > 0) {
+        unsigned long long covered = st->wrem_prev - wtot;
+        if (covered > 0) s_prev = fmin(1.0, st->tgt_prev / (double)covered);
+    }
+    int left = P - range;
+    if (left < 1) left = 1;
+    double tgt = s_prev * (double)wtot / (double)left;
+    unsigned long long run = wpre;
+    for (int j = 0; j < PER; j++) {
+        int b = threadIdx.x * PER + j;
+        run += w[j];
+        if (c[j]) {
+            atomicMin(&s_first, b);
+            atomicMax(&s_last, b);
+            if ((double)run >= tgt) atomicMin(&s_pick, b);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->n_remaining = (int32_t)ctot;
+        if (ctot > 0) {
+            int b = s_pick;
+            if (tgt <= 0.0) b = s_first;
+            if (b >= NBUCKET) b = s_last;
+            unsigned long long top = bucket_top(b);
+            st->hi = top == ~0ull ? ~0ull : top + 1ull;
+        }
+        st->wrem_prev = wtot;
+        st->tgt_prev = tgt;
+    }
+}
+
+__global__ void k_set_hi(CdDev *st, unsigned long long hi) {
+    st->hi = hi;
+    st->n_remaining = 1;
+}
+
+// First activeSet of a range: remaining vertices with sup < hi, compacted
+// with a warp ballot and one atomic per warp.
+__global__ void k_cd_frontier(int32_t n, const int32_t *__restrict__ sub,
+                              const unsigned long long *__restrict__ sup, CdDev *st,
+                              int32_t *__restrict__ F) {
+    const unsigned long long hi = st->hi;
+    const int lane = threadIdx.x & 31;
+    for (int32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        int32_t x = base + threadIdx.x;
+        bool take = x < n && sub[x] < 0 && sup[x] < hi;
+        unsigned bal = __ballot_sync(0xffffffffu, take);
+        if (bal) {
+            int pos = 0;
+            if (lane == 0) pos = atomicAdd(&st->nF, __popc(bal));
+            pos = __shfl_sync(0xffffffffu, pos, 0);
+            if (take) F[pos + __popc(bal & lanemask_lt())] = x;
+        }
+    }
+}
+
+__device__ __forceinline__ void warp_append(bool take, int32_t x, int32_t *cnt, int32_t *list) {
+    unsigned bal = __ballot_sync(0xffffffffu, take);
+    if (!bal) return;
+    const int lane = threadIdx.x & 31;
+    int leader = __ffs(bal) - 1;
+    int pos = 0;
+    if (lane == leader) pos = atomicAdd(cnt, __popc(bal));
+    pos = __shfl_sync(0xffffffffu, pos, leader);
+    if (take) list[pos + __popc(bal & lanemask_lt())] = x;
+}
+
+// Assigns the activeSet to subset `range` and splits the vertices that have
+// updates to make into the three engine tiers.
+__global__ void k_cd_prepare(const int32_t *__restrict__ F, CdDev *st, int32_t range,
+                             int32_t *__restrict__ sub, const unsigned long long *__restrict__ sup,
+                             const unsigned long long *__restrict__ wfull,
+                             const int64_t *__restrict__ off, int cta_ok, int32_t *__restrict__ Lw,
+                             int32_t *__restrict__ Lc, int32_t *__restrict__ Lg) {
+    const int32_t nF = st->nF;
+    unsigned long long wsum = 0;
+    for (int32_t base = blockIdx.x * blockDim.x; base < nF; base += gridDim.x * blockDim.x) {
+        int32_t i = base + threadIdx.x;
+        int32_t x = -1;
+        int tier = -1;
+        if (i < nF) {
+            x = F[i];
+            sub[x] = range;
+            if (sup[x] > 0) {
+                unsigned long long W = wfull[x];
+                int64_t deg = off[x + 1] - off[x];
+                wsum += W;
+                if (W <= (unsigned long long)WARP_MAX_W)
+                    tier = 0;
+                else if (cta_ok && deg < 65535)
+                    tier = 1;
+                else
+                    tier = 2;
+            }
+        }
+        warp_append(tier == 0, x, &st->nLw, Lw);
+        warp_append(tier == 1, x, &st->nLc, Lc);
+        warp_append(tier == 2, x, &st->nLg, Lg);
+    }
+    wsum = warp_sum(wsum);
+    if ((threadIdx.x & 31) == 0 && wsum) atomicAdd(&st->wedges, wsum);
+}
+
+// Support decrement of one (x, x') pair with crossing detection.
+struct CdEmit {
+    unsigned long long *sup;
+    const int32_t *sub;
+    unsigned long long hi;
+    int32_t *next;
+    int32_t *n_next;
+    __device__ __forceinline__ void operator()(int32_t k, uint32_t c) {
+        if (sub[k] >= 0) return;
+        unsigned long long d = choose2(c);
+        unsigned long long old = atomicAdd(&sup[k], 0ull - d);
+        if (old >= hi && old - d < hi) next[atomicAdd(n_next, 1)] = k;
+    }
+};
+
+struct PeelMids {
+    const int32_t *adj_s;
+    const int64_t *off_o;
+    __device__ __forceinline__ void seg(int64_t q, int64_t &beg, int32_t &len) const {
+        int32_t y = adj_s[q];
+        beg = off_o[y];
+        len = (int32_t)(off_o[y + 1] - beg);
+    }
+};
+
+struct PeelArgs {
+    const int64_t *off_s;
+    const int32_t *adj_s;
+    const int64_t *off_o;
+    const int32_t *adj_o;
+    unsigned long long *sup;
+    const int32_t *sub;
+    CdDev *st;
+    const int32_t *Lw, *Lc, *Lg;
+    int32_t *Lo;
+    int32_t *next;
+};
+
+__global__ void __launch_bounds__(256) k_cd_update_warp(PeelArgs a) {
+    __shared__ int32_t skey[8][WARP_SLOTS];
+    __shared__ uint32_t sval[8][WARP_SLOTS];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    WarpHash H{skey[w], sval[w]};
+    H.clear(lane);
+    __syncwarp();
+    const int32_t n = a.st->nLw;
+    CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext};
+    for (;;) {
+        int idx = 0;
+        if (lane == 0) idx = atomicAdd(&a.st->work[0], 1);
+        idx = __shfl_sync(0xffffffffu, idx, 0);
+        if (idx >= n) break;
+        const int32_t x = a.Lw[idx];
+        const int64_t q0 = a.off_s[x], q1 = a.off_s[x + 1];
+        for (int64_t qb = q0; qb < q1; qb += 32) {
+            int64_t q = qb + lane;
+            int64_t beg = 0;
+            int32_t len = 0;
+            if (q < q1) {
+                int32_t y = a.adj_s[q];
+                beg = a.off_o[y];
+                len = (int32_t)(a.off_o[y + 1] - beg);
+            }
+            int cnt = (int)imin64(32, q1 - qb);
+            for (int t = 0; t < cnt; t++) {
+                int64_t b = __shfl_sync(0xffffffffu, beg, t);
+                int32_t l = __shfl_sync(0xffffffffu, len, t);
+                for (int p = lane; p < l; p += 32) {
+                    int32_t k = a.adj_o[b + p];
+                    if (k != x) H.add(k);
+                }
+            }
+        }
+        __syncwarp();
+        for (int i = lane; i < WARP_SLOTS; i += 32) {
+            int32_t k = skey[w][i];
+            if (k != EMPTY_KEY) {
+                uint32_t c = sval[w][i];
+                if (c >= 2) emit(k, c);
+                skey[w][i] = EMPTY_KEY;
+                sval[w][i] = 0;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <class Eng>
+struct PeelVisit {
+    Eng *eng;
+    int32_t self;
+    __device__ __forceinline__ void operator()(int, int32_t key) {
+        if (key != self) eng->add(key);
+    }
+};
+
+__global__ void __launch_bounds__(CTA_THREADS) k_cd_update_cta(PeelArgs a, int32_t headn, int32_t bm_words,
+                                                            int32_t keyspace) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_idx, s_used, s_over;
+    CtaHybrid H;
+    size_t hw = (size_t)(((headn >> 1) + 3) & ~3);
+    H.head = (uint32_t *)smem;
+    H.bm = H.head + hw;
+    H.rkey = (int32_t *)(H.bm + bm_words);
+    H.rval = (uint32_t *)(H.rkey + REPEAT_SLOTS);
+    Chunk ch;
+    ch.beg = (int64_t *)(H.rval + REPEAT_SLOTS);
+    ch.pre = (int32_t *)(ch.beg + MID_CHUNK);
+    ch.tmp = ch.pre + MID_CHUNK + 1;
+    H.s_used = &s_used;
+    H.s_over = &s_over;
+    H.headn = headn;
+    H.bm_words = bm_words;
+    H.set_active(keyspace);
+    H.clear_all();
+    __syncthreads();
+    const int32_t n = a.st->nLc;
+    CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext};
+    PeelMids M{a.adj_s, a.off_o};
+    for (;;) {
+        if (threadIdx.x == 0) s_idx = atomicAdd(&a.st->work[1], 1);
+        __syncthreads();
+        int idx = s_idx;
+        if (idx >= n) break;
+        const int32_t x = a.Lc[idx];
+        PeelVisit<CtaHybrid> v{&H, x};
+        cta_walk(M, a.off_s[x], a.off_s[x + 1], a.adj_o, ch, v);
+        if (!s_over)
+            H.flush(emit);
+        else if (threadIdx.x == 0)
+            a.Lo[atomicAdd(&a.st->nLo, 1)] = x;
+        __syncthreads();
+        H.clear_active();
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(CTA_THREADS) k_cd_update_global(PeelArgs a, uint32_t *gcnt,
+                                                               int32_t *gtouch, int64_t keyspace) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_idx, s_nt;
+    Chunk ch;
+    ch.beg = (int64_t *)smem;
+    ch.pre = (int32_t *)(ch.beg + MID_CHUNK);
+    ch.tmp = ch.pre + MID_CHUNK + 1;
+    GlobalDense G{gcnt + (size_t)blockIdx.x * keyspace, gtouch + (size_t)blockIdx.x * keyspace, &s_nt};
+    const int32_t n1 = a.st->nLg, n2 = a.st->nLo;
+    CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext};
+    PeelMids M{a.adj_s, a.off_o};
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_idx = atomicAdd(&a.st->work[2], 1);
+            s_nt = 0;
+        }
+        __syncthreads();
+        int idx = s_idx;
+        if (idx >= n1 + n2) break;
+        const int32_t x = idx < n1 ? a.Lg[idx] : a.Lo[idx - n1];
+        PeelVisit<GlobalDense> v{&G, x};
+        cta_walk(M, a.off_s[x], a.off_s[x + 1], a.adj_o, ch, v);
+        G.flush(emit);
+        __syncthreads();
+        G.clear();
+        __syncthreads();
+    }
+}
+
+// Next round: the vertices that crossed below hi become the activeSet.
+__global__ void k_cd_advance(CdDev *st) {
+    st->nF = st->nNext;
+    st->nNext = 0;
+    st->nLw = st->nLc = st->nLg = st->nLo = 0;
+    st->work[0] = st->work[1] = st->work[2] = st->work[3] = 0;
+}
+
+__global__ void k_cd_new_range(CdDev *st) {
+    st->nF = st->nNext = 0;
+    st->nLw = st->nLc = st->nLg = st->nLo = 0;
+    st->work[0] = st->work[1] = st->work[2] = st->work[3] = 0;
+    for (int b = 0; b < NBUCKET; b++) {
+        st->hist_w[b] = 0;
+        st->hist_c[b] = 0;
+    }
+}
+
+// Vertices left after the last range form one more subset; their init is
+// their current support.
+__global__ void k_cd_leftover(int32_t n, int32_t *__restrict__ sub,
+                              const unsigned long long *__restrict__ sup,
+                              unsigned long long *__restrict__ init, int32_t range, int *any) {
+    for (int32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
+        if (sub[x] < 0) {
+            init[x] = sup[x];
+            sub[x] = range;
+            *any = 1;
+        }
+    }
+}
+
+}  // namespace
+
+int64_t max_cta_keyspace(int64_t want, size_t extra) {
+    const size_t cap = (size_t)max_smem_optin();
+    if (hybrid_bytes(want, nullptr, nullptr) + extra <= cap) return want;
+    int64_t lo = 0, hi = want;
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) / 2;
+        if (hybrid_bytes(mid, nullptr, nullptr) + extra <= cap)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
+    const int32_t n = D.n;
+    const int sms = num_sms();
+    const Side &S = *D.S;
+    const Side &O = *D.O;
+    const int P = opt.P > 0 ? opt.P : 150;
+    D.bounds.clear();
+    D.bounds.push_back(0);
+    if (n == 0) {
+        D.p_eff = 0;
+        return;
+    }
+    DevBuf<CdDev> st(1, s);
+    st.zero();
+    DevBuf<int32_t> F(n, s), Nx(n, s), Lw(n, s), Lc(n, s), Lg(n, s), Lo(n, s);
+    // tiers available for peel anchors (key space = whole side)
+    const size_t chunk_extra = CHUNK_BYTES;
+    int32_t headn = 0, bmw = 0;
+    const bool cta_ok = max_cta_keyspace(n, chunk_extra) >= n;
+    size_t smem_cta = cta_ok ? hybrid_bytes(n, &headn, &bmw) + chunk_extra : 0;
+    if (cta_ok)
+        RC_CUDA(cudaFuncSetAttribute(k_cd_update_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem_cta));
+    const int gblocks = std::max(1, sms / 2);
+    DevBuf<uint32_t> gcnt((size_t)gblocks * n, s);
+    DevBuf<int32_t> gtouch((size_t)gblocks * n, s);
+    gcnt.zero();
+    const size_t smem_glob = chunk_extra;
+    RC_CUDA(cudaFuncSetAttribute(k_cd_update_global, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_glob));
+    unsigned long long *hpin = nullptr;
+    RC_CUDA(cudaMallocHost((void **)&hpin, 64));
+    struct PinGuard {
+        void *p;
+        ~PinGuard() { cudaFreeHost(p); }
+    } pg{hpin};
+    int32_t *hi32 = reinterpret_cast<int32_t *>(hpin);
+
+    k_init_state<<<ceil_div(n, 256), 256, 0, s>>>(D.sub, n);
+    RC_LAUNCH();
+    const int nb = std::min(ceil_div(n, 512), sms * 4);
+    int range = 0;
+    uint64_t lo = 0;
+    const int nranges = opt.n_bounds > 0 ? std::min(opt.n_bounds, P) : P;
+    int32_t *cur = F.get(), *nxt = Nx.get();
+    for (range = 0; range < nranges; range++) {
+        k_cd_new_range<<<1, 1, 0, s>>>(st.get());
+        RC_LAUNCH();
+        k_cd_hist<<<nb, 512, 0, s>>>(n, D.sub, D.sup, D.wfull, S.off, D.init, st.get());
+        RC_LAUNCH();
+        if (opt.n_bounds > 0) {
+            k_set_hi<<<1, 1, 0, s>>>(st.get(), opt.h_bounds[range]);
+        } else {
+            k_cd_select<<<1, 1024, 0, s>>>(st.get(), range, P);
+        }
+        RC_LAUNCH();
+        // hi (8 B) and n_remaining (4 B) back to the host
+        RC_CUDA(cudaMemcpyAsync(hpin, &st.get()->hi, 8, cudaMemcpyDeviceToHost, s));
+        RC_CUDA(cudaMemcpyAsync(hi32 + 2, &st.get()->n_remaining, 4, cudaMemcpyDeviceToHost, s));
+        RC_CUDA(cudaStreamSynchronize(s));
+        const uint64_t hi = hpin[0];
+        if (hi32[2] == 0) break;  // nothing remains
+        k_cd_frontier<<<nb, 512, 0, s>>>(n, D.sub, D.sup, st.get(), cur);
+        RC_LAUNCH();
+        for (;;) {
+            k_cd_prepare<<<nb, 512, 0, s>>>(cur, st.get(), range, D.sub, D.sup, D.wfull, S.off,
+                                            cta_ok ? 1 : 0, Lw.get(), Lc.get(), Lg.get());
+            RC_LAUNCH();
+            PeelArgs a{S.off, S.adj, O.off, O.adj, D.sup, D.sub, st.get(),
+                       Lw.get(), Lc.get(), Lg.get(), Lo.get(), nxt};
+            k_cd_update_warp<<<sms * 8, 256, 0, s>>>(a);
+            RC_LAUNCH();
+            if (cta_ok) {
+                k_cd_update_cta<<<sms, CTA_THREADS, smem_cta, s>>>(a, headn, bmw, n);
+                RC_LAUNCH();
+            }
+            k_cd_update_global<<<gblocks, CTA_THREADS, smem_glob, s>>>(a, gcnt.get(), gtouch.get(),
+                                                                      n);
+            RC_LAUNCH();
+            D.rounds++;
+            RC_CUDA(cudaMemcpyAsync(hi32 + 4, &st.get()->nNext, 4, cudaMemcpyDeviceToHost, s));
+            RC_CUDA(cudaStreamSynchronize(s));
+            if (hi32[4] == 0) break;
+            k_cd_advance<<<1, 1, 0, s>>>(st.get());
+            RC_LAUNCH();
+            std::swap(cur, nxt);
+        }
+        lo = hi;
+        D.bounds.push_back(hi);
+    }
+    // leftover subset with an open range
+    DevBuf<int> any(1, s);
+    any.zero();
+    k_cd_leftover<<<nb, 512, 0, s>>>(n, D.sub, D.sup, D.init, range, any.get());
+    RC_LAUNCH();
+    int hany = 0;
+    RC_CUDA(cudaMemcpyAsync(&hany, any.get(), 4, cudaMemcpyDeviceToHost, s));
+    unsigned long long hw = 0;
+    RC_CUDA(cudaMemcpyAsync(&hw, &st.get()->wedges, 8, cudaMemcpyDeviceToHost, s));
+    RC_CUDA(cudaStreamSynchronize(s));
+    D.p_eff = range + (hany ? 1 : 0);
+    if (hany) D.bounds.push_back(~0ull);
+    D.wedges_cd = hw;
+    (void)lo;
+}
+
+// wfull for side s
+void compute_wfull(const Side &S, const Side &O, int64_t m, unsigned long long *wfull,
+                   cudaStream_t s) {
+    if (S.n == 0) return;
+    if (m == 0) {
+        RC_CUDA(cudaMemsetAsync(wfull, 0, sizeof(unsigned long long) * S.n, s));
+        return;
+    }
+    DevBuf<int64_t> dn(m + 1, s), ps(m + 1, s);
+    k_deg_of_nbr<<<ceil_div(m, 256), 256, 0, s>>>(S.adj, m, O.off, dn.get());
+    RC_LAUNCH();
+    RC_CUDA(cudaMemsetAsync(dn.get() + m, 0, sizeof(int64_t), s));
+    scan_exclusive<int64_t>(dn.get(), ps.get(), m + 1, s);
+    k_wfull<<<ceil_div(S.n, 256), 256, 0, s>>>(S.off, S.n, ps.get(), wfull);
+    RC_LAUNCH();
+}
+
+}  // namespace receipt

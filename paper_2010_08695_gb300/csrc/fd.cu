@@ -1,0 +1,429 @@
+// Fine-grained decomposition, Algorithm 4 (RECEIPT FD), with the
+// workload-aware scheduling of Sec. 3.2.1.
+//
+// Setup (all on the device):
+//  * members of every subset U_i, ordered by local id; rank[x] = position of
+//    x inside its subset (the key space of G_i's aggregation);
+//  * the induced subgraphs G_i = (U_i, V, E_i) all at once: the other side's
+//    adjacency (sorted by (y, x)) is stably sorted by sub(x), so the block of
+//    subset i lists, for every y, the ranks of y's neighbours inside U_i as
+//    one contiguous run; every edge (x, y) of side s records where its run
+//    (sub(x), y) starts and how long it is;
+//  * a task queue of subset ids in decreasing order of their wedge count
+//    (Longest Processing Time first).
+//
+// Peeling: persistent CTAs pop subsets from the queue with one atomic each.
+// Inside a subset the CTA runs bottom-up peeling level by level: the level
+// mu = max(previous level, min support over the remaining vertices); every
+// vertex whose raw support is <= mu is peeled with tip number mu, and the
+// updates of Algorithm 2 restricted to G_i are applied. Peeling all
+// minimum-support vertices together gives the same tip numbers as peeling
+// them one at a time: max(mu, max(mu, a) - b) = max(mu, a - b) for b >= 0,
+// and supports are order independent (Lemma 1).
+#include <algorithm>
+
+#include "engine.cuh"
+#include "internal.cuh"
+
+namespace receipt {
+
+namespace {
+
+constexpr int FD_THREADS = 512;
+
+__global__ void k_sub_keys(const int32_t *__restrict__ sub, int32_t n, uint64_t *__restrict__ key,
+                           uint32_t *__restrict__ val, int32_t *__restrict__ cnt) {
+    int32_t x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x < n) {
+        key[x] = (uint64_t)sub[x];
+        val[x] = (uint32_t)x;
+        atomicAdd(&cnt[sub[x]], 1);
+    }
+}
+
+__global__ void k_members(const uint32_t *__restrict__ sorted_x, int32_t n,
+                          const int32_t *__restrict__ sub, const int32_t *__restrict__ mstart,
+                          int32_t *__restrict__ members, int32_t *__restrict__ rank) {
+    int32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) {
+        int32_t x = (int32_t)sorted_x[p];
+        members[p] = x;
+        rank[x] = p - mstart[sub[x]];
+    }
+}
+
+__global__ void k_edge_sub_keys(const int32_t *__restrict__ adj_o, int64_t m,
+                                const int32_t *__restrict__ sub, uint64_t *__restrict__ key,
+                                uint32_t *__restrict__ val) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < m) {
+        key[k] = (uint64_t)sub[adj_o[k]];
+        val[k] = (uint32_t)k;
+    }
+}
+
+__device__ __forceinline__ int32_t owner_of(const int64_t *off, int32_t n, int64_t q) {
+    int32_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int32_t mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= q)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// For sorted position p: y, sub, rank, and run head flag.
+__global__ void k_fd_fill(const uint32_t *__restrict__ perm, int64_t m, const int32_t *__restrict__ adj_o,
+                          const int64_t *__restrict__ off_o, int32_t n_o,
+                          const int32_t *__restrict__ sub, const int32_t *__restrict__ rank,
+                          int32_t *__restrict__ fd_adj, int32_t *__restrict__ fd_y,
+                          uint32_t *__restrict__ head) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= m) return;
+    int64_t k = perm[p];
+    int32_t x = adj_o[k];
+    int32_t y = owner_of(off_o, n_o, k);
+    fd_adj[p] = rank[x];
+    fd_y[p] = y;
+    uint32_t h = 1;
+    if (p > 0) {
+        int64_t k2 = perm[p - 1];
+        int32_t x2 = adj_o[k2];
+        int32_t y2 = owner_of(off_o, n_o, k2);
+        h = (sub[x2] != sub[x] || y2 != y) ? 1u : 0u;
+    }
+    head[p] = h;
+}
+
+__global__ void k_run_starts(const uint32_t *__restrict__ head, const uint32_t *__restrict__ hpos,
+                             int64_t m, int64_t *__restrict__ run_start) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < m && head[p]) run_start[hpos[p]] = p;
+}
+
+// Run of every side-s edge (x, y), and each subset's wedge count.
+__global__ void k_fd_edges(const uint32_t *__restrict__ perm, int64_t m,
+                           const int32_t *__restrict__ adj_o, const int32_t *__restrict__ fd_y,
+                           const uint32_t *__restrict__ head, const uint32_t *__restrict__ hpos,
+                           const int64_t *__restrict__ run_start, int64_t nruns,
+                           const int64_t *__restrict__ off_s, const int32_t *__restrict__ adj_s,
+                           const int32_t *__restrict__ sub, int64_t *__restrict__ fd_beg,
+                           int32_t *__restrict__ fd_len, unsigned long long *__restrict__ wsub) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= m) return;
+    int64_t r = (int64_t)hpos[p] + head[p] - 1;  // run id
+    int64_t rs = run_start[r];
+    int64_t re = r + 1 < nruns ? run_start[r + 1] : m;
+    int32_t x = adj_o[perm[p]];
+    int32_t y = fd_y[p];
+    int64_t b = off_s[x];
+    int64_t ps = b + lower_bound_i32(adj_s + b, off_s[x + 1] - b, y);
+    fd_beg[ps] = rs;
+    fd_len[ps] = (int32_t)(re - rs);
+    if (head[p]) {
+        unsigned long long L = (unsigned long long)(re - rs);
+        if (L > 1) atomicAdd(&wsub[sub[x]], L * (L - 1));
+    }
+}
+
+// LPT order: rank of subset i = number of subsets with larger work (ties by id).
+__global__ void k_lpt(const unsigned long long *__restrict__ wsub, const int32_t *__restrict__ mstart,
+                      int32_t P, int32_t *__restrict__ queue) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    unsigned long long ki = wsub[i] + (unsigned long long)(mstart[i + 1] - mstart[i]);
+    int32_t r = 0;
+    for (int32_t j = 0; j < P; j++) {
+        unsigned long long kj = wsub[j] + (unsigned long long)(mstart[j + 1] - mstart[j]);
+        if (kj > ki || (kj == ki && j < i)) r++;
+    }
+    queue[r] = i;
+}
+
+struct FdArgs {
+    const int32_t *queue;
+    int32_t P;
+    int32_t *qhead;
+    const int32_t *mstart;
+    const int32_t *members;
+    const int64_t *off_s;
+    const int64_t *fd_beg;
+    const int32_t *fd_len;
+    const int32_t *fd_adj;
+    const int32_t *new2old;
+    const unsigned long long *init;
+    unsigned long long *fsup;  // by member position
+    uint8_t *alive;            // by member position
+    int32_t *alist;            // by member position
+    int32_t *plist;            // by member position
+    unsigned long long *tip;   // output, original ids
+    unsigned long long *stats; // [0] wedges, [1] levels
+    uint32_t *gcnt;            // global engine, per CTA slot
+    int32_t *gtouch;
+    int64_t gks;               // global engine key space per slot
+    int32_t cta_ks;            // largest subset the shared-memory engine takes
+};
+
+struct FdMids {
+    const int64_t *fd_beg;
+    const int32_t *fd_len;
+    __device__ __forceinline__ void seg(int64_t q, int64_t &beg, int32_t &len) const {
+        beg = fd_beg[q];
+        len = fd_len[q];
+    }
+};
+
+struct FdEmit {
+    unsigned long long *fsup;  // subset base
+    const uint8_t *alive;      // subset base
+    __device__ __forceinline__ void operator()(int32_t k, uint32_t c) {
+        if (alive[k]) atomicAdd(&fsup[k], 0ull - choose2(c));
+    }
+};
+
+template <class Eng>
+struct FdVisit {
+    Eng *eng;
+    int32_t self;
+    __device__ __forceinline__ void operator()(int, int32_t key) {
+        if (key != self) eng->add(key);
+    }
+};
+
+__global__ void __launch_bounds__(FD_THREADS) k_fd_peel(FdArgs a, int32_t headn, int32_t bm_words) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_t, s_used, s_over, s_nt, s_np, s_nk;
+    __shared__ unsigned long long s_min[32];
+    __shared__ int32_t s_tmp[33];
+    CtaHybrid H;
+    size_t hw = (size_t)(((headn >> 1) + 3) & ~3);
+    H.head = (uint32_t *)smem;
+    H.bm = H.head + hw;
+    H.rkey = (int32_t *)(H.bm + bm_words);
+    H.rval = (uint32_t *)(H.rkey + REPEAT_SLOTS);
+    Chunk ch;
+    ch.beg = (int64_t *)(H.rval + REPEAT_SLOTS);
+    ch.pre = (int32_t *)(ch.beg + MID_CHUNK);
+    ch.tmp = ch.pre + MID_CHUNK + 1;
+    H.s_used = &s_used;
+    H.s_over = &s_over;
+    H.headn = headn;
+    H.bm_words = bm_words;
+    H.set_active((int64_t)headn + (int64_t)bm_words * 32);
+    H.clear_all();
+    GlobalDense G{a.gcnt ? a.gcnt + (size_t)blockIdx.x * a.gks : nullptr,
+                  a.gtouch ? a.gtouch + (size_t)blockIdx.x * a.gks : nullptr, &s_nt};
+    FdMids M{a.fd_beg, a.fd_len};
+    unsigned long long wedges = 0, levels = 0;
+    __syncthreads();
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_t = atomicAdd(a.qhead, 1);
+        __syncthreads();
+        const int t = s_t;
+        if (t >= a.P) break;
+        const int32_t i = a.queue[t];
+        const int32_t mb = a.mstart[i];
+        const int32_t ni = a.mstart[i + 1] - mb;
+        if (ni == 0) continue;
+        unsigned long long *fsup = a.fsup + mb;
+        uint8_t *alive = a.alive + mb;
+        int32_t *alist = a.alist + mb;
+        int32_t *plist = a.plist + mb;
+        const int32_t *mem = a.members + mb;
+        for (int r = threadIdx.x; r < ni; r += blockDim.x) {
+            fsup[r] = a.init[mem[r]];
+            alive[r] = 1;
+            alist[r] = r;
+        }
+        const bool small = ni <= a.cta_ks;
+        if (small) {
+            H.set_active(ni);
+        }
+        int32_t nalive = ni;
+        unsigned long long level = 0;
+        __syncthreads();
+        while (nalive > 0) {
+            // minimum support over the remaining vertices
+            unsigned long long mn = ~0ull;
+            for (int j = threadIdx.x; j < nalive; j += blockDim.x) {
+                unsigned long long v = fsup[alist[j]];
+                mn = v < mn ? v : mn;
+            }
+            mn = warp_min(mn);
+            if ((threadIdx.x & 31) == 0) s_min[threadIdx.x >> 5] = mn;
+            __syncthreads();
+            if (threadIdx.x < 32) {
+                unsigned long long v = threadIdx.x < (blockDim.x >> 5) ? s_min[threadIdx.x] : ~0ull;
+                v = warp_min(v);
+                if (threadIdx.x == 0) s_min[0] = v;
+            }
+            __syncthreads();
+            const unsigned long long mu = s_min[0] > level ? s_min[0] : level;
+            level = mu;
+            levels++;
+            // peel every remaining vertex with support <= mu; compact the rest
+            if (threadIdx.x == 0) {
+                s_np = 0;
+                s_nk = 0;
+            }
+            __syncthreads();
+            for (int base = 0; base < nalive; base += blockDim.x) {
+                int j = base + threadIdx.x;
+                int32_t r = -1;
+                unsigned long long v = 0;
+                if (j < nalive) {
+                    r = alist[j];
+                    v = fsup[r];
+                }
+                bool keep = (r >= 0) && v > mu;
+                int32_t total;
+                int32_t pos = block_exclusive_scan<int32_t>(keep ? 1 : 0, s_tmp, &total);
+                if (keep) alist[s_nk + pos] = r;
+                if (r >= 0 && !keep) {
+                    alive[r] = 0;
+                    a.tip[a.new2old[mem[r]]] = mu;
+                    if (v > 0) plist[atomicAdd(&s_np, 1)] = r;
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) s_nk += total;
+                __syncthreads();
+            }
+            nalive = s_nk;
+            const int np = s_np;
+            // updates of the peeled vertices inside G_i
+            for (int pi = 0; pi < np; pi++) {
+                const int32_t r = plist[pi];
+                const int32_t x = mem[r];
+                const int64_t q0 = a.off_s[x], q1 = a.off_s[x + 1];
+                FdEmit emit{fsup, alive};
+                if (small && q1 - q0 < 65535) {
+                    FdVisit<CtaHybrid> v{&H, r};
+                    wedges += cta_walk(M, q0, q1, a.fd_adj, ch, v);
+                    if (!s_over) {
+                        H.flush(emit);
+                        __syncthreads();
+                        H.clear_active();
+                        __syncthreads();
+                        continue;
+                    }
+                    __syncthreads();
+                    H.clear_active();
+                    __syncthreads();
+                }
+                if (threadIdx.x == 0) s_nt = 0;
+                __syncthreads();
+                FdVisit<GlobalDense> v{&G, r};
+                cta_walk(M, q0, q1, a.fd_adj, ch, v);
+                G.flush(emit);
+                __syncthreads();
+                G.clear();
+                __syncthreads();
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(&a.stats[0], wedges);
+        atomicAdd(&a.stats[1], levels);
+    }
+}
+
+}  // namespace
+
+void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
+    const int32_t n = D.n;
+    const int64_t m = D.m;
+    const int32_t P = D.p_eff;
+    if (n == 0 || P == 0) return;
+    const Side &S = *D.S;
+    const Side &O = *D.O;
+    // members and ranks
+    DevBuf<int32_t> cnt(P + 1, s), mstart(P + 1, s), members(n, s), rank(n, s);
+    cnt.zero();
+    {
+        DevBuf<uint64_t> key(n, s);
+        DevBuf<uint32_t> val(n, s);
+        k_sub_keys<<<ceil_div(n, 256), 256, 0, s>>>(D.sub, n, key.get(), val.get(), cnt.get());
+        RC_LAUNCH();
+        radix_sort_pairs(key.get(), val.get(), n, 0, bits_for((uint64_t)P), s);
+        scan_exclusive<int32_t>(cnt.get(), mstart.get(), P + 1, s);
+        k_members<<<ceil_div(n, 256), 256, 0, s>>>(val.get(), n, D.sub, mstart.get(), members.get(),
+                                                   rank.get());
+        RC_LAUNCH();
+    }
+    // induced subgraphs
+    DevBuf<int32_t> fd_adj(m, s), fd_len(m, s);
+    DevBuf<int64_t> fd_beg(m, s);
+    DevBuf<unsigned long long> wsub(P, s);
+    wsub.zero();
+    if (m > 0) {
+        DevBuf<uint64_t> key(m, s);
+        DevBuf<uint32_t> perm(m, s);
+        k_edge_sub_keys<<<ceil_div(m, 256), 256, 0, s>>>(O.adj, m, D.sub, key.get(), perm.get());
+        RC_LAUNCH();
+        radix_sort_pairs(key.get(), perm.get(), m, 0, bits_for((uint64_t)P), s);
+        key.release();
+        DevBuf<int32_t> fd_y(m, s);
+        DevBuf<uint32_t> head(m + 1, s), hpos(m + 1, s);
+        k_fd_fill<<<ceil_div(m, 256), 256, 0, s>>>(perm.get(), m, O.adj, O.off, O.n, D.sub,
+                                                   rank.get(), fd_adj.get(), fd_y.get(), head.get());
+        RC_LAUNCH();
+        RC_CUDA(cudaMemsetAsync(head.get() + m, 0, 4, s));
+        scan_exclusive<uint32_t>(head.get(), hpos.get(), m + 1, s);
+        uint32_t nruns = 0;
+        RC_CUDA(cudaMemcpyAsync(&nruns, hpos.get() + m, 4, cudaMemcpyDeviceToHost, s));
+        RC_CUDA(cudaStreamSynchronize(s));
+        DevBuf<int64_t> run_start(nruns + 1, s);
+        k_run_starts<<<ceil_div(m, 256), 256, 0, s>>>(head.get(), hpos.get(), m, run_start.get());
+        RC_LAUNCH();
+        k_fd_edges<<<ceil_div(m, 256), 256, 0, s>>>(perm.get(), m, O.adj, fd_y.get(), head.get(),
+                                                    hpos.get(), run_start.get(), nruns, S.off, S.adj,
+                                                    D.sub, fd_beg.get(), fd_len.get(), wsub.get());
+        RC_LAUNCH();
+    }
+    DevBuf<int32_t> queue(P, s);
+    k_lpt<<<ceil_div(P, 256), 256, 0, s>>>(wsub.get(), mstart.get(), P, queue.get());
+    RC_LAUNCH();
+    // largest subset
+    std::vector<int32_t> hms(P + 1);
+    RC_CUDA(cudaMemcpyAsync(hms.data(), mstart.get(), sizeof(int32_t) * (P + 1),
+                            cudaMemcpyDeviceToHost, s));
+    RC_CUDA(cudaStreamSynchronize(s));
+    int32_t maxn = 0;
+    for (int i = 0; i < P; i++) maxn = std::max(maxn, hms[i + 1] - hms[i]);
+    const int64_t cta_ks = max_cta_keyspace(maxn, CHUNK_BYTES);
+    int32_t headn = 0, bmw = 0;
+    size_t smem = hybrid_bytes(std::max<int64_t>(cta_ks, 2), &headn, &bmw) + CHUNK_BYTES;
+    RC_CUDA(cudaFuncSetAttribute(k_fd_peel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int occ = 0;
+    RC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fd_peel, FD_THREADS, smem));
+    const int grid = std::max(1, std::min(num_sms() * std::max(occ, 1), P));
+    // global engine slots: subsets above the shared-memory key space, hub
+    // anchors (degree >= 2^16) and anchors whose repeat table overflowed
+    DevBuf<uint32_t> gcnt((size_t)grid * maxn, s);
+    DevBuf<int32_t> gtouch((size_t)grid * maxn, s);
+    gcnt.zero();
+    DevBuf<unsigned long long> fsup(n, s);
+    DevBuf<uint8_t> alive(n, s);
+    DevBuf<int32_t> alist(n, s), plist(n, s), qhead(1, s);
+    DevBuf<unsigned long long> stats(2, s);
+    qhead.zero();
+    stats.zero();
+    FdArgs a{queue.get(),   P,           qhead.get(),     mstart.get(), members.get(),
+             S.off,         fd_beg.get(), fd_len.get(),   fd_adj.get(), S.new2old,
+             D.init,        fsup.get(),  alive.get(),     alist.get(),  plist.get(),
+             (unsigned long long *)d_tip, stats.get(),    gcnt.get(),   gtouch.get(),
+             (int64_t)maxn, (int32_t)cta_ks};
+    k_fd_peel<<<grid, FD_THREADS, smem, s>>>(a, headn, bmw);
+    RC_LAUNCH();
+    unsigned long long hs[2] = {0, 0};
+    RC_CUDA(cudaMemcpyAsync(hs, stats.get(), sizeof(hs), cudaMemcpyDeviceToHost, s));
+    RC_CUDA(cudaStreamSynchronize(s));
+    D.wedges_fd = hs[0];
+    D.levels = (int64_t)hs[1];
+}
+
+}  // namespace receipt

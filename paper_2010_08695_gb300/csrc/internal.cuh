@@ -1,0 +1,50 @@
+// Cross-translation-unit declarations of libreceipt.so (host side).
+#pragma once
+
+#include "common.cuh"
+
+namespace receipt {
+
+receipt_graph *build_graph(const int32_t *d_eu, const int32_t *d_ev, int64_t m, int32_t nu,
+                           int32_t nv, int dedup, cudaStream_t s);
+void destroy_graph(receipt_graph *g);
+
+// Butterfly counts of both sides by local id; returns wedges traversed.
+uint64_t count_local(const receipt_graph *g, unsigned long long *cnt_u, unsigned long long *cnt_v,
+                     cudaStream_t s);
+void scatter_to_original(const unsigned long long *local, const int32_t *new2old, int32_t n,
+                         unsigned long long *out, cudaStream_t s);
+
+// Largest key space whose CtaHybrid engine plus `extra` bytes fits in the
+// opt-in shared memory of one CTA (capped at `want`); 0 if none.
+int64_t max_cta_keyspace(int64_t want, size_t extra);
+
+// Full tip decomposition of side `side` of g into d_tip (original ids).
+void tip_decompose_impl(receipt_graph *g, int side, uint64_t *d_tip, const receipt_options *opt,
+                        cudaStream_t s);
+
+}  // namespace receipt
+
+namespace receipt {
+
+// Working state of one decomposition of side `s` (device pointers, local ids).
+struct Decomp {
+    int s = 0;
+    const Side *S = nullptr;  // side being decomposed
+    const Side *O = nullptr;  // other side
+    int32_t n = 0;
+    int64_t m = 0;
+    unsigned long long *sup = nullptr;    // raw supports
+    unsigned long long *init = nullptr;   // support when the vertex's range began
+    int32_t *sub = nullptr;               // subset index, -1 while remaining
+    unsigned long long *wfull = nullptr;  // sum of d_y over y in N_x
+    int32_t p_eff = 0;
+    std::vector<uint64_t> bounds;         // theta(1..p_eff+1)
+    uint64_t wedges_cd = 0, wedges_fd = 0;
+    int64_t rounds = 0, levels = 0;
+};
+
+void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s);
+void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s);
+
+}  // namespace receipt

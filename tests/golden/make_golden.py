@@ -1,0 +1,63 @@
+"""Writes the stored expected values of the large parity cases.
+
+Calls only ``synth`` (the seeded inputs) and ``oracle`` (the CPU reference);
+nothing here touches the CUDA library. For each workload it records the
+SHA-256 of the generated edge list (so a different draw on another machine is
+caught before any comparison), the SHA-256 of the oracle's per-vertex
+butterfly counts on both sides and of its tip numbers for the decomposed
+side, plus a seeded sample of individual values for readable failures.
+
+Usage: python tests/golden/make_golden.py CFG [CFG ...]
+"""
+import hashlib
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import oracle  # noqa: E402
+import synth  # noqa: E402
+
+
+def sha(a):
+    return hashlib.sha256(np.ascontiguousarray(a, dtype="<u8").tobytes()).hexdigest()
+
+
+def make(cfg, with_tips=True):
+    t0 = time.time()
+    eu, ev, nu, nv, side = synth.config_graph(cfg)
+    rec = {"config": cfg, "nu": nu, "nv": nv, "m": int(len(eu)), "side": side,
+           "edges_sha256": synth.edges_sha256(eu, ev)}
+    cu, cv = oracle.count_2hop(eu, ev, nu, nv)
+    rec["count_u_sha256"] = sha(cu)
+    rec["count_v_sha256"] = sha(cv)
+    rec["butterflies"] = int(cu.sum()) // 2
+    rng = np.random.default_rng(1234 + cfg)
+    su = np.unique(rng.integers(0, nu, 64))
+    sv = np.unique(rng.integers(0, nv, 64))
+    rec["sample_u"] = {int(x): int(cu[x]) for x in su}
+    rec["sample_v"] = {int(x): int(cv[x]) for x in sv}
+    if with_tips:
+        tips, st = oracle.bup(eu, ev, nu, nv, side)
+        assert st["complete"]
+        rec["tips_sha256"] = sha(tips)
+        rec["tip_max"] = int(tips.max()) if len(tips) else 0
+        rec["bup_wedges"] = st["wedges"]
+        ss = su if side == 0 else sv
+        rec["sample_tips"] = {int(x): int(tips[x]) for x in ss}
+        rec["oracle_seconds"] = {"count": st["seconds_count"], "peel": st["seconds_peel"]}
+    rec["oracle_threads"] = oracle.num_threads()
+    rec["wall_seconds"] = time.time() - t0
+    with open(os.path.join(HERE, f"cfg{cfg}.json"), "w") as f:
+        json.dump(rec, f, indent=1, sort_keys=True)
+    print(json.dumps({k: rec[k] for k in rec if not k.startswith("sample")}))
+
+
+if __name__ == "__main__":
+    for a in sys.argv[1:]:
+        make(int(a))

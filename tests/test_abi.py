@@ -1,0 +1,67 @@
+"""CPU-side checks of the boundary: the library builds for sm_103a, loads,
+and exports every entry point declared in include/*.h (no compute calls)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(receipt_[a-z_0-9]+)\s*\(", src))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2010_08695_gb300 import _build
+    path = _build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for f in ("receipt_build_csr", "receipt_count_butterflies", "receipt_tip_decompose",
+              "receipt_decompose_batch", "receipt_get_stats", "receipt_last_error",
+              "receipt_graph_destroy", "receipt_tip_decompose_host"):
+        assert f in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in sorted(_declared()):
+        assert hasattr(lib, name), name
+
+
+def test_symbols_are_c_linkage(lib):
+    from paper_2010_08695_gb300 import _build
+    out = subprocess.run(["nm", "-D", "--defined-only", _build.LIB], capture_output=True,
+                         text=True).stdout
+    exported = set(re.findall(r"\bT (receipt_\w+)", out))
+    assert _declared() <= exported
+
+
+def test_options_default_and_last_error_without_gpu(lib):
+    import paper_2010_08695_gb300 as R
+    o = R.Options()
+    lib.receipt_options_default(ctypes.byref(o))
+    assert o.P == 150 and o.n_bounds == 0 and o.timing == 0
+    lib.receipt_last_error.restype = ctypes.c_char_p
+    assert isinstance(lib.receipt_last_error(), bytes)
+
+
+def test_null_arguments_are_rejected_without_gpu(lib):
+    import paper_2010_08695_gb300 as R
+    R.load()
+    # null output handle / null graph: validated before any CUDA call
+    assert lib.receipt_build_csr(None, None, 0, 1, 1, 1, None, None) == 1
+    assert lib.receipt_get_stats(None, None) == 1
+    assert lib.receipt_graph_info(None, None, None, None) == 1
+    assert lib.receipt_graph_destroy(None) == 0

@@ -1,0 +1,228 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle: butterfly
+counts and tip numbers must match bit for bit, on seeded synthetic graphs
+that exercise every aggregation tier (warp table, shared-memory hybrid,
+global dense counters), both sides, empty and degenerate inputs, and the
+theorems the method rests on (Theorem 2: any ranges give the same tip
+numbers; Theorem 1: every vertex's tip number lies in its subset's range)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def R():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2010_08695_gb300 as R
+    R.load()
+    return R
+
+
+def _gpu_counts(R, eu, ev, nu, nv):
+    g = R.Graph(eu, ev, nu, nv)
+    cu, cv = g.count_butterflies()
+    return R.as_u64(cu), R.as_u64(cv)
+
+
+def _gpu_tips(R, eu, ev, nu, nv, side, **kw):
+    g = R.Graph(eu, ev, nu, nv)
+    t = g.tip_decompose(side, **kw)
+    return R.as_u64(t), g
+
+
+def _check_graph(R, eu, ev, nu, nv, sides=(0, 1)):
+    cu, cv = oracle.count_2hop(eu, ev, nu, nv)
+    gu, gv = _gpu_counts(R, eu, ev, nu, nv)
+    assert np.array_equal(gu, cu), "U counts differ"
+    assert np.array_equal(gv, cv), "V counts differ"
+    for side in sides:
+        want, _ = oracle.bup(eu, ev, nu, nv, side)
+        got, _ = _gpu_tips(R, eu, ev, nu, nv, side)
+        bad = np.nonzero(got != want)[0]
+        assert len(bad) == 0, f"side {side}: {len(bad)} tips differ, e.g. {bad[:5]} " \
+                              f"got {got[bad[:5]]} want {want[bad[:5]]}"
+
+
+def test_tiny_random_graphs(R):
+    rng = np.random.default_rng(101)
+    for _ in range(40):
+        nu, nv = int(rng.integers(1, 30)), int(rng.integers(1, 30))
+        eu, ev = synth.random_small(nu, nv, float(rng.uniform(0.1, 0.9)), int(rng.integers(1 << 30)))
+        _check_graph(R, eu, ev, nu, nv)
+
+
+def test_config1_er(R):
+    eu, ev, nu, nv, side = synth.config_graph(1)
+    gold = json.load(open(os.path.join(HERE, "golden", "cfg1.json")))
+    assert synth.edges_sha256(eu, ev) == gold["edges_sha256"]
+    _check_graph(R, eu, ev, nu, nv)
+
+
+@pytest.mark.parametrize("seed,nu,nv,m,gu,gv", [
+    (11, 30000, 6000, 200000, 2.5, 2.1),
+    (12, 5000, 20000, 150000, 2.1, 2.6),
+    (13, 60000, 2000, 300000, 2.3, 2.0),
+])
+def test_chung_lu_medium(R, seed, nu, nv, m, gu, gv):
+    eu, ev = synth.chung_lu(nu, nv, m, gu, gv, seed)
+    _check_graph(R, eu, ev, nu, nv)
+
+
+def test_repeat_table_overflow_path(R):
+    # every U vertex has ~10 neighbours among 200 V vertices of degree ~2000:
+    # thousands of repeated end points per anchor, beyond the shared table
+    eu, ev = synth.er(40000, 200, 400000, seed=21)
+    _check_graph(R, eu, ev, 40000, 200, sides=(0,))
+
+
+def test_hub_with_degree_above_16_bits(R):
+    rng = np.random.default_rng(22)
+    nu, nv = 80000, 50
+    eu = [np.arange(70000, dtype=np.int32)]
+    ev = [np.zeros(70000, np.int32)]
+    for v in range(1, nv):
+        us = rng.choice(nu, 1200, replace=False).astype(np.int32)
+        eu.append(us)
+        ev.append(np.full(len(us), v, np.int32))
+    eu, ev = np.concatenate(eu), np.concatenate(ev)
+    _check_graph(R, eu, ev, nu, nv, sides=(1,))
+
+
+def test_complete_bipartite_and_degenerate(R):
+    for a, b in [(1, 1), (2, 2), (9, 7), (64, 33), (300, 5)]:
+        eu, ev = synth.complete_bipartite(a, b)
+        t, _ = _gpu_tips(R, eu, ev, a, b, 0)
+        assert (t == (a - 1) * (b * (b - 1) // 2)).all()
+        t, _ = _gpu_tips(R, eu, ev, a, b, 1)
+        assert (t == (b - 1) * (a * (a - 1) // 2)).all()
+    # empty graph, isolated vertices, single edge, empty side
+    e = np.zeros(0, np.int32)
+    t, _ = _gpu_tips(R, e, e, 5, 3, 0)
+    assert (t == 0).all() and len(t) == 5
+    t, _ = _gpu_tips(R, e, e, 0, 3, 0)
+    assert len(t) == 0
+    t, _ = _gpu_tips(R, np.array([2], np.int32), np.array([1], np.int32), 4, 3, 1)
+    assert (t == 0).all()
+    # a star and a hub adjacent to everything
+    eu = np.zeros(100, np.int32)
+    ev = np.arange(100, dtype=np.int32)
+    _check_graph(R, eu, ev, 1, 100)
+    eu, ev = synth.er(300, 40, 2000, seed=5)
+    eu = np.concatenate([eu, np.full(300, 0, np.int32)])
+    ev = np.concatenate([ev, np.arange(300, dtype=np.int32) % 40])
+    eu, ev = np.concatenate([eu, np.arange(300, dtype=np.int32)]), \
+        np.concatenate([ev, np.full(300, 39, np.int32)])
+    _check_graph(R, eu, ev, 300, 40)
+
+
+def test_equal_degrees_regular(R):
+    # 2-regular cycle-like bipartite graph and a 3-regular circulant
+    n = 500
+    u = np.arange(n, dtype=np.int32)
+    for k in (2, 3):
+        eu = np.concatenate([u] * k)
+        ev = np.concatenate([(u + j) % n for j in range(k)]).astype(np.int32)
+        _check_graph(R, eu, ev, n, n)
+
+
+def test_duplicates_and_errors(R):
+    eu = np.array([0, 0, 1, 1, 0, 1], np.int32)
+    ev = np.array([0, 1, 0, 1, 0, 1], np.int32)
+    t, g = _gpu_tips(R, eu, ev, 3, 2, 0)
+    assert t.tolist() == [1, 1, 0] and g.m == 4
+    with pytest.raises(R.ReceiptError) as ei:
+        R.Graph(eu, ev, 3, 2, dedup=False)
+    assert ei.value.status == 1
+    with pytest.raises(R.ReceiptError) as ei:
+        R.Graph(np.array([3], np.int32), np.array([0], np.int32), 3, 2)
+    assert ei.value.status == 1
+    g = R.Graph(eu, ev, 3, 2)
+    with pytest.raises(R.ReceiptError):
+        g.tip_decompose(side=2)
+
+
+def test_any_P_and_injected_ranges_give_same_tips(R):
+    eu, ev = synth.chung_lu(20000, 4000, 120000, 2.4, 2.2, seed=31)
+    want, _ = oracle.bup(eu, ev, 20000, 4000, 0)
+    g = R.Graph(eu, ev, 20000, 4000)
+    for P in (1, 2, 7, 150, 600):
+        t, sub, bounds = g.tip_decompose(0, P=P, subsets=True)
+        t = R.as_u64(t)
+        assert np.array_equal(t, want), f"P={P}"
+        sub = sub.cpu().numpy()
+        # Theorem 1: theta(i) <= tip < theta(i+1) for every vertex of U_i
+        lo = bounds[sub]
+        hi = bounds[sub + 1]
+        assert (lo <= t).all() and (t < hi).all(), f"P={P}"
+    rng = np.random.default_rng(3)
+    top = int(want.max()) + 2
+    for trial in range(4):
+        k = int(rng.integers(1, 12))
+        b = np.unique(rng.integers(1, top, size=k)).astype(np.uint64)
+        t, sub, bounds = g.tip_decompose(0, P=len(b), bounds=b, subsets=True)
+        assert np.array_equal(R.as_u64(t), want), f"bounds {b}"
+
+
+def test_batch_equals_alone(R):
+    specs = synth.batch_specs(24, seed=4)
+    graphs, sides, wants = [], [], []
+    for i, s in enumerate(specs):
+        eu, ev = synth.graph_from_spec(s)
+        side = i % 2
+        graphs.append(R.Graph(eu, ev, s.nu, s.nv))
+        sides.append(side)
+        wants.append(oracle.bup(eu, ev, s.nu, s.nv, side)[0])
+    outs = R.receipt_decompose_batch(graphs, sides)
+    for i, (o, w) in enumerate(zip(outs, wants)):
+        assert np.array_equal(R.as_u64(o), w), f"graph {i}"
+        alone = R.as_u64(graphs[i].tip_decompose(sides[i]))
+        assert np.array_equal(alone, w)
+
+
+def test_host_buffer_entry(R):
+    eu, ev, nu, nv, side = synth.config_graph(1)
+    got = R.receipt_tip_decompose_host(eu, ev, nu, nv, 0)
+    want, _ = oracle.bup(eu, ev, nu, nv, 0)
+    assert np.array_equal(got, want)
+
+
+def test_stats_are_reported(R):
+    eu, ev, nu, nv, side = synth.config_graph(1)
+    g = R.Graph(eu, ev, nu, nv)
+    g.tip_decompose(0, timing=True)
+    st = g.stats()
+    assert st["p_eff"] >= 1 and st["rounds_cd"] >= 1 and st["wedges_count"] > 0
+    assert st["ms_total"] > 0
+
+
+def test_config2_golden(R):
+    path = os.path.join(HERE, "golden", "cfg2.json")
+    if not os.path.exists(path):
+        pytest.skip("golden digests of the 10M-edge workload not generated")
+    gold = json.load(open(path))
+    eu, ev, nu, nv, side = synth.config_graph(2)
+    assert synth.edges_sha256(eu, ev) == gold["edges_sha256"], "generator drew a different graph"
+    import hashlib
+    g = R.Graph(eu, ev, nu, nv)
+    cu, cv = g.count_butterflies()
+    cu, cv = R.as_u64(cu), R.as_u64(cv)
+    for k, v in gold["sample_u"].items():
+        assert int(cu[int(k)]) == v
+    for k, v in gold["sample_v"].items():
+        assert int(cv[int(k)]) == v
+    assert hashlib.sha256(cu.astype("<u8").tobytes()).hexdigest() == gold["count_u_sha256"]
+    assert hashlib.sha256(cv.astype("<u8").tobytes()).hexdigest() == gold["count_v_sha256"]
+    t = R.as_u64(g.tip_decompose(side))
+    for k, v in gold["sample_tips"].items():
+        assert int(t[int(k)]) == v, f"vertex {k}"
+    assert hashlib.sha256(t.astype("<u8").tobytes()).hexdigest() == gold["tips_sha256"]
