@@ -94,6 +94,16 @@ typedef struct {
     int32_t p_eff;           /* subsets actually created                     */
     int32_t reserved;
     float ms_csr, ms_count, ms_cd, ms_fd, ms_total; /* only if timing != 0   */
+    /* Batched peel update of the coarse-grained step, per aggregation tier
+     * (0 = warp table, 1 = shared-memory hybrid, 2 = global dense counters):
+     * wedges walked, middle vertices (edge visits), anchors (peeled vertices
+     * with updates), kernel launches and device time (only if timing != 0). */
+    uint64_t peel_wedges[3];
+    uint64_t peel_mids[3];
+    uint64_t peel_anchors[3];
+    int64_t peel_launches[3];
+    float ms_peel[3];
+    float reserved2;
 } receipt_stats;
 
 /* Fills `opt` with the defaults (P = 150, nothing optional). */
@@ -173,6 +183,9 @@ receipt_status receipt_get_stats(const receipt_graph *g, receipt_stats *out);
 
 /* Thread-local text of the last error on the calling thread ("" if none). */
 const char *receipt_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process. */
+uint64_t receipt_kernel_launches(void);
 
 #ifdef __cplusplus
 }

@@ -70,6 +70,9 @@ def _load():
         lib.oracle_bup.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, i32p, i32p,
                                    ctypes.c_int, u64p, ctypes.c_uint64,
                                    ctypes.POINTER(BupStats)]
+        lib.oracle_bup_from_counts.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                               i32p, i32p, ctypes.c_int, u64p, u64p,
+                                               ctypes.c_uint64, ctypes.POINTER(BupStats)]
         lib.oracle_num_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -132,6 +135,23 @@ def bup(eu, ev, nu, nv, side, max_wedges: int = 0):
     st = BupStats()
     _check(_load().oracle_bup(nu, nv, len(eu), eu, ev, int(side), _ptr(tips),
                               int(max_wedges), ctypes.byref(st)))
+    return tips, {"wedges": int(st.wedges), "peeled": int(st.peeled),
+                  "seconds_count": st.seconds_count, "seconds_peel": st.seconds_peel,
+                  "complete": bool(st.complete)}
+
+
+def bup_from_counts(eu, ev, nu, nv, side, sup0, max_wedges: int = 0):
+    """``bup`` started from given initial supports (the decomposed side's
+    butterfly counts, e.g. from ``count_2hop``) instead of counting them."""
+    eu, ev = _prep(eu, ev)
+    n = nu if side == 0 else nv
+    sup0 = np.ascontiguousarray(sup0, dtype=np.uint64)
+    if len(sup0) != n:
+        raise ValueError("sup0 has the wrong length")
+    tips = np.zeros(n, np.uint64)
+    st = BupStats()
+    _check(_load().oracle_bup_from_counts(nu, nv, len(eu), eu, ev, int(side), _ptr(sup0),
+                                          _ptr(tips), int(max_wedges), ctypes.byref(st)))
     return tips, {"wedges": int(st.wedges), "peeled": int(st.peeled),
                   "seconds_count": st.seconds_count, "seconds_peel": st.seconds_peel,
                   "complete": bool(st.complete)}

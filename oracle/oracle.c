@@ -428,8 +428,28 @@ static double now_s(void) {
  * `max_wedges` > 0 stops the peel once that many wedges were traversed (the
  * CPU-baseline sample); tips of unpeeled vertices are then left untouched.
  */
+static int bup_impl(int32_t nu, int32_t nv, int64_t m, const int32_t *eu, const int32_t *ev,
+                    int side, const uint64_t *sup0, uint64_t *tip, uint64_t max_wedges,
+                    oracle_bup_stats *st);
+
 int oracle_bup(int32_t nu, int32_t nv, int64_t m, const int32_t *eu, const int32_t *ev,
                int side, uint64_t *tip, uint64_t max_wedges, oracle_bup_stats *st) {
+    return bup_impl(nu, nv, m, eu, ev, side, NULL, tip, max_wedges, st);
+}
+
+/* Same peel, started from given initial supports sup0 (the butterfly counts
+ * of the decomposed side, e.g. from oracle_count_2hop) instead of counting
+ * them again; used to time bounded peel samples. */
+int oracle_bup_from_counts(int32_t nu, int32_t nv, int64_t m, const int32_t *eu,
+                           const int32_t *ev, int side, const uint64_t *sup0, uint64_t *tip,
+                           uint64_t max_wedges, oracle_bup_stats *st) {
+    if (!sup0) return ORC_EINVAL;
+    return bup_impl(nu, nv, m, eu, ev, side, sup0, tip, max_wedges, st);
+}
+
+static int bup_impl(int32_t nu, int32_t nv, int64_t m, const int32_t *eu, const int32_t *ev,
+                    int side, const uint64_t *sup0, uint64_t *tip, uint64_t max_wedges,
+                    oracle_bup_stats *st) {
     side_adj U, V;
     int rc = build_both(nu, nv, m, eu, ev, &U, &V);
     if (rc) return rc;
@@ -448,7 +468,10 @@ int oracle_bup(int32_t nu, int32_t nv, int64_t m, const int32_t *eu, const int32
         goto done;
     }
     double t0 = now_s();
-    rc = count_side_2hop(S, O, sup); /* initial supports: butterflies of x in G */
+    if (sup0)
+        memcpy(sup, sup0, sizeof(uint64_t) * (size_t)n);
+    else
+        rc = count_side_2hop(S, O, sup); /* initial supports: butterflies of x in G */
     if (rc) goto done;
     double t1 = now_s();
     s.seconds_count = t1 - t0;

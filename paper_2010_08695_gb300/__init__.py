@@ -53,7 +53,10 @@ class Stats(ctypes.Structure):
                 ("rounds_cd", ctypes.c_int64), ("levels_fd", ctypes.c_int64),
                 ("p_eff", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("ms_csr", ctypes.c_float), ("ms_count", ctypes.c_float), ("ms_cd", ctypes.c_float),
-                ("ms_fd", ctypes.c_float), ("ms_total", ctypes.c_float)]
+                ("ms_fd", ctypes.c_float), ("ms_total", ctypes.c_float),
+                ("peel_wedges", ctypes.c_uint64 * 3), ("peel_mids", ctypes.c_uint64 * 3),
+                ("peel_anchors", ctypes.c_uint64 * 3), ("peel_launches", ctypes.c_int64 * 3),
+                ("ms_peel", ctypes.c_float * 3), ("reserved2", ctypes.c_float)]
 
 
 def lib_path() -> str:
@@ -88,6 +91,7 @@ def load(build_if_missing: bool = True):
         lib.receipt_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
         lib.receipt_last_error.restype = ctypes.c_char_p
         lib.receipt_options_default.argtypes = [ctypes.POINTER(Options)]
+        lib.receipt_kernel_launches.restype = ctypes.c_uint64
         for f in ("receipt_build_csr", "receipt_graph_destroy", "receipt_graph_info",
                   "receipt_count_butterflies", "receipt_tip_decompose",
                   "receipt_decompose_batch", "receipt_tip_decompose_host", "receipt_get_stats"):
@@ -162,7 +166,18 @@ def receipt_tip_decompose(handle, side: int, tip, options=None, stream=None):
 def receipt_get_stats(handle) -> dict:
     st = Stats()
     _check(load().receipt_get_stats(handle, ctypes.byref(st)))
-    return {k: getattr(st, k) for k, _ in Stats._fields_ if k != "reserved"}
+    out = {}
+    for k, _ in Stats._fields_:
+        if k.startswith("reserved"):
+            continue
+        v = getattr(st, k)
+        out[k] = list(v) if hasattr(v, "__len__") else v
+    return out
+
+
+def receipt_kernel_launches() -> int:
+    """Kernels launched by libreceipt in this process so far."""
+    return int(load().receipt_kernel_launches())
 
 
 class Graph:

@@ -1,5 +1,7 @@
 // extern "C" entry points of libreceipt.so (declared in include/receipt.h),
 // the decomposition driver, and the batch packer.
+#include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <cstring>
 #include <mutex>
@@ -10,6 +12,9 @@
 namespace receipt {
 
 static thread_local std::string g_last_error;
+static std::atomic<uint64_t> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_last_error(const std::string &msg) { g_last_error = msg; }
 
@@ -69,6 +74,17 @@ __global__ void k_scatter_i32(const int32_t *__restrict__ v, const int32_t *__re
     if (x < n) out[new2old[x]] = v[x];
 }
 
+// sum over the other side of d(d - 1): wedges bottom-up peeling walks
+__global__ void k_bup_wedges(const int64_t *__restrict__ off, int32_t n, unsigned long long *out) {
+    unsigned long long acc = 0;
+    for (int32_t y = blockIdx.x * blockDim.x + threadIdx.x; y < n; y += gridDim.x * blockDim.x) {
+        unsigned long long d = (unsigned long long)(off[y + 1] - off[y]);
+        acc += d * (d ? d - 1 : 0);
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
+}
+
 struct Timer {
     bool on;
     cudaStream_t s;
@@ -121,8 +137,18 @@ void tip_decompose_impl(receipt_graph *g, int side, uint64_t *d_tip, const recei
     D.O = &g->side[1 - side];
     D.n = n;
     D.m = g->m;
+    D.timing = opt.timing != 0;
     DevBuf<unsigned long long> cu(g->nu, s), cv(g->nv, s), init(n, s), wfull(n, s);
     DevBuf<int32_t> sub(n, s);
+    DevBuf<unsigned long long> wbup(1, s);
+    wbup.zero();
+    if (D.O->n > 0) {
+        k_bup_wedges<<<std::min(ceil_div(D.O->n, 256), 1024), 256, 0, s>>>(D.O->off, D.O->n,
+                                                                           wbup.get());
+        RC_LAUNCH();
+    }
+    unsigned long long h_wbup = 0;
+    RC_CUDA(cudaMemcpyAsync(&h_wbup, wbup.get(), 8, cudaMemcpyDeviceToHost, s));
     uint64_t wc = count_local(g, cu.get(), cv.get(), s);
     T.mark();
     D.sup = side ? cv.get() : cu.get();
@@ -146,11 +172,19 @@ void tip_decompose_impl(receipt_graph *g, int side, uint64_t *d_tip, const recei
     receipt_stats &st = g->stats;
     st = receipt_stats{};
     st.wedges_count = wc;
+    st.wedges_bup = h_wbup;
     st.wedges_cd = D.wedges_cd;
     st.wedges_fd = D.wedges_fd;
     st.rounds_cd = D.rounds;
     st.levels_fd = D.levels;
     st.p_eff = D.p_eff;
+    for (int t = 0; t < 3; t++) {
+        st.peel_wedges[t] = D.tier_wedges[t];
+        st.peel_mids[t] = D.tier_mids[t];
+        st.peel_anchors[t] = D.tier_anchors[t];
+        st.peel_launches[t] = D.tier_launches[t];
+        st.ms_peel[t] = D.tier_ms[t];
+    }
     if (opt.timing) {
         st.ms_count = T.ms(0, 1);
         st.ms_cd = T.ms(1, 2);
@@ -461,5 +495,7 @@ receipt_status receipt_get_stats(const receipt_graph *g, receipt_stats *out) {
 }
 
 const char *receipt_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t receipt_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 }  // extern "C"

@@ -56,6 +56,7 @@ struct CdDev {
     unsigned long long wrem_prev;
     double tgt_prev;
     unsigned long long wedges;
+    unsigned long long tier_w[3], tier_m[3], tier_a[3];  // per-tier wedges, mids, anchors
     unsigned long long hist_w[NBUCKET];
     uint32_t hist_c[NBUCKET];
 };
@@ -294,6 +295,7 @@ __global__ void __launch_bounds__(256) k_cd_update_warp(PeelArgs a) {
     __syncwarp();
     const int32_t n = a.st->nLw;
     CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext};
+    unsigned long long cw = 0, cm = 0, ca = 0;
     for (;;) {
         int idx = 0;
         if (lane == 0) idx = atomicAdd(&a.st->work[0], 1);
@@ -301,6 +303,8 @@ __global__ void __launch_bounds__(256) k_cd_update_warp(PeelArgs a) {
         if (idx >= n) break;
         const int32_t x = a.Lw[idx];
         const int64_t q0 = a.off_s[x], q1 = a.off_s[x + 1];
+        cm += (unsigned long long)(q1 - q0);
+        ca++;
         for (int64_t qb = q0; qb < q1; qb += 32) {
             int64_t q = qb + lane;
             int64_t beg = 0;
@@ -314,6 +318,7 @@ __global__ void __launch_bounds__(256) k_cd_update_warp(PeelArgs a) {
             for (int t = 0; t < cnt; t++) {
                 int64_t b = __shfl_sync(0xffffffffu, beg, t);
                 int32_t l = __shfl_sync(0xffffffffu, len, t);
+                cw += (unsigned long long)l;
                 for (int p = lane; p < l; p += 32) {
                     int32_t k = a.adj_o[b + p];
                     if (k != x) H.add(k);
@@ -331,6 +336,11 @@ __global__ void __launch_bounds__(256) k_cd_update_warp(PeelArgs a) {
             }
         }
         __syncwarp();
+    }
+    if (lane == 0 && ca) {
+        atomicAdd(&a.st->tier_w[0], cw);
+        atomicAdd(&a.st->tier_m[0], cm);
+        atomicAdd(&a.st->tier_a[0], ca);
     }
 }
 
@@ -367,6 +377,7 @@ __global__ void __launch_bounds__(CTA_THREADS) k_cd_update_cta(PeelArgs a, int32
     const int32_t n = a.st->nLc;
     CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext};
     PeelMids M{a.adj_s, a.off_o};
+    unsigned long long cw = 0, cm = 0, ca = 0;
     for (;;) {
         if (threadIdx.x == 0) s_idx = atomicAdd(&a.st->work[1], 1);
         __syncthreads();
@@ -374,7 +385,9 @@ __global__ void __launch_bounds__(CTA_THREADS) k_cd_update_cta(PeelArgs a, int32
         if (idx >= n) break;
         const int32_t x = a.Lc[idx];
         PeelVisit<CtaHybrid> v{&H, x};
-        cta_walk(M, a.off_s[x], a.off_s[x + 1], a.adj_o, ch, v);
+        cw += cta_walk(M, a.off_s[x], a.off_s[x + 1], a.adj_o, ch, v);
+        cm += (unsigned long long)(a.off_s[x + 1] - a.off_s[x]);
+        ca++;
         if (!s_over)
             H.flush(emit);
         else if (threadIdx.x == 0)
@@ -382,6 +395,11 @@ __global__ void __launch_bounds__(CTA_THREADS) k_cd_update_cta(PeelArgs a, int32
         __syncthreads();
         H.clear_active();
         __syncthreads();
+    }
+    if (threadIdx.x == 0 && ca) {
+        atomicAdd(&a.st->tier_w[1], cw);
+        atomicAdd(&a.st->tier_m[1], cm);
+        atomicAdd(&a.st->tier_a[1], ca);
     }
 }
 
@@ -397,6 +415,7 @@ __global__ void __launch_bounds__(CTA_THREADS) k_cd_update_global(PeelArgs a, ui
     const int32_t n1 = a.st->nLg, n2 = a.st->nLo;
     CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext};
     PeelMids M{a.adj_s, a.off_o};
+    unsigned long long cw = 0, cm = 0, ca = 0;
     for (;;) {
         if (threadIdx.x == 0) {
             s_idx = atomicAdd(&a.st->work[2], 1);
@@ -407,11 +426,18 @@ __global__ void __launch_bounds__(CTA_THREADS) k_cd_update_global(PeelArgs a, ui
         if (idx >= n1 + n2) break;
         const int32_t x = idx < n1 ? a.Lg[idx] : a.Lo[idx - n1];
         PeelVisit<GlobalDense> v{&G, x};
-        cta_walk(M, a.off_s[x], a.off_s[x + 1], a.adj_o, ch, v);
+        cw += cta_walk(M, a.off_s[x], a.off_s[x + 1], a.adj_o, ch, v);
+        cm += (unsigned long long)(a.off_s[x + 1] - a.off_s[x]);
+        ca++;
         G.flush(emit);
         __syncthreads();
         G.clear();
         __syncthreads();
+    }
+    if (threadIdx.x == 0 && ca) {
+        atomicAdd(&a.st->tier_w[2], cw);
+        atomicAdd(&a.st->tier_m[2], cm);
+        atomicAdd(&a.st->tier_a[2], ca);
     }
 }
 
@@ -501,11 +527,20 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
     } pg{hpin};
     int32_t *hi32 = reinterpret_cast<int32_t *>(hpin);
 
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    struct EvGuard {
+        cudaEvent_t *e;
+        ~EvGuard() {
+            for (int i = 0; i < 4; i++)
+                if (e[i]) cudaEventDestroy(e[i]);
+        }
+    } eg{ev};
+    if (D.timing)
+        for (int i = 0; i < 4; i++) RC_CUDA(cudaEventCreate(&ev[i]));
     k_init_state<<<ceil_div(n, 256), 256, 0, s>>>(D.sub, n);
     RC_LAUNCH();
     const int nb = std::min(ceil_div(n, 512), sms * 4);
     int range = 0;
-    uint64_t lo = 0;
     const int nranges = opt.n_bounds > 0 ? std::min(opt.n_bounds, P) : P;
     int32_t *cur = F.get(), *nxt = Nx.get();
     for (range = 0; range < nranges; range++) {
@@ -533,24 +568,37 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
             RC_LAUNCH();
             PeelArgs a{S.off, S.adj, O.off, O.adj, D.sup, D.sub, st.get(),
                        Lw.get(), Lc.get(), Lg.get(), Lo.get(), nxt};
+            if (D.timing) RC_CUDA(cudaEventRecord(ev[0], s));
             k_cd_update_warp<<<sms * 8, 256, 0, s>>>(a);
             RC_LAUNCH();
+            if (D.timing) RC_CUDA(cudaEventRecord(ev[1], s));
             if (cta_ok) {
                 k_cd_update_cta<<<sms, CTA_THREADS, smem_cta, s>>>(a, headn, bmw, n);
                 RC_LAUNCH();
+                D.tier_launches[1]++;
             }
+            if (D.timing) RC_CUDA(cudaEventRecord(ev[2], s));
             k_cd_update_global<<<gblocks, CTA_THREADS, smem_glob, s>>>(a, gcnt.get(), gtouch.get(),
                                                                       n);
             RC_LAUNCH();
+            if (D.timing) RC_CUDA(cudaEventRecord(ev[3], s));
+            D.tier_launches[0]++;
+            D.tier_launches[2]++;
             D.rounds++;
             RC_CUDA(cudaMemcpyAsync(hi32 + 4, &st.get()->nNext, 4, cudaMemcpyDeviceToHost, s));
             RC_CUDA(cudaStreamSynchronize(s));
+            if (D.timing) {
+                for (int t = 0; t < 3; t++) {
+                    float ms = 0;
+                    RC_CUDA(cudaEventElapsedTime(&ms, ev[t], ev[t + 1]));
+                    D.tier_ms[t] += ms;
+                }
+            }
             if (hi32[4] == 0) break;
             k_cd_advance<<<1, 1, 0, s>>>(st.get());
             RC_LAUNCH();
             std::swap(cur, nxt);
         }
-        lo = hi;
         D.bounds.push_back(hi);
     }
     // leftover subset with an open range
@@ -560,13 +608,18 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
     RC_LAUNCH();
     int hany = 0;
     RC_CUDA(cudaMemcpyAsync(&hany, any.get(), 4, cudaMemcpyDeviceToHost, s));
-    unsigned long long hw = 0;
+    unsigned long long hw = 0, ht[9];
     RC_CUDA(cudaMemcpyAsync(&hw, &st.get()->wedges, 8, cudaMemcpyDeviceToHost, s));
+    RC_CUDA(cudaMemcpyAsync(ht, st.get()->tier_w, sizeof(ht), cudaMemcpyDeviceToHost, s));
     RC_CUDA(cudaStreamSynchronize(s));
     D.p_eff = range + (hany ? 1 : 0);
     if (hany) D.bounds.push_back(~0ull);
     D.wedges_cd = hw;
-    (void)lo;
+    for (int t = 0; t < 3; t++) {
+        D.tier_wedges[t] = ht[t];
+        D.tier_mids[t] = ht[3 + t];
+        D.tier_anchors[t] = ht[6 + t];
+    }
 }
 
 // wfull for side s

@@ -24,7 +24,12 @@ void check_cuda(cudaError_t e, const char *what, const char *file, int line);
 void set_last_error(const std::string &msg);
 
 #define RC_CUDA(call) ::receipt::check_cuda((call), #call, __FILE__, __LINE__)
-#define RC_LAUNCH() ::receipt::check_cuda(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
+void count_launch();
+#define RC_LAUNCH()                                                                  \
+    do {                                                                             \
+        ::receipt::check_cuda(cudaGetLastError(), "kernel launch", __FILE__, __LINE__); \
+        ::receipt::count_launch();                                                   \
+    } while (0)
 
 int num_sms();
 int max_smem_optin();

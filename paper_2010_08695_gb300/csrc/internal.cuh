@@ -42,6 +42,10 @@ struct Decomp {
     std::vector<uint64_t> bounds;         // theta(1..p_eff+1)
     uint64_t wedges_cd = 0, wedges_fd = 0;
     int64_t rounds = 0, levels = 0;
+    bool timing = false;
+    uint64_t tier_wedges[3] = {0, 0, 0}, tier_mids[3] = {0, 0, 0}, tier_anchors[3] = {0, 0, 0};
+    int64_t tier_launches[3] = {0, 0, 0};
+    float tier_ms[3] = {0, 0, 0};
 };
 
 void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s);

@@ -174,3 +174,12 @@ def test_bounded_peel_sample():
     part, st = oracle.bup(eu, ev, nu, nv, 0, max_wedges=st_full["wedges"] // 3)
     assert not st["complete"] and 0 < st["peeled"] < nu
     assert st["wedges"] >= st_full["wedges"] // 3
+
+
+def test_peel_from_given_counts_equals_full_bup():
+    eu, ev = synth.chung_lu(3000, 700, 25000, 2.3, 2.2, seed=17)
+    for side in (0, 1):
+        full, _ = oracle.bup(eu, ev, 3000, 700, side)
+        c = oracle.count_2hop(eu, ev, 3000, 700)[side]
+        again, st = oracle.bup_from_counts(eu, ev, 3000, 700, side, c)
+        assert st["complete"] and (again == full).all()
