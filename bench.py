@@ -207,10 +207,14 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    last_trace = []
+
     def step(timing):
         g = R.Graph(eu_d, ev_d, nu, nv, stream=stream)
         g.tip_decompose(side, timing=timing, out=tip, stream=stream)
         st = g.stats()
+        if args.trace:
+            last_trace[:] = g.trace()
         g.close()
         return st
 
@@ -232,6 +236,9 @@ def run_ours(args):
             times.append(e0.elapsed_time(e1))
         barrier()
     launches = R.receipt_kernel_launches() - launches0
+    if args.trace and rank == 0:
+        with open(args.trace, "w") as f:
+            json.dump(last_trace, f)
     ms = statistics.mean(times)
     if dist is not None:
         t = torch.tensor([ms], device=dev)
@@ -266,8 +273,8 @@ def run_ours(args):
 
     # roofline of the dominant peel kernel (tier with the most device time)
     st = stats[-1]
-    names = ["k_cd_update_warp", "k_cd_update_cta", "k_cd_update_global"]
-    tier = max(range(3), key=lambda t: st["ms_peel"][t])
+    names = ["k_cd_update_warp", "k_cd_update_cta", "k_cd_update_global", "k_cd_update_slice"]
+    tier = max(range(4), key=lambda t: st["ms_peel"][t])
     lau = max(1, st["peel_launches"][tier])
     alg_bytes = (4 * st["peel_wedges"][tier] + 16 * st["peel_mids"][tier]
                  + 24 * st["peel_anchors"][tier]) / lau
@@ -298,6 +305,9 @@ def run_ours(args):
             "phase_ms": {"count": st["ms_count"], "cd": st["ms_cd"], "fd": st["ms_fd"],
                          "peel_tiers": st["ms_peel"]},
             "rounds_cd": st["rounds_cd"], "levels_fd": st["levels_fd"], "subsets": st["p_eff"],
+            "fd_slowest_subset": {"ms": st["ms_fd_max_subset"], "n": st["fd_max_subset_n"],
+                                  "levels": st["fd_max_subset_levels"]},
+            "peel_tier_wedges": st["peel_wedges"], "peel_tier_anchors": st["peel_anchors"],
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": names[tier],
                          "peak_source": peak_kind,
@@ -325,6 +335,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--trace", default=None,
+                    help="write the per-round trace of the last timed step to this JSON file")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -80,6 +80,12 @@ typedef struct {
     int32_t *h_p_eff;
     /* Non-zero: record per-phase CUDA-event timings in the graph's stats. */
     int32_t timing;
+    /* Tier thresholds of the peel update (0 = built-in defaults): anchors
+     * with at most warp_max_w wedges (<= 256) use one warp each; anchors with
+     * more than slice_min_w wedges aggregate key slice by key slice. They
+     * change speed only, never results. */
+    int32_t warp_max_w;
+    int32_t slice_min_w;
 } receipt_options;
 
 /* Counters of the last call on a graph (Sec. 5: wedges and rounds). */
@@ -95,16 +101,30 @@ typedef struct {
     int32_t reserved;
     float ms_csr, ms_count, ms_cd, ms_fd, ms_total; /* only if timing != 0   */
     /* Batched peel update of the coarse-grained step, per aggregation tier
-     * (0 = warp table, 1 = shared-memory hybrid, 2 = global dense counters):
+     * (0 = warp table, 1 = shared-memory hybrid over the whole side,
+     * 2 = global dense counters for hubs, 3 = hybrid over key slices):
      * wedges walked, middle vertices (edge visits), anchors (peeled vertices
      * with updates), kernel launches and device time (only if timing != 0). */
-    uint64_t peel_wedges[3];
-    uint64_t peel_mids[3];
-    uint64_t peel_anchors[3];
-    int64_t peel_launches[3];
-    float ms_peel[3];
-    float reserved2;
+    uint64_t peel_wedges[4];
+    uint64_t peel_mids[4];
+    uint64_t peel_anchors[4];
+    int64_t peel_launches[4];
+    float ms_peel[4];
+    /* Slowest subset of the fine-grained step: device time, size, levels. */
+    float ms_fd_max_subset;
+    int32_t fd_max_subset_n;
+    int64_t fd_max_subset_levels;
 } receipt_stats;
+
+/* One synchronisation round of the coarse-grained step (Algorithm 3). */
+typedef struct {
+    int32_t range;        /* 0-based subset index the round belongs to        */
+    int32_t frontier;     /* activeSet size (vertices peeled this round)      */
+    uint64_t hi;          /* upper bound theta(range + 2) of the range        */
+    uint64_t anchors[4];  /* peeled vertices with updates, per peel tier      */
+    uint64_t wedges[4];   /* wedges walked, per peel tier                     */
+    float ms[4];          /* device time per peel tier (only if timing != 0)  */
+} receipt_round;
 
 /* Fills `opt` with the defaults (P = 150, nothing optional). */
 void receipt_options_default(receipt_options *opt);
@@ -180,6 +200,11 @@ receipt_status receipt_tip_decompose_host(const int32_t *h_eu, const int32_t *h_
 
 /* Counters of the last count/decompose call on g. */
 receipt_status receipt_get_stats(const receipt_graph *g, receipt_stats *out);
+
+/* Per-round trace of the last tip decomposition on g: copies up to `cap`
+ * records to `out` (host array) and the number of rounds to *n_rounds. */
+receipt_status receipt_get_trace(const receipt_graph *g, receipt_round *out, int32_t cap,
+                                 int32_t *n_rounds);
 
 /* Thread-local text of the last error on the calling thread ("" if none). */
 const char *receipt_last_error(void);

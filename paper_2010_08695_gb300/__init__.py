@@ -44,7 +44,8 @@ class Options(ctypes.Structure):
     _fields_ = [("P", ctypes.c_int32), ("h_bounds", ctypes.POINTER(ctypes.c_uint64)),
                 ("n_bounds", ctypes.c_int32), ("d_subset", ctypes.c_void_p),
                 ("h_bounds_out", ctypes.POINTER(ctypes.c_uint64)), ("h_bounds_cap", ctypes.c_int32),
-                ("h_p_eff", ctypes.POINTER(ctypes.c_int32)), ("timing", ctypes.c_int32)]
+                ("h_p_eff", ctypes.POINTER(ctypes.c_int32)), ("timing", ctypes.c_int32),
+                ("warp_max_w", ctypes.c_int32), ("slice_min_w", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -54,9 +55,16 @@ class Stats(ctypes.Structure):
                 ("p_eff", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("ms_csr", ctypes.c_float), ("ms_count", ctypes.c_float), ("ms_cd", ctypes.c_float),
                 ("ms_fd", ctypes.c_float), ("ms_total", ctypes.c_float),
-                ("peel_wedges", ctypes.c_uint64 * 3), ("peel_mids", ctypes.c_uint64 * 3),
-                ("peel_anchors", ctypes.c_uint64 * 3), ("peel_launches", ctypes.c_int64 * 3),
-                ("ms_peel", ctypes.c_float * 3), ("reserved2", ctypes.c_float)]
+                ("peel_wedges", ctypes.c_uint64 * 4), ("peel_mids", ctypes.c_uint64 * 4),
+                ("peel_anchors", ctypes.c_uint64 * 4), ("peel_launches", ctypes.c_int64 * 4),
+                ("ms_peel", ctypes.c_float * 4), ("ms_fd_max_subset", ctypes.c_float),
+                ("fd_max_subset_n", ctypes.c_int32), ("fd_max_subset_levels", ctypes.c_int64)]
+
+
+class Round(ctypes.Structure):
+    _fields_ = [("range", ctypes.c_int32), ("frontier", ctypes.c_int32), ("hi", ctypes.c_uint64),
+                ("anchors", ctypes.c_uint64 * 4), ("wedges", ctypes.c_uint64 * 4),
+                ("ms", ctypes.c_float * 4)]
 
 
 def lib_path() -> str:
@@ -92,6 +100,8 @@ def load(build_if_missing: bool = True):
         lib.receipt_last_error.restype = ctypes.c_char_p
         lib.receipt_options_default.argtypes = [ctypes.POINTER(Options)]
         lib.receipt_kernel_launches.restype = ctypes.c_uint64
+        lib.receipt_get_trace.argtypes = [vp, ctypes.POINTER(Round), i32, ctypes.POINTER(i32)]
+        lib.receipt_get_trace.restype = ctypes.c_int
         for f in ("receipt_build_csr", "receipt_graph_destroy", "receipt_graph_info",
                   "receipt_count_butterflies", "receipt_tip_decompose",
                   "receipt_decompose_batch", "receipt_tip_decompose_host", "receipt_get_stats"):
@@ -119,10 +129,13 @@ def _dptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
-def _options(P=150, bounds=None, subset=None, bounds_out=None, p_eff=None, timing=False):
+def _options(P=150, bounds=None, subset=None, bounds_out=None, p_eff=None, timing=False,
+             warp_max_w=0, slice_min_w=0):
     o = Options()
     load().receipt_options_default(ctypes.byref(o))
     o.P = int(P)
+    o.warp_max_w = int(warp_max_w)
+    o.slice_min_w = int(slice_min_w)
     keep = []
     if bounds is not None:
         b = np.ascontiguousarray(bounds, dtype=np.uint64)
@@ -175,6 +188,17 @@ def receipt_get_stats(handle) -> dict:
     return out
 
 
+def receipt_get_trace(handle) -> list:
+    """Per-round records of the last decomposition (coarse-grained step)."""
+    lib = load()
+    n = ctypes.c_int32(0)
+    _check(lib.receipt_get_trace(handle, None, 0, ctypes.byref(n)))
+    buf = (Round * max(1, n.value))()
+    _check(lib.receipt_get_trace(handle, buf, n.value, ctypes.byref(n)))
+    return [{"range": r.range, "frontier": r.frontier, "hi": r.hi, "anchors": list(r.anchors),
+             "wedges": list(r.wedges), "ms": list(r.ms)} for r in buf[: n.value]]
+
+
 def receipt_kernel_launches() -> int:
     """Kernels launched by libreceipt in this process so far."""
     return int(load().receipt_kernel_launches())
@@ -220,7 +244,7 @@ class Graph:
         return cu, cv
 
     def tip_decompose(self, side: int = SIDE_U, P: int = 150, bounds=None, subsets=False,
-                      timing=False, out=None, stream=None):
+                      timing=False, out=None, stream=None, warp_max_w=0, slice_min_w=0):
         """Tip numbers of ``side`` (Algorithms 3 and 4). With ``subsets=True``
         returns ``(tips, subset_of_vertex, range_bounds)``."""
         import torch
@@ -230,7 +254,7 @@ class Graph:
         bout = np.zeros(P + (len(bounds) if bounds is not None else 0) + 4, np.uint64) \
             if subsets else None
         peff = ctypes.c_int32(0)
-        o, keep = _options(P, bounds, sub, bout, peff, timing)
+        o, keep = _options(P, bounds, sub, bout, peff, timing, warp_max_w, slice_min_w)
         receipt_tip_decompose(self._h, side, tip, o, stream)
         if subsets:
             return tip, sub, bout[: peff.value + 1]
@@ -238,6 +262,9 @@ class Graph:
 
     def stats(self) -> dict:
         return receipt_get_stats(self._h)
+
+    def trace(self) -> list:
+        return receipt_get_trace(self._h)
 
 
 def receipt_decompose_batch(graphs, sides, outs=None, P: int = 150, stream=None):

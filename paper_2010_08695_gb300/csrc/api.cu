@@ -178,7 +178,11 @@ void tip_decompose_impl(receipt_graph *g, int side, uint64_t *d_tip, const recei
     st.rounds_cd = D.rounds;
     st.levels_fd = D.levels;
     st.p_eff = D.p_eff;
-    for (int t = 0; t < 3; t++) {
+    g->trace = std::move(D.trace);
+    st.ms_fd_max_subset = D.fd_max_ms;
+    st.fd_max_subset_n = D.fd_max_n;
+    st.fd_max_subset_levels = D.fd_max_levels;
+    for (int t = 0; t < 4; t++) {
         st.peel_wedges[t] = D.tier_wedges[t];
         st.peel_mids[t] = D.tier_mids[t];
         st.peel_anchors[t] = D.tier_anchors[t];
@@ -343,6 +347,7 @@ void decompose_batch_impl(receipt_graph *const *gs, const receipt_side *sides, i
         RC_CUDA(cudaStreamSynchronize(s));
     }
     gs[0]->stats = U.stats;
+    gs[0]->trace = std::move(U.trace);
 }
 
 }  // namespace receipt
@@ -491,6 +496,17 @@ receipt_status receipt_get_stats(const receipt_graph *g, receipt_stats *out) {
     return guarded([&] {
         if (!g || !out) fail(RECEIPT_ERR_INVALID, "null argument");
         *out = g->stats;
+    });
+}
+
+receipt_status receipt_get_trace(const receipt_graph *g, receipt_round *out, int32_t cap,
+                                 int32_t *n_rounds) {
+    return guarded([&] {
+        if (!g) fail(RECEIPT_ERR_INVALID, "null graph");
+        if (cap > 0 && !out) fail(RECEIPT_ERR_INVALID, "null output with cap > 0");
+        const int32_t n = (int32_t)g->trace.size();
+        for (int32_t i = 0; i < n && i < cap; i++) out[i] = g->trace[i];
+        if (n_rounds) *n_rounds = n;
     });
 }
 

@@ -23,6 +23,7 @@
 // A peeled vertex whose raw support is 0 shares no butterfly with any
 // remaining vertex, so its update is skipped.
 #include <algorithm>
+#include <cstddef>
 
 #include "engine.cuh"
 #include "internal.cuh"
@@ -49,14 +50,14 @@ __device__ __forceinline__ unsigned long long bucket_top(int b) {
 
 struct CdDev {
     unsigned long long hi;
-    int32_t nF, nNext, nLw, nLc, nLg, nLo;
+    int32_t nF, nNext, nLw, nLc, nLg, nLo, nLs, pad2;
     int32_t work[4];
     int32_t n_remaining;
     int32_t pad;
     unsigned long long wrem_prev;
     double tgt_prev;
     unsigned long long wedges;
-    unsigned long long tier_w[3], tier_m[3], tier_a[3];  // per-tier wedges, mids, anchors
+    unsigned long long tier_w[4], tier_m[4], tier_a[4];  // per-tier wedges, mids, anchors
     unsigned long long hist_w[NBUCKET];
     uint32_t hist_c[NBUCKET];
 };
@@ -218,7 +219,8 @@ __global__ void k_cd_prepare(const int32_t *__restrict__ F, CdDev *st, int32_t r
                              int32_t *__restrict__ sub, const unsigned long long *__restrict__ sup,
                              const unsigned long long *__restrict__ wfull,
                              const int64_t *__restrict__ off, int cta_ok, int32_t *__restrict__ Lw,
-                             int32_t *__restrict__ Lc, int32_t *__restrict__ Lg) {
+                             int32_t *__restrict__ Lc, int32_t *__restrict__ Lg,
+                             int32_t *__restrict__ Ls, int32_t warp_max_w, int32_t slice_min_w) {
     const int32_t nF = st->nF;
     unsigned long long wsum = 0;
     for (int32_t base = blockIdx.x * blockDim.x; base < nF; base += gridDim.x * blockDim.x) {
@@ -232,17 +234,20 @@ __global__ void k_cd_prepare(const int32_t *__restrict__ F, CdDev *st, int32_t r
                 unsigned long long W = wfull[x];
                 int64_t deg = off[x + 1] - off[x];
                 wsum += W;
-                if (W <= (unsigned long long)WARP_MAX_W)
+                if (W <= (unsigned long long)warp_max_w)
                     tier = 0;
-                else if (cta_ok && deg < 65535)
+                else if (deg >= 65535)
+                    tier = 2;
+                else if (cta_ok && W <= (unsigned long long)slice_min_w)
                     tier = 1;
                 else
-                    tier = 2;
+                    tier = 3;
             }
         }
         warp_append(tier == 0, x, &st->nLw, Lw);
         warp_append(tier == 1, x, &st->nLc, Lc);
         warp_append(tier == 2, x, &st->nLg, Lg);
+        warp_append(tier == 3, x, &st->nLs, Ls);
     }
     wsum = warp_sum(wsum);
     if ((threadIdx.x & 31) == 0 && wsum) atomicAdd(&st->wedges, wsum);
@@ -282,8 +287,11 @@ struct PeelArgs {
     const int32_t *sub;
     CdDev *st;
     const int32_t *Lw, *Lc, *Lg;
-    int32_t *Lo;
+    int32_t *Ls;           // sliced anchors (the hybrid tier appends its overflows)
     int32_t *next;
+    const int32_t *soff;   // per other-side vertex: C + 1 slice starts within its list
+    int32_t C;             // key slices
+    int32_t SW;            // keys per slice
 };
 
 __global__ void __launch_bounds__(256) k_cd_update_warp(PeelArgs a) {
@@ -388,13 +396,14 @@ __global__ void __launch_bounds__(CTA_THREADS) k_cd_update_cta(PeelArgs a, int32
         cw += cta_walk(M, a.off_s[x], a.off_s[x + 1], a.adj_o, ch, v);
         cm += (unsigned long long)(a.off_s[x + 1] - a.off_s[x]);
         ca++;
-        if (!s_over)
-            H.flush(emit);
-        else if (threadIdx.x == 0)
-            a.Lo[atomicAdd(&a.st->nLo, 1)] = x;
+        if (!s_over) {
+            H.flush_clear<true>(emit);
+        } else {
+            H.flush_clear<false>(emit);
+            if (threadIdx.x == 0) a.Ls[atomicAdd(&a.st->nLs, 1)] = x;
+        }
         __syncthreads();
-        H.clear_active();
-        __syncthreads();
+        H.reset_scalars();
     }
     if (threadIdx.x == 0 && ca) {
         atomicAdd(&a.st->tier_w[1], cw);
@@ -412,7 +421,7 @@ __global__ void __launch_bounds__(CTA_THREADS) k_cd_update_global(PeelArgs a, ui
     ch.pre = (int32_t *)(ch.beg + MID_CHUNK);
     ch.tmp = ch.pre + MID_CHUNK + 1;
     GlobalDense G{gcnt + (size_t)blockIdx.x * keyspace, gtouch + (size_t)blockIdx.x * keyspace, &s_nt};
-    const int32_t n1 = a.st->nLg, n2 = a.st->nLo;
+    const int32_t n1 = a.st->nLg, n2 = 0;
     CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext};
     PeelMids M{a.adj_s, a.off_o};
     unsigned long long cw = 0, cm = 0, ca = 0;
@@ -424,7 +433,7 @@ __global__ void __launch_bounds__(CTA_THREADS) k_cd_update_global(PeelArgs a, ui
         __syncthreads();
         int idx = s_idx;
         if (idx >= n1 + n2) break;
-        const int32_t x = idx < n1 ? a.Lg[idx] : a.Lo[idx - n1];
+        const int32_t x = a.Lg[idx];
         PeelVisit<GlobalDense> v{&G, x};
         cw += cta_walk(M, a.off_s[x], a.off_s[x + 1], a.adj_o, ch, v);
         cm += (unsigned long long)(a.off_s[x + 1] - a.off_s[x]);
@@ -441,17 +450,144 @@ __global__ void __launch_bounds__(CTA_THREADS) k_cd_update_global(PeelArgs a, ui
     }
 }
 
+// Segment of a middle vertex restricted to key slice j.
+struct SlicedMids {
+    const int32_t *adj_s;
+    const int64_t *off_o;
+    const int32_t *soff;
+    int32_t C1;  // C + 1
+    int32_t j;
+    __device__ __forceinline__ void seg(int64_t q, int64_t &beg, int32_t &len) const {
+        int32_t y = adj_s[q];
+        const int32_t *so = soff + (size_t)y * C1 + j;
+        int32_t b = so[0], e = so[1];
+        beg = off_o[y] + b;
+        len = e - b;
+    }
+};
+
+// Keys of slice j shifted to the slice's local key space.
+template <class Eng>
+struct SliceVisit {
+    Eng *eng;
+    int32_t self_local;  // anchor's own key in this slice's frame (or -1)
+    int32_t base;
+    __device__ __forceinline__ void operator()(int, int32_t key) {
+        int32_t k = key - base;
+        if (k != self_local) eng->add(k);
+    }
+};
+
+struct SliceEmit {
+    CdEmit *e;
+    int32_t base;
+    __device__ __forceinline__ void operator()(int32_t k, uint32_t c) { (*e)(k + base, c); }
+};
+
+// Anchors with many wedges: the key space is cut into C slices of SW keys,
+// and the CTA aggregates one slice at a time with the hybrid engine sized
+// for SW keys (dense head counters only on slice 0, where the high-degree
+// end points sit). A slice whose repeat table overflows is redone with dense
+// counters in this CTA's slot of global memory.
+__global__ void __launch_bounds__(CTA_THREADS) k_cd_update_slice(PeelArgs a, int32_t bm_words,
+                                                              int32_t n, uint32_t *gcnt,
+                                                              int32_t *gtouch) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_idx, s_used, s_over, s_nt;
+    CtaHybrid H;
+    H.head = (uint32_t *)smem;
+    H.bm = H.head + HEAD_MAX / 2;
+    H.rkey = (int32_t *)(H.bm + bm_words);
+    H.rval = (uint32_t *)(H.rkey + REPEAT_SLOTS);
+    Chunk ch;
+    ch.beg = (int64_t *)(H.rval + REPEAT_SLOTS);
+    ch.pre = (int32_t *)(ch.beg + MID_CHUNK);
+    ch.tmp = ch.pre + MID_CHUNK + 1;
+    H.s_used = &s_used;
+    H.s_over = &s_over;
+    H.headn = HEAD_MAX;
+    H.bm_words = bm_words;
+    H.clear_all();
+    GlobalDense G{gcnt + (size_t)blockIdx.x * a.SW, gtouch + (size_t)blockIdx.x * a.SW, &s_nt};
+    __syncthreads();
+    CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext};
+    unsigned long long cw = 0, cm = 0, ca = 0;
+    const int64_t items = (int64_t)a.st->nLs * a.C;
+    for (;;) {
+        if (threadIdx.x == 0) s_idx = atomicAdd(&a.st->work[3], 1);
+        __syncthreads();
+        const int64_t idx = s_idx;
+        if (idx >= items) break;
+        // work item = (anchor, key slice): the slices of one anchor go to
+        // different CTAs
+        const int32_t x = a.Ls[idx / a.C];
+        const int32_t j = (int32_t)(idx % a.C);
+        const int64_t q0 = a.off_s[x], q1 = a.off_s[x + 1];
+        if (j == 0) {
+            cm += (unsigned long long)(q1 - q0);
+            ca++;
+        }
+        const int32_t base = j * a.SW;
+        const int32_t w = (int32_t)imin64(a.SW, (int64_t)n - base);
+        int32_t hn = j == 0 ? (int32_t)imin64(HEAD_MAX, w) : (int32_t)imin64(HEAD_SLICE, w);
+        H.headn = (hn + 1) & ~1;
+        H.set_active(w);
+        SlicedMids M{a.adj_s, a.off_o, a.soff, a.C + 1, j};
+        const int32_t self = (x >= base && x < base + w) ? x - base : -1;
+        SliceVisit<CtaHybrid> v{&H, self, base};
+        int64_t walked = cta_walk(M, q0, q1, a.adj_o, ch, v);
+        cw += walked;
+        if (walked == 0) continue;
+        SliceEmit em{&emit, base};
+        const bool over = s_over;
+        if (!over)
+            H.flush_clear<true>(em);
+        else
+            H.flush_clear<false>(em);
+        __syncthreads();
+        H.reset_scalars();
+        if (over) {
+            if (threadIdx.x == 0) s_nt = 0;
+            __syncthreads();
+            SliceVisit<GlobalDense> gv{&G, self, base};
+            cta_walk(M, q0, q1, a.adj_o, ch, gv);
+            G.flush(em);
+            __syncthreads();
+            G.clear();
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) {
+        if (cw) atomicAdd(&a.st->tier_w[3], cw);
+        if (ca) {
+            atomicAdd(&a.st->tier_m[3], cm);
+            atomicAdd(&a.st->tier_a[3], ca);
+        }
+    }
+}
+
+// soff[y * (C + 1) + j] = number of entries of N_y below j * SW (j = 0..C).
+__global__ void k_slice_table(const int64_t *__restrict__ off_o, const int32_t *__restrict__ adj_o,
+                              int32_t n_o, int32_t C, int32_t SW, int32_t *__restrict__ soff) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t tot = (int64_t)n_o * (C + 1);
+    if (i >= tot) return;
+    int32_t y = (int32_t)(i / (C + 1)), j = (int32_t)(i % (C + 1));
+    int64_t b = off_o[y], e = off_o[y + 1];
+    soff[i] = j == C ? (int32_t)(e - b) : (int32_t)lower_bound_i32(adj_o + b, e - b, j * SW);
+}
+
 // Next round: the vertices that crossed below hi become the activeSet.
 __global__ void k_cd_advance(CdDev *st) {
     st->nF = st->nNext;
     st->nNext = 0;
-    st->nLw = st->nLc = st->nLg = st->nLo = 0;
+    st->nLw = st->nLc = st->nLg = st->nLo = st->nLs = 0;
     st->work[0] = st->work[1] = st->work[2] = st->work[3] = 0;
 }
 
 __global__ void k_cd_new_range(CdDev *st) {
     st->nF = st->nNext = 0;
-    st->nLw = st->nLc = st->nLg = st->nLo = 0;
+    st->nLw = st->nLc = st->nLg = st->nLo = st->nLs = 0;
     st->work[0] = st->work[1] = st->work[2] = st->work[3] = 0;
     for (int b = 0; b < NBUCKET; b++) {
         st->hist_w[b] = 0;
@@ -503,7 +639,31 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
     }
     DevBuf<CdDev> st(1, s);
     st.zero();
-    DevBuf<int32_t> F(n, s), Nx(n, s), Lw(n, s), Lc(n, s), Lg(n, s), Lo(n, s);
+    DevBuf<int32_t> F(n, s), Nx(n, s), Lw(n, s), Lc(n, s), Lg(n, s), Ls(n, s);
+    const int32_t warp_max_w =
+        opt.warp_max_w > 0 ? std::min(opt.warp_max_w, WARP_MAX_W) : WARP_MAX_W;
+    const int32_t slice_min_w = opt.slice_min_w > 0 ? opt.slice_min_w : SLICE_MIN_W;
+    // key slices for anchors with many wedges
+    const int32_t SW = SLICE_KEYS;
+    const int32_t C = std::max(1, ceil_div(n, SW));
+    DevBuf<int32_t> soff((size_t)O.n * (C + 1), s);
+    if (O.n > 0) {
+        k_slice_table<<<ceil_div((int64_t)O.n * (C + 1), 256), 256, 0, s>>>(O.off, O.adj, O.n, C,
+                                                                          SW, soff.get());
+        RC_LAUNCH();
+    }
+    const int32_t bmw_s = ((SW / 32) + 3) & ~3;
+    const size_t smem_slice = (size_t)HEAD_MAX / 2 * 4 + (size_t)bmw_s * 4 +
+                              (size_t)REPEAT_SLOTS * 8 + CHUNK_BYTES;
+    RC_CUDA(cudaFuncSetAttribute(k_cd_update_slice, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_slice));
+    int occ_s = 1;
+    RC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, k_cd_update_slice, CTA_THREADS,
+                                                          smem_slice));
+    const int sblocks = sms * std::max(1, occ_s);
+    DevBuf<uint32_t> scnt((size_t)sblocks * SW, s);
+    DevBuf<int32_t> stouch((size_t)sblocks * SW, s);
+    scnt.zero();
     // tiers available for peel anchors (key space = whole side)
     const size_t chunk_extra = CHUNK_BYTES;
     int32_t headn = 0, bmw = 0;
@@ -520,23 +680,26 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
     RC_CUDA(cudaFuncSetAttribute(k_cd_update_global, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem_glob));
     unsigned long long *hpin = nullptr;
-    RC_CUDA(cudaMallocHost((void **)&hpin, 64));
+    RC_CUDA(cudaMallocHost((void **)&hpin, 64 + sizeof(CdDev)));
+    CdDev *hst = reinterpret_cast<CdDev *>(hpin + 8);
+    const size_t hdr = offsetof(CdDev, hist_w);
+    unsigned long long prev_w[4] = {0, 0, 0, 0}, prev_a[4] = {0, 0, 0, 0};
     struct PinGuard {
         void *p;
         ~PinGuard() { cudaFreeHost(p); }
     } pg{hpin};
     int32_t *hi32 = reinterpret_cast<int32_t *>(hpin);
 
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     struct EvGuard {
         cudaEvent_t *e;
         ~EvGuard() {
-            for (int i = 0; i < 4; i++)
+            for (int i = 0; i < 5; i++)
                 if (e[i]) cudaEventDestroy(e[i]);
         }
     } eg{ev};
     if (D.timing)
-        for (int i = 0; i < 4; i++) RC_CUDA(cudaEventCreate(&ev[i]));
+        for (int i = 0; i < 5; i++) RC_CUDA(cudaEventCreate(&ev[i]));
     k_init_state<<<ceil_div(n, 256), 256, 0, s>>>(D.sub, n);
     RC_LAUNCH();
     const int nb = std::min(ceil_div(n, 512), sms * 4);
@@ -564,10 +727,11 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
         RC_LAUNCH();
         for (;;) {
             k_cd_prepare<<<nb, 512, 0, s>>>(cur, st.get(), range, D.sub, D.sup, D.wfull, S.off,
-                                            cta_ok ? 1 : 0, Lw.get(), Lc.get(), Lg.get());
+                                            cta_ok ? 1 : 0, Lw.get(), Lc.get(), Lg.get(),
+                                            Ls.get(), warp_max_w, slice_min_w);
             RC_LAUNCH();
-            PeelArgs a{S.off, S.adj, O.off, O.adj, D.sup, D.sub, st.get(),
-                       Lw.get(), Lc.get(), Lg.get(), Lo.get(), nxt};
+            PeelArgs a{S.off, S.adj, O.off, O.adj, D.sup, D.sub, st.get(), Lw.get(), Lc.get(),
+                       Lg.get(), Ls.get(), nxt, soff.get(), C, SW};
             if (D.timing) RC_CUDA(cudaEventRecord(ev[0], s));
             k_cd_update_warp<<<sms * 8, 256, 0, s>>>(a);
             RC_LAUNCH();
@@ -582,19 +746,36 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
                                                                       n);
             RC_LAUNCH();
             if (D.timing) RC_CUDA(cudaEventRecord(ev[3], s));
+            k_cd_update_slice<<<sblocks, CTA_THREADS, smem_slice, s>>>(a, bmw_s, n, scnt.get(),
+                                                                       stouch.get());
+            RC_LAUNCH();
+            if (D.timing) RC_CUDA(cudaEventRecord(ev[4], s));
             D.tier_launches[0]++;
             D.tier_launches[2]++;
+            D.tier_launches[3]++;
             D.rounds++;
-            RC_CUDA(cudaMemcpyAsync(hi32 + 4, &st.get()->nNext, 4, cudaMemcpyDeviceToHost, s));
+            RC_CUDA(cudaMemcpyAsync(hst, st.get(), hdr, cudaMemcpyDeviceToHost, s));
             RC_CUDA(cudaStreamSynchronize(s));
+            receipt_round rr{};
+            rr.range = range;
+            rr.frontier = hst->nF;
+            rr.hi = hi;
+            for (int t = 0; t < 4; t++) {
+                rr.anchors[t] = hst->tier_a[t] - prev_a[t];
+                rr.wedges[t] = hst->tier_w[t] - prev_w[t];
+                prev_a[t] = hst->tier_a[t];
+                prev_w[t] = hst->tier_w[t];
+            }
             if (D.timing) {
-                for (int t = 0; t < 3; t++) {
+                for (int t = 0; t < 4; t++) {
                     float ms = 0;
                     RC_CUDA(cudaEventElapsedTime(&ms, ev[t], ev[t + 1]));
                     D.tier_ms[t] += ms;
+                    rr.ms[t] = ms;
                 }
             }
-            if (hi32[4] == 0) break;
+            D.trace.push_back(rr);
+            if (hst->nNext == 0) break;
             k_cd_advance<<<1, 1, 0, s>>>(st.get());
             RC_LAUNCH();
             std::swap(cur, nxt);
@@ -608,17 +789,17 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
     RC_LAUNCH();
     int hany = 0;
     RC_CUDA(cudaMemcpyAsync(&hany, any.get(), 4, cudaMemcpyDeviceToHost, s));
-    unsigned long long hw = 0, ht[9];
+    unsigned long long hw = 0, ht[12];
     RC_CUDA(cudaMemcpyAsync(&hw, &st.get()->wedges, 8, cudaMemcpyDeviceToHost, s));
     RC_CUDA(cudaMemcpyAsync(ht, st.get()->tier_w, sizeof(ht), cudaMemcpyDeviceToHost, s));
     RC_CUDA(cudaStreamSynchronize(s));
     D.p_eff = range + (hany ? 1 : 0);
     if (hany) D.bounds.push_back(~0ull);
     D.wedges_cd = hw;
-    for (int t = 0; t < 3; t++) {
+    for (int t = 0; t < 4; t++) {
         D.tier_wedges[t] = ht[t];
-        D.tier_mids[t] = ht[3 + t];
-        D.tier_anchors[t] = ht[6 + t];
+        D.tier_mids[t] = ht[4 + t];
+        D.tier_anchors[t] = ht[8 + t];
     }
 }
 

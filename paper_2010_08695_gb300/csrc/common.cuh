@@ -105,6 +105,7 @@ struct receipt_graph {
     int32_t max_deg[2] = {0, 0};
     receipt::Side side[2];
     receipt_stats stats{};
+    std::vector<receipt_round> trace;  // rounds of the last decomposition
     void *owned = nullptr;  // device allocation holding every array above
 };
 

@@ -34,7 +34,11 @@ constexpr int MID_CHUNK = CTA_THREADS;
 constexpr int REPEAT_SLOTS = 4096;  // CtaHybrid repeat table
 constexpr int REPEAT_LIMIT = REPEAT_SLOTS / 2;
 constexpr int HEAD_MAX = 16384;     // dense 16-bit counters for keys < head
+constexpr int HEAD_SLICE = 2048;    // head of the key slices after the first
+constexpr int SLICE_KEYS = 65536;   // keys per slice of the sliced tier
+constexpr int SLICE_MIN_W = 49152;  // anchors with more wedges use the sliced tier
 constexpr int MAX_PROBE = 64;
+constexpr int WALK_UNROLL = 8;     // independent loads in flight per warp in cta_walk
 
 __device__ __forceinline__ uint32_t hash_key(int32_t k) {
     return (uint32_t)k * 2654435761u;
@@ -190,6 +194,45 @@ struct CtaHybrid {
         }
         return 1u;
     }
+    // Emits (EMIT) every key with count >= 2 and returns the engine to all
+    // zeros for the active key range, reading each structure once. The
+    // caller synchronises afterwards and then calls reset_scalars().
+    template <bool EMIT, class Emit>
+    __device__ void flush_clear(Emit &emit) {
+        const int used = *(volatile int *)s_used;
+        const int hw = act_hw;
+        for (int w = threadIdx.x; w < hw; w += blockDim.x) {
+            uint32_t v = head[w];
+            if (v) {
+                head[w] = 0;
+                if (EMIT) {
+                    uint32_t c0 = v & 0xffffu, c1 = v >> 16;
+                    if (c0 >= 2) emit(2 * w, c0);
+                    if (c1 >= 2) emit(2 * w + 1, c1);
+                }
+            }
+        }
+        if (used > 0) {
+            for (int i = threadIdx.x; i < REPEAT_SLOTS; i += blockDim.x) {
+                int32_t k = rkey[i];
+                if (k != EMPTY_KEY) {
+                    if (EMIT) emit(k, 1u + rval[i]);
+                    rkey[i] = EMPTY_KEY;
+                    rval[i] = 0;
+                }
+            }
+        }
+        uint4 z = make_uint4(0, 0, 0, 0);
+        for (int i = threadIdx.x; i < (act_bw >> 2); i += blockDim.x) ((uint4 *)bm)[i] = z;
+        for (int i = (act_bw & ~3) + threadIdx.x; i < act_bw; i += blockDim.x) bm[i] = 0;
+    }
+    __device__ void reset_scalars() {
+        if (threadIdx.x == 0) {
+            *s_used = 0;
+            *s_over = 0;
+        }
+    }
+
     // calls emit(key, count) for every key with count >= 2
     template <class Emit>
     __device__ void flush(Emit &emit) {
@@ -288,8 +331,11 @@ __device__ int64_t cta_walk(const Mids &M, int64_t q0, int64_t q1, const int32_t
         ch.pre[threadIdx.x] = ex;
         if (threadIdx.x == 0) ch.pre[blockDim.x] = total;
         __syncthreads();
-        // warps take 32-wide slabs of the flat wedge index
-        for (int32_t base = warp * 32; base < total; base += nwarps * 32) {
+        // Each warp takes WALK_UNROLL consecutive 32-wide slabs of the flat
+        // wedge index per step and issues all their loads before using any,
+        // so WALK_UNROLL independent L2 reads are in flight per warp.
+        for (int32_t base = warp * 32 * WALK_UNROLL; base < total;
+             base += nwarps * 32 * WALK_UNROLL) {
             // largest k with pre[k] <= base (binary search, broadcast reads)
             int lo = 0, hi = nm - 1;
             while (lo < hi) {
@@ -299,13 +345,22 @@ __device__ int64_t cta_walk(const Mids &M, int64_t q0, int64_t q1, const int32_t
                 else
                     hi = mid - 1;
             }
-            int32_t j = base + lane;
-            if (j < total) {
-                int k = lo;
-                while (k + 1 < nm && ch.pre[k + 1] <= j) k++;
-                int32_t key = keys[ch.beg[k] + (j - ch.pre[k])];
-                visit(k, key);
+            int kk[WALK_UNROLL];
+            int32_t key[WALK_UNROLL];
+            int k = lo;
+#pragma unroll
+            for (int u = 0; u < WALK_UNROLL; u++) {
+                int32_t j = base + u * 32 + lane;
+                kk[u] = -1;
+                if (j < total) {
+                    while (k + 1 < nm && ch.pre[k + 1] <= j) k++;
+                    kk[u] = k;
+                    key[u] = __ldg(keys + ch.beg[k] + (j - ch.pre[k]));
+                }
             }
+#pragma unroll
+            for (int u = 0; u < WALK_UNROLL; u++)
+                if (kk[u] >= 0) visit(kk[u], key[u]);
         }
         walked += total;
         __syncthreads();

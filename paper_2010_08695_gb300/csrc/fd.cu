@@ -158,8 +158,11 @@ struct FdArgs {
     uint8_t *alive;            // by member position
     int32_t *alist;            // by member position
     int32_t *plist;            // by member position
+    int32_t *blist;            // by member position: peeled vertices with big updates
     unsigned long long *tip;   // output, original ids
     unsigned long long *stats; // [0] wedges, [1] levels
+    unsigned long long *sub_ns;     // per subset: nanoseconds spent
+    unsigned long long *sub_levels; // per subset: peeling levels
     uint32_t *gcnt;            // global engine, per CTA slot
     int32_t *gtouch;
     int64_t gks;               // global engine key space per slot
@@ -194,7 +197,7 @@ struct FdVisit {
 
 __global__ void __launch_bounds__(FD_THREADS) k_fd_peel(FdArgs a, int32_t headn, int32_t bm_words) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_t, s_used, s_over, s_nt, s_np, s_nk;
+    __shared__ int s_t, s_used, s_over, s_nt, s_np, s_nk, s_nbig;
     __shared__ unsigned long long s_min[32];
     __shared__ int32_t s_tmp[33];
     CtaHybrid H;
@@ -207,6 +210,11 @@ __global__ void __launch_bounds__(FD_THREADS) k_fd_peel(FdArgs a, int32_t headn,
     ch.beg = (int64_t *)(H.rval + REPEAT_SLOTS);
     ch.pre = (int32_t *)(ch.beg + MID_CHUNK);
     ch.tmp = ch.pre + MID_CHUNK + 1;
+    // warp-private tables after the chunk staging
+    int32_t *wkey = (int32_t *)(((uintptr_t)(ch.tmp + 33) + 15) & ~(uintptr_t)15);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    WarpHash WH{wkey + warp * WARP_SLOTS, (uint32_t *)(wkey + nwarps * WARP_SLOTS) + warp * WARP_SLOTS};
+    WH.clear(lane);
     H.s_used = &s_used;
     H.s_over = &s_over;
     H.headn = headn;
@@ -228,10 +236,14 @@ __global__ void __launch_bounds__(FD_THREADS) k_fd_peel(FdArgs a, int32_t headn,
         const int32_t mb = a.mstart[i];
         const int32_t ni = a.mstart[i + 1] - mb;
         if (ni == 0) continue;
+        unsigned long long t_start = 0;
+        if (threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
+        const unsigned long long levels0 = levels;
         unsigned long long *fsup = a.fsup + mb;
         uint8_t *alive = a.alive + mb;
         int32_t *alist = a.alist + mb;
         int32_t *plist = a.plist + mb;
+        int32_t *blist = a.blist + mb;
         const int32_t *mem = a.members + mb;
         for (int r = threadIdx.x; r < ni; r += blockDim.x) {
             fsup[r] = a.init[mem[r]];
@@ -293,25 +305,72 @@ __global__ void __launch_bounds__(FD_THREADS) k_fd_peel(FdArgs a, int32_t headn,
             }
             nalive = s_nk;
             const int np = s_np;
-            // updates of the peeled vertices inside G_i
-            for (int pi = 0; pi < np; pi++) {
+            // updates of the peeled vertices inside G_i. Phase A: one warp per
+            // peeled vertex whose update walks at most WARP_MAX_W wedges.
+            FdEmit emit_w{fsup, alive};
+            if (threadIdx.x == 0) s_nbig = 0;
+            __syncthreads();
+            for (int pi = warp; pi < np; pi += nwarps) {
                 const int32_t r = plist[pi];
+                const int32_t x = mem[r];
+                const int64_t q0 = a.off_s[x], q1 = a.off_s[x + 1];
+                int64_t W = 0;
+                for (int64_t q = q0 + lane; q < q1; q += 32) W += a.fd_len[q];
+                W = warp_sum(W);
+                if (W > WARP_MAX_W) {
+                    if (lane == 0) blist[atomicAdd(&s_nbig, 1)] = r;
+                    continue;
+                }
+                for (int64_t qb = q0; qb < q1; qb += 32) {
+                    int64_t q = qb + lane;
+                    int64_t beg = 0;
+                    int32_t len = 0;
+                    if (q < q1) {
+                        beg = a.fd_beg[q];
+                        len = a.fd_len[q];
+                    }
+                    const int cnt = (int)imin64(32, q1 - qb);
+                    for (int t2 = 0; t2 < cnt; t2++) {
+                        int64_t b = __shfl_sync(0xffffffffu, beg, t2);
+                        int32_t l = __shfl_sync(0xffffffffu, len, t2);
+                        for (int p = lane; p < l; p += 32) {
+                            int32_t k = a.fd_adj[b + p];
+                            if (k != r) WH.add(k);
+                        }
+                    }
+                }
+                __syncwarp();
+                for (int sl = lane; sl < WARP_SLOTS; sl += 32) {
+                    int32_t k = WH.key[sl];
+                    if (k != EMPTY_KEY) {
+                        uint32_t c = WH.val[sl];
+                        if (c >= 2) emit_w(k, c);
+                        WH.key[sl] = EMPTY_KEY;
+                        WH.val[sl] = 0;
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) wedges += (unsigned long long)W;
+            }
+            __syncthreads();
+            const int nbig = s_nbig;
+            // Phase B: the whole CTA per peeled vertex with a bigger update
+            for (int pi = 0; pi < nbig; pi++) {
+                const int32_t r = blist[pi];
                 const int32_t x = mem[r];
                 const int64_t q0 = a.off_s[x], q1 = a.off_s[x + 1];
                 FdEmit emit{fsup, alive};
                 if (small && q1 - q0 < 65535) {
                     FdVisit<CtaHybrid> v{&H, r};
                     wedges += cta_walk(M, q0, q1, a.fd_adj, ch, v);
-                    if (!s_over) {
-                        H.flush(emit);
-                        __syncthreads();
-                        H.clear_active();
-                        __syncthreads();
-                        continue;
-                    }
+                    const bool over = s_over;
+                    if (!over)
+                        H.flush_clear<true>(emit);
+                    else
+                        H.flush_clear<false>(emit);
                     __syncthreads();
-                    H.clear_active();
-                    __syncthreads();
+                    H.reset_scalars();
+                    if (!over) continue;
                 }
                 if (threadIdx.x == 0) s_nt = 0;
                 __syncthreads();
@@ -324,6 +383,12 @@ __global__ void __launch_bounds__(FD_THREADS) k_fd_peel(FdArgs a, int32_t headn,
             }
         }
         __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long t_end;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
+            a.sub_ns[i] = t_end - t_start;
+            a.sub_levels[i] = levels - levels0;
+        }
     }
     if (threadIdx.x == 0) {
         atomicAdd(&a.stats[0], wedges);
@@ -394,9 +459,11 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
     RC_CUDA(cudaStreamSynchronize(s));
     int32_t maxn = 0;
     for (int i = 0; i < P; i++) maxn = std::max(maxn, hms[i + 1] - hms[i]);
-    const int64_t cta_ks = max_cta_keyspace(maxn, CHUNK_BYTES);
+    const size_t warp_tables = (size_t)(FD_THREADS / 32) * WARP_SLOTS * 8 + 16;
+    const int64_t cta_ks = max_cta_keyspace(maxn, CHUNK_BYTES + warp_tables);
     int32_t headn = 0, bmw = 0;
-    size_t smem = hybrid_bytes(std::max<int64_t>(cta_ks, 2), &headn, &bmw) + CHUNK_BYTES;
+    size_t smem =
+        hybrid_bytes(std::max<int64_t>(cta_ks, 2), &headn, &bmw) + CHUNK_BYTES + warp_tables;
     RC_CUDA(cudaFuncSetAttribute(k_fd_peel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
     RC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fd_peel, FD_THREADS, smem));
@@ -408,15 +475,17 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
     gcnt.zero();
     DevBuf<unsigned long long> fsup(n, s);
     DevBuf<uint8_t> alive(n, s);
-    DevBuf<int32_t> alist(n, s), plist(n, s), qhead(1, s);
-    DevBuf<unsigned long long> stats(2, s);
+    DevBuf<int32_t> alist(n, s), plist(n, s), blist(n, s), qhead(1, s);
+    DevBuf<unsigned long long> stats(2, s), sub_ns(P, s), sub_lv(P, s);
     qhead.zero();
     stats.zero();
+    sub_ns.zero();
+    sub_lv.zero();
     FdArgs a{queue.get(),   P,           qhead.get(),     mstart.get(), members.get(),
              S.off,         fd_beg.get(), fd_len.get(),   fd_adj.get(), S.new2old,
-             D.init,        fsup.get(),  alive.get(),     alist.get(),  plist.get(),
-             (unsigned long long *)d_tip, stats.get(),    gcnt.get(),   gtouch.get(),
-             (int64_t)maxn, (int32_t)cta_ks};
+             D.init,        fsup.get(),  alive.get(),     alist.get(),  plist.get(), blist.get(),
+             (unsigned long long *)d_tip, stats.get(),    sub_ns.get(), sub_lv.get(),
+             gcnt.get(),    gtouch.get(), (int64_t)maxn, (int32_t)cta_ks};
     k_fd_peel<<<grid, FD_THREADS, smem, s>>>(a, headn, bmw);
     RC_LAUNCH();
     unsigned long long hs[2] = {0, 0};
@@ -424,6 +493,15 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
     RC_CUDA(cudaStreamSynchronize(s));
     D.wedges_fd = hs[0];
     D.levels = (int64_t)hs[1];
+    std::vector<unsigned long long> hns(P), hlv(P);
+    RC_CUDA(cudaMemcpy(hns.data(), sub_ns.get(), 8 * P, cudaMemcpyDeviceToHost));
+    RC_CUDA(cudaMemcpy(hlv.data(), sub_lv.get(), 8 * P, cudaMemcpyDeviceToHost));
+    int worst = 0;
+    for (int i = 1; i < P; i++)
+        if (hns[i] > hns[worst]) worst = i;
+    D.fd_max_ms = (float)(hns[worst] * 1e-6);
+    D.fd_max_n = hms[worst + 1] - hms[worst];
+    D.fd_max_levels = (int64_t)hlv[worst];
 }
 
 }  // namespace receipt

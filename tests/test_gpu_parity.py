@@ -85,6 +85,22 @@ def test_repeat_table_overflow_path(R):
     _check_graph(R, eu, ev, 40000, 200, sides=(0,))
 
 
+def test_sliced_tier_over_several_key_slices(R):
+    # 150k U vertices (three 64K-key slices); a low slice threshold sends every
+    # anchor with more than 2,000 wedges through the sliced tier, and a tiny
+    # threshold also exercises its repeat-table fallback
+    eu, ev = synth.chung_lu(150000, 3000, 450000, 2.4, 2.3, seed=41)
+    want, _ = oracle.bup(eu, ev, 150000, 3000, 0)
+    g = R.Graph(eu, ev, 150000, 3000)
+    for smw in (2000, 300):
+        t = R.as_u64(g.tip_decompose(0, slice_min_w=smw, timing=True))
+        assert np.array_equal(t, want), f"slice_min_w={smw}"
+        st = g.stats()
+        assert st["peel_anchors"][3] > 0
+    t = R.as_u64(g.tip_decompose(0, warp_max_w=32))
+    assert np.array_equal(t, want)
+
+
 def test_hub_with_degree_above_16_bits(R):
     rng = np.random.default_rng(22)
     nu, nv = 80000, 50
