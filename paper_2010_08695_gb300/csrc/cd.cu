@@ -361,25 +361,17 @@ struct PeelVisit {
     }
 };
 
-__global__ void __launch_bounds__(CTA_THREADS) k_cd_update_cta(PeelArgs a, int32_t headn, int32_t bm_words,
-                                                            int32_t keyspace) {
+__global__ void __launch_bounds__(CTA_THREADS) k_cd_update_cta(PeelArgs a, int32_t head_cap,
+                                                            int32_t bm_cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_idx, s_used, s_over;
     CtaHybrid H;
-    size_t hw = (size_t)(((headn >> 1) + 3) & ~3);
-    H.head = (uint32_t *)smem;
-    H.bm = H.head + hw;
-    H.rkey = (int32_t *)(H.bm + bm_words);
-    H.rval = (uint32_t *)(H.rkey + REPEAT_SLOTS);
+    unsigned char *p = H.bind(smem, head_cap, bm_cap, &s_used, &s_over);
     Chunk ch;
-    ch.beg = (int64_t *)(H.rval + REPEAT_SLOTS);
+    ch.beg = (int64_t *)p;
     ch.pre = (int32_t *)(ch.beg + MID_CHUNK);
     ch.tmp = ch.pre + MID_CHUNK + 1;
-    H.s_used = &s_used;
-    H.s_over = &s_over;
-    H.headn = headn;
-    H.bm_words = bm_words;
-    H.set_active(keyspace);
+    ch.len = chunk_len_ptr(ch.tmp);
     H.clear_all();
     __syncthreads();
     const int32_t n = a.st->nLc;
@@ -420,6 +412,7 @@ __global__ void __launch_bounds__(CTA_THREADS) k_cd_update_global(PeelArgs a, ui
     ch.beg = (int64_t *)smem;
     ch.pre = (int32_t *)(ch.beg + MID_CHUNK);
     ch.tmp = ch.pre + MID_CHUNK + 1;
+    ch.len = chunk_len_ptr(ch.tmp);
     GlobalDense G{gcnt + (size_t)blockIdx.x * keyspace, gtouch + (size_t)blockIdx.x * keyspace, &s_nt};
     const int32_t n1 = a.st->nLg, n2 = 0;
     CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext};
@@ -484,31 +477,21 @@ struct SliceEmit {
     __device__ __forceinline__ void operator()(int32_t k, uint32_t c) { (*e)(k + base, c); }
 };
 
-// Anchors with many wedges: the key space is cut into C slices of SW keys,
-// and the CTA aggregates one slice at a time with the hybrid engine sized
-// for SW keys (dense head counters only on slice 0, where the high-degree
-// end points sit). A slice whose repeat table overflows is redone with dense
-// counters in this CTA's slot of global memory.
-__global__ void __launch_bounds__(CTA_THREADS) k_cd_update_slice(PeelArgs a, int32_t bm_words,
-                                                              int32_t n, uint32_t *gcnt,
-                                                              int32_t *gtouch) {
+// Anchors with many wedges: the key space is cut into C slices of SW keys and
+// every (anchor, slice) pair is one work item, so the slices of a heavy
+// anchor run on different CTAs. Each item aggregates its slice with dense
+// 16-bit counters in shared memory.
+__global__ void __launch_bounds__(SLICE_THREADS, 2) k_cd_update_slice(PeelArgs a, int32_t n) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_idx, s_used, s_over, s_nt;
-    CtaHybrid H;
-    H.head = (uint32_t *)smem;
-    H.bm = H.head + HEAD_MAX / 2;
-    H.rkey = (int32_t *)(H.bm + bm_words);
-    H.rval = (uint32_t *)(H.rkey + REPEAT_SLOTS);
+    __shared__ int s_idx, s_nt;
+    DenseSlice H;
+    unsigned char *p = H.bind(smem, &s_nt);
     Chunk ch;
-    ch.beg = (int64_t *)(H.rval + REPEAT_SLOTS);
+    ch.beg = (int64_t *)p;
     ch.pre = (int32_t *)(ch.beg + MID_CHUNK);
     ch.tmp = ch.pre + MID_CHUNK + 1;
-    H.s_used = &s_used;
-    H.s_over = &s_over;
-    H.headn = HEAD_MAX;
-    H.bm_words = bm_words;
+    ch.len = chunk_len_ptr(ch.tmp);
     H.clear_all();
-    GlobalDense G{gcnt + (size_t)blockIdx.x * a.SW, gtouch + (size_t)blockIdx.x * a.SW, &s_nt};
     __syncthreads();
     CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext};
     unsigned long long cw = 0, cm = 0, ca = 0;
@@ -518,8 +501,6 @@ __global__ void __launch_bounds__(CTA_THREADS) k_cd_update_slice(PeelArgs a, int
         __syncthreads();
         const int64_t idx = s_idx;
         if (idx >= items) break;
-        // work item = (anchor, key slice): the slices of one anchor go to
-        // different CTAs
         const int32_t x = a.Ls[idx / a.C];
         const int32_t j = (int32_t)(idx % a.C);
         const int64_t q0 = a.off_s[x], q1 = a.off_s[x + 1];
@@ -529,33 +510,17 @@ __global__ void __launch_bounds__(CTA_THREADS) k_cd_update_slice(PeelArgs a, int
         }
         const int32_t base = j * a.SW;
         const int32_t w = (int32_t)imin64(a.SW, (int64_t)n - base);
-        int32_t hn = j == 0 ? (int32_t)imin64(HEAD_MAX, w) : (int32_t)imin64(HEAD_SLICE, w);
-        H.headn = (hn + 1) & ~1;
-        H.set_active(w);
+        H.set_width(w);
         SlicedMids M{a.adj_s, a.off_o, a.soff, a.C + 1, j};
         const int32_t self = (x >= base && x < base + w) ? x - base : -1;
-        SliceVisit<CtaHybrid> v{&H, self, base};
+        SliceVisit<DenseSlice> v{&H, self, base};
         int64_t walked = cta_walk(M, q0, q1, a.adj_o, ch, v);
         cw += walked;
         if (walked == 0) continue;
         SliceEmit em{&emit, base};
-        const bool over = s_over;
-        if (!over)
-            H.flush_clear<true>(em);
-        else
-            H.flush_clear<false>(em);
+        H.sweep<true, true>(em);
         __syncthreads();
         H.reset_scalars();
-        if (over) {
-            if (threadIdx.x == 0) s_nt = 0;
-            __syncthreads();
-            SliceVisit<GlobalDense> gv{&G, self, base};
-            cta_walk(M, q0, q1, a.adj_o, ch, gv);
-            G.flush(em);
-            __syncthreads();
-            G.clear();
-            __syncthreads();
-        }
     }
     if (threadIdx.x == 0) {
         if (cw) atomicAdd(&a.st->tier_w[3], cw);
@@ -652,23 +617,18 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
                                                                           SW, soff.get());
         RC_LAUNCH();
     }
-    const int32_t bmw_s = ((SW / 32) + 3) & ~3;
-    const size_t smem_slice = (size_t)HEAD_MAX / 2 * 4 + (size_t)bmw_s * 4 +
-                              (size_t)REPEAT_SLOTS * 8 + CHUNK_BYTES;
+    const size_t smem_slice = DenseSlice::bytes() + CHUNK_BYTES;
     RC_CUDA(cudaFuncSetAttribute(k_cd_update_slice, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem_slice));
     int occ_s = 1;
-    RC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, k_cd_update_slice, CTA_THREADS,
+    RC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, k_cd_update_slice, SLICE_THREADS,
                                                           smem_slice));
     const int sblocks = sms * std::max(1, occ_s);
-    DevBuf<uint32_t> scnt((size_t)sblocks * SW, s);
-    DevBuf<int32_t> stouch((size_t)sblocks * SW, s);
-    scnt.zero();
     // tiers available for peel anchors (key space = whole side)
     const size_t chunk_extra = CHUNK_BYTES;
-    int32_t headn = 0, bmw = 0;
+    int32_t head_cap = 0, bm_cap = 0;
     const bool cta_ok = max_cta_keyspace(n, chunk_extra) >= n;
-    size_t smem_cta = cta_ok ? hybrid_bytes(n, &headn, &bmw) + chunk_extra : 0;
+    size_t smem_cta = cta_ok ? hybrid_bytes(n, &head_cap, &bm_cap) + chunk_extra : 0;
     if (cta_ok)
         RC_CUDA(cudaFuncSetAttribute(k_cd_update_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem_cta));
@@ -737,7 +697,7 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
             RC_LAUNCH();
             if (D.timing) RC_CUDA(cudaEventRecord(ev[1], s));
             if (cta_ok) {
-                k_cd_update_cta<<<sms, CTA_THREADS, smem_cta, s>>>(a, headn, bmw, n);
+                k_cd_update_cta<<<sms, CTA_THREADS, smem_cta, s>>>(a, head_cap, bm_cap);
                 RC_LAUNCH();
                 D.tier_launches[1]++;
             }
@@ -746,8 +706,7 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
                                                                       n);
             RC_LAUNCH();
             if (D.timing) RC_CUDA(cudaEventRecord(ev[3], s));
-            k_cd_update_slice<<<sblocks, CTA_THREADS, smem_slice, s>>>(a, bmw_s, n, scnt.get(),
-                                                                       stouch.get());
+            k_cd_update_slice<<<sblocks, SLICE_THREADS, smem_slice, s>>>(a, n);
             RC_LAUNCH();
             if (D.timing) RC_CUDA(cudaEventRecord(ev[4], s));
             D.tier_launches[0]++;

@@ -219,32 +219,26 @@ __device__ unsigned long long block_sum_u64(unsigned long long v, unsigned long 
     return r;
 }
 
-__global__ void __launch_bounds__(CTA_THREADS) k_count_cta(CountArgs a, int32_t headn, int32_t bm_words,
-                                                        int32_t *over_list, int32_t *n_over) {
+__global__ void __launch_bounds__(CTA_THREADS) k_count_cta(CountArgs a, int32_t head_cap,
+                                                        int32_t bm_cap, int32_t *over_list,
+                                                        int32_t *n_over) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_idx, s_used, s_over;
     __shared__ unsigned long long s_red[32];
     CtaHybrid H;
-    size_t hw = (size_t)(((headn >> 1) + 3) & ~3);
-    H.head = (uint32_t *)smem;
-    H.bm = H.head + hw;
-    H.rkey = (int32_t *)(H.bm + bm_words);
-    H.rval = (uint32_t *)(H.rkey + REPEAT_SLOTS);
-    unsigned char *p = (unsigned char *)(H.rval + REPEAT_SLOTS);
+    unsigned char *p = H.bind(smem, head_cap, bm_cap, &s_used, &s_over);
     Chunk ch;
     ch.beg = (int64_t *)p;
     unsigned long long *sacc = (unsigned long long *)(ch.beg + MID_CHUNK);
     ch.pre = (int32_t *)(sacc + MID_CHUNK);
     ch.tmp = ch.pre + MID_CHUNK + 1;
-    H.s_used = &s_used;
-    H.s_over = &s_over;
-    H.headn = headn;
-    H.bm_words = bm_words;
+    ch.len = chunk_len_ptr(ch.tmp);
     H.clear_all();
     for (int i = threadIdx.x; i < MID_CHUNK; i += blockDim.x) sacc[i] = 0;
     __syncthreads();
     const int32_t n = *a.nlist;
     CountMids M{a.adjA, a.offB, a.plen};
+    NoEmit ne;
     for (;;) {
         if (threadIdx.x == 0) s_idx = atomicAdd(a.work, 1);
         __syncthreads();
@@ -252,12 +246,13 @@ __global__ void __launch_bounds__(CTA_THREADS) k_count_cta(CountArgs a, int32_t 
         if (idx >= n) break;
         const int32_t sp = a.list[idx];
         const int64_t q0 = a.offA[sp], q1 = a.offA[sp + 1];
-        H.set_active(sp);
+        H.set_range((int32_t)imin64(head_cap, sp), sp);
         AddVisit<CtaHybrid> add{&H};
         cta_walk(M, q0, q1, a.adjB, ch, add);
-        if (!s_over) {
+        const bool over = s_over;
+        if (!over) {
             CountSameEmit<CtaHybrid> em{a.cntA, 0};
-            H.flush(em);
+            H.sweep<true, false>(em);
             unsigned long long tot = block_sum_u64(em.acc, s_red);
             if (threadIdx.x == 0 && tot) atomicAdd(&a.cntA[sp], tot);
             CountOppVisit<CtaHybrid> ov{&H, sacc};
@@ -267,8 +262,9 @@ __global__ void __launch_bounds__(CTA_THREADS) k_count_cta(CountArgs a, int32_t 
             over_list[atomicAdd(n_over, 1)] = sp;
         }
         __syncthreads();
-        H.clear_active();
+        H.sweep<false, true>(ne);
         __syncthreads();
+        H.reset_scalars();
     }
 }
 
@@ -283,6 +279,7 @@ __global__ void __launch_bounds__(CTA_THREADS) k_count_global(CountArgs a, const
     unsigned long long *sacc = (unsigned long long *)(ch.beg + MID_CHUNK);
     ch.pre = (int32_t *)(sacc + MID_CHUNK);
     ch.tmp = ch.pre + MID_CHUNK + 1;
+    ch.len = chunk_len_ptr(ch.tmp);
     GlobalDense G{gcnt + (size_t)blockIdx.x * keyspace, gtouch + (size_t)blockIdx.x * keyspace, &s_nt};
     for (int i = threadIdx.x; i < MID_CHUNK; i += blockDim.x) sacc[i] = 0;
     const int32_t n1 = *a.nlist, n2 = *n_over;
@@ -320,8 +317,8 @@ __global__ void k_scatter_counts(const unsigned long long *__restrict__ cnt,
 
 }  // namespace
 
-size_t count_cta_smem(int64_t keyspace, int32_t *headn, int32_t *bmw) {
-    return hybrid_bytes(keyspace, headn, bmw) + MID_CHUNK * 8 /*sacc*/ + CHUNK_BYTES;
+size_t count_cta_smem(int64_t keyspace, int32_t *head_cap, int32_t *bm_cap) {
+    return hybrid_bytes(keyspace, head_cap, bm_cap) + MID_CHUNK * 8 /*sacc*/ + CHUNK_BYTES;
 }
 
 // Counts butterflies of both sides into cnt_local[side] (local ids, zeroed

@@ -30,12 +30,13 @@ constexpr int32_t EMPTY_KEY = -1;
 constexpr int WARP_MAX_W = 256;     // wedges of a warp-tier anchor
 constexpr int WARP_SLOTS = 512;     // per-warp table (load factor <= 1/2)
 constexpr int CTA_THREADS = 1024;
+constexpr int SLICE_THREADS = 512;  // CTAs of the key-sliced tier (two per SM)
 constexpr int MID_CHUNK = CTA_THREADS;
 constexpr int REPEAT_SLOTS = 4096;  // CtaHybrid repeat table
 constexpr int REPEAT_LIMIT = REPEAT_SLOTS / 2;
 constexpr int HEAD_MAX = 16384;     // dense 16-bit counters for keys < head
 constexpr int HEAD_SLICE = 2048;    // head of the key slices after the first
-constexpr int SLICE_KEYS = 65536;   // keys per slice of the sliced tier
+constexpr int SLICE_KEYS = 36864;   // keys per slice of the sliced tier (= dense slice)
 constexpr int SLICE_MIN_W = 49152;  // anchors with more wedges use the sliced tier
 constexpr int MAX_PROBE = 64;
 constexpr int WALK_UNROLL = 8;     // independent loads in flight per warp in cta_walk
@@ -92,47 +93,71 @@ struct WarpHash {
 // ------------------------------------------------------------------
 // CTA hybrid: dense head counters + tail bitmap + repeat table
 // ------------------------------------------------------------------
+// Keys below `headn` (low labels = high degree, where repeated end points
+// concentrate) have 16-bit counters, two per word: key k < hw sits in the low
+// half of word k, key k >= hw in the high half of word k - hw, so consecutive
+// keys land in different words (no same-address atomics within a warp).
+// Keys from headn on set a bit in a bitmap; a bit found already set sends the
+// key to a small open-addressing table of extra occurrences; every repeat slot
+// taken is listed, so the table is flushed and cleared in time proportional
+// to its use. Head counters and the bitmap are swept with 16-byte accesses
+// over the key range in use.
 struct CtaHybrid {
-    uint32_t *head;   // head/2 words, two 16-bit counters each
-    uint32_t *bm;     // bitmap over keys [head, keyspace)
+    uint32_t *head;   // head_cap/2 words
+    uint32_t *hsum;   // reserved (keeps the layout 16-byte aligned)
+    uint32_t *bm;     // bm_cap words over keys [headn, headn + 32 * bm_cap)
+    uint32_t *tsum;   // reserved
     int32_t *rkey;    // REPEAT_SLOTS
     uint32_t *rval;   // REPEAT_SLOTS: extra occurrences (count - 1)
-    int *s_used;      // shared scalar: repeat slots in use
+    int32_t *rlist;   // REPEAT_LIMIT + 1: slots taken, in order
+    int *s_used;      // shared scalar: repeat slots taken
     int *s_over;      // shared scalar: repeat table overflowed
-    int32_t headn;    // number of head keys (even)
-    int32_t bm_words; // bitmap words
-    int32_t act_hw;   // head words in use for the current anchor
-    int32_t act_bw;   // bitmap words in use for the current anchor
+    int32_t headn;    // keys with dense counters (<= head_cap)
+    int32_t hw;       // (headn + 1) / 2
+    int32_t act_bw;   // bitmap words the current key range can touch
+    int32_t head_cap; // capacity in keys
+    int32_t bm_cap;   // capacity in bitmap words
 
-    // Restricts clear/flush to keys below ks (counting: end points < sp).
-    __device__ void set_active(int64_t ks) {
-        int64_t h = ks < headn ? ks : headn;
-        act_hw = (int32_t)((h + 1) >> 1);
-        int64_t t = ks - headn;
-        act_bw = t > 0 ? (int32_t)imin64((t + 31) >> 5, bm_words) : 0;
+    __host__ __device__ static int32_t pad4(int64_t w) { return (int32_t)((w + 3) & ~3ll); }
+    __host__ __device__ static size_t bytes(int32_t head_cap, int32_t bm_cap) {
+        int32_t hwc = pad4((head_cap + 1) / 2), hs = pad4((hwc + 31) / 32);
+        int32_t bmc = pad4(bm_cap), ts = pad4((bmc + 31) / 32);
+        return (size_t)4 * (hwc + hs + bmc + ts) + (size_t)REPEAT_SLOTS * 8 +
+               (size_t)(REPEAT_LIMIT + 4) * 4;
     }
-    __device__ void clear_active() {
-        for (int i = threadIdx.x; i < act_hw; i += blockDim.x) head[i] = 0;
-        uint4 z = make_uint4(0, 0, 0, 0);
-        for (int i = threadIdx.x; i < (act_bw >> 2); i += blockDim.x) ((uint4 *)bm)[i] = z;
-        for (int i = (act_bw & ~3) + threadIdx.x; i < act_bw; i += blockDim.x) bm[i] = 0;
-        for (int i = threadIdx.x; i < REPEAT_SLOTS; i += blockDim.x) {
-            rkey[i] = EMPTY_KEY;
-            rval[i] = 0;
-        }
-        if (threadIdx.x == 0) {
-            *s_used = 0;
-            *s_over = 0;
-        }
+    // Lays the engine out from `base` (16-byte aligned); returns the end.
+    __device__ unsigned char *bind(unsigned char *base, int32_t hcap, int32_t bcap, int *used,
+                                   int *over) {
+        head_cap = hcap;
+        bm_cap = pad4(bcap);
+        int32_t hwc = pad4((hcap + 1) / 2), hs = pad4((hwc + 31) / 32);
+        int32_t ts = pad4((bm_cap + 31) / 32);
+        head = (uint32_t *)base;
+        hsum = head + hwc;
+        bm = hsum + hs;
+        tsum = bm + bm_cap;
+        rkey = (int32_t *)(tsum + ts);
+        rval = (uint32_t *)(rkey + REPEAT_SLOTS);
+        rlist = (int32_t *)(rval + REPEAT_SLOTS);
+        s_used = used;
+        s_over = over;
+        set_range(hcap, (int64_t)hcap + 32 * (int64_t)bm_cap);
+        return (unsigned char *)(rlist + REPEAT_LIMIT + 4);
     }
-
+    // Current key range [0, keys) with dense counters for the first h keys.
+    __device__ void set_range(int32_t h, int64_t keys) {
+        headn = h;
+        hw = (h + 1) >> 1;
+        int64_t t = keys - h;
+        act_bw = t > 0 ? (int32_t)imin64((t + 31) >> 5, bm_cap) : 0;
+    }
+    // Zeroes everything (once per kernel).
     __device__ void clear_all() {
-        uint4 z = make_uint4(0, 0, 0, 0);
-        int hw = headn >> 1;
-        for (int i = threadIdx.x; i < (hw >> 2); i += blockDim.x) ((uint4 *)head)[i] = z;
-        for (int i = (hw & ~3) + threadIdx.x; i < hw; i += blockDim.x) head[i] = 0;
-        for (int i = threadIdx.x; i < (bm_words >> 2); i += blockDim.x) ((uint4 *)bm)[i] = z;
-        for (int i = (bm_words & ~3) + threadIdx.x; i < bm_words; i += blockDim.x) bm[i] = 0;
+        int32_t hwc = pad4((head_cap + 1) / 2), hs = pad4((hwc + 31) / 32);
+        int32_t ts = pad4((bm_cap + 31) / 32);
+        uint32_t *w0 = head;
+        int32_t nw = hwc + hs + bm_cap + ts;
+        for (int i = threadIdx.x; i < nw; i += blockDim.x) w0[i] = 0;
         for (int i = threadIdx.x; i < REPEAT_SLOTS; i += blockDim.x) {
             rkey[i] = EMPTY_KEY;
             rval[i] = 0;
@@ -144,11 +169,13 @@ struct CtaHybrid {
     }
     __device__ __forceinline__ void add(int32_t k) {
         if (k < headn) {
-            atomicAdd(&head[k >> 1], 1u << ((k & 1) << 4));
+            const bool hi = k >= hw;
+            const int32_t w = hi ? k - hw : k;
+            atomicAdd(&head[w], hi ? 0x10000u : 1u);
             return;
         }
-        int32_t t = k - headn;
-        uint32_t bit = 1u << (t & 31);
+        const int32_t t = k - headn;
+        const uint32_t bit = 1u << (t & 31);
         uint32_t old = atomicOr(&bm[t >> 5], bit);
         if (old & bit) add_repeat(k);
     }
@@ -162,16 +189,16 @@ struct CtaHybrid {
                 return;
             }
             if (cur == EMPTY_KEY) {
-                if (atomicAdd(s_used, 1) >= REPEAT_LIMIT) {
-                    *(volatile int *)s_over = 1;
-                    return;
-                }
                 int32_t prev = atomicCAS(&rkey[h], EMPTY_KEY, k);
                 if (prev == EMPTY_KEY) {
                     atomicAdd(&rval[h], 1u);
+                    int pos = atomicAdd(s_used, 1);
+                    if (pos < REPEAT_LIMIT)
+                        rlist[pos] = (int32_t)h;
+                    else
+                        *(volatile int *)s_over = 1;
                     return;
                 }
-                atomicSub(s_used, 1);
                 if (prev == k) {
                     atomicAdd(&rval[h], 1u);
                     return;
@@ -181,10 +208,12 @@ struct CtaHybrid {
         }
         *(volatile int *)s_over = 1;
     }
-    // count of key k after aggregation (k must have been added at least once
-    // if k >= head; head keys may be 0)
+    // Count of key k after aggregation (a key >= headn must have been added).
     __device__ __forceinline__ uint32_t count(int32_t k) const {
-        if (k < headn) return (head[k >> 1] >> ((k & 1) << 4)) & 0xffffu;
+        if (k < headn) {
+            const bool hi = k >= hw;
+            return (head[hi ? k - hw : k] >> (hi ? 16 : 0)) & 0xffffu;
+        }
         uint32_t h = hash_key(k) & (REPEAT_SLOTS - 1);
         for (int p = 0; p < MAX_PROBE; p++) {
             int32_t cur = rkey[h];
@@ -194,37 +223,58 @@ struct CtaHybrid {
         }
         return 1u;
     }
-    // Emits (EMIT) every key with count >= 2 and returns the engine to all
-    // zeros for the active key range, reading each structure once. The
-    // caller synchronises afterwards and then calls reset_scalars().
-    template <bool EMIT, class Emit>
-    __device__ void flush_clear(Emit &emit) {
+    // Visits what the anchor touched: EMIT calls emit(key, count) for every
+    // key with count >= 2 (only valid without overflow); CLEAR returns the
+    // touched words and slots to zero. All threads call it; the caller
+    // synchronises afterwards, and after a CLEAR calls reset_scalars().
+    template <bool EMIT, bool CLEAR, class Emit>
+    __device__ void sweep(Emit &emit) {
         const int used = *(volatile int *)s_used;
-        const int hw = act_hw;
-        for (int w = threadIdx.x; w < hw; w += blockDim.x) {
-            uint32_t v = head[w];
-            if (v) {
-                head[w] = 0;
-                if (EMIT) {
-                    uint32_t c0 = v & 0xffffu, c1 = v >> 16;
-                    if (c0 >= 2) emit(2 * w, c0);
-                    if (c1 >= 2) emit(2 * w + 1, c1);
+        const int over = *(volatile int *)s_over;
+        // head: words [0, hw), four at a time
+        const int hw4 = (hw + 3) >> 2;
+        for (int i = threadIdx.x; i < hw4; i += blockDim.x) {
+            uint4 v = ((uint4 *)head)[i];
+            if ((v.x | v.y | v.z | v.w) == 0) continue;
+            if (CLEAR) ((uint4 *)head)[i] = make_uint4(0, 0, 0, 0);
+            if (EMIT) {
+                const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    const int w = 4 * i + e;
+                    const uint32_t c0 = vv[e] & 0xffffu, c1 = vv[e] >> 16;
+                    if (c0 >= 2) emit(w, c0);
+                    if (c1 >= 2) emit(w + hw, c1);
                 }
             }
         }
-        if (used > 0) {
-            for (int i = threadIdx.x; i < REPEAT_SLOTS; i += blockDim.x) {
-                int32_t k = rkey[i];
-                if (k != EMPTY_KEY) {
-                    if (EMIT) emit(k, 1u + rval[i]);
+        // tail bitmap: the words the current key range can use
+        if (CLEAR) {
+            const int bw4 = (act_bw + 3) >> 2;
+            for (int i = threadIdx.x; i < bw4; i += blockDim.x)
+                ((uint4 *)bm)[i] = make_uint4(0, 0, 0, 0);
+        }
+        if (over) {
+            if (CLEAR)
+                for (int i = threadIdx.x; i < REPEAT_SLOTS; i += blockDim.x) {
                     rkey[i] = EMPTY_KEY;
                     rval[i] = 0;
                 }
+        } else {
+            const int nl = used < REPEAT_LIMIT ? used : REPEAT_LIMIT;
+            for (int i = threadIdx.x; i < nl; i += blockDim.x) {
+                const int32_t h = rlist[i];
+                if (EMIT) emit(rkey[h], 1u + rval[h]);
+                if (CLEAR) {
+                    rkey[h] = EMPTY_KEY;
+                    rval[h] = 0;
+                }
             }
         }
-        uint4 z = make_uint4(0, 0, 0, 0);
-        for (int i = threadIdx.x; i < (act_bw >> 2); i += blockDim.x) ((uint4 *)bm)[i] = z;
-        for (int i = (act_bw & ~3) + threadIdx.x; i < act_bw; i += blockDim.x) bm[i] = 0;
+    }
+    template <bool EMIT, class Emit>
+    __device__ void flush_clear(Emit &emit) {
+        sweep<EMIT, true>(emit);
     }
     __device__ void reset_scalars() {
         if (threadIdx.x == 0) {
@@ -232,39 +282,126 @@ struct CtaHybrid {
             *s_over = 0;
         }
     }
-
-    // calls emit(key, count) for every key with count >= 2
-    template <class Emit>
-    __device__ void flush(Emit &emit) {
-        int hw = act_hw;
-        for (int w = threadIdx.x; w < hw; w += blockDim.x) {
-            uint32_t v = head[w];
-            if (v) {
-                uint32_t c0 = v & 0xffffu, c1 = v >> 16;
-                if (c0 >= 2) emit(2 * w, c0);
-                if (c1 >= 2) emit(2 * w + 1, c1);
-            }
-        }
-        for (int i = threadIdx.x; i < REPEAT_SLOTS; i += blockDim.x) {
-            int32_t k = rkey[i];
-            if (k != EMPTY_KEY) emit(k, 1u + rval[i]);
-        }
-    }
 };
 
-// smem bytes of a CtaHybrid for a key space (excluding the chunk arrays)
-inline size_t hybrid_bytes(int64_t keyspace, int32_t *headn_out, int32_t *bm_words_out) {
-    int64_t headn = keyspace < HEAD_MAX ? keyspace : HEAD_MAX;
-    headn = (headn + 1) & ~1ll;
-    int64_t tail = keyspace - headn;
-    if (tail < 0) tail = 0;
-    int64_t bmw = (tail + 31) / 32;
-    bmw = (bmw + 3) & ~3ll;
-    int64_t hw = ((headn >> 1) + 3) & ~3ll;
-    if (headn_out) *headn_out = (int32_t)headn;
-    if (bm_words_out) *bm_words_out = (int32_t)bmw;
-    return (size_t)(hw * 4 + bmw * 4 + (int64_t)REPEAT_SLOTS * 8);
+struct NoEmit {
+    __device__ void operator()(int32_t, uint32_t) {}
+};
+
+// Head and bitmap capacities for a key space (head = the first
+// min(keyspace, HEAD_MAX) keys).
+inline void hybrid_caps(int64_t keyspace, int32_t *head_cap, int32_t *bm_cap) {
+    int64_t h = keyspace < HEAD_MAX ? keyspace : HEAD_MAX;
+    int64_t tail = keyspace - h;
+    *head_cap = (int32_t)h;
+    *bm_cap = (int32_t)((tail + 31) / 32);
 }
+
+// shared-memory bytes of a CtaHybrid for a key space
+inline size_t hybrid_bytes(int64_t keyspace, int32_t *head_cap_out = nullptr,
+                           int32_t *bm_cap_out = nullptr) {
+    int32_t hc, bc;
+    hybrid_caps(keyspace, &hc, &bc);
+    if (head_cap_out) *head_cap_out = hc;
+    if (bm_cap_out) *bm_cap_out = bc;
+    return CtaHybrid::bytes(hc, bc);
+}
+
+// ------------------------------------------------------------------
+// Dense slice: 16-bit counters for every key of one key slice
+// ------------------------------------------------------------------
+// Key k < hw sits in the low half of word k, key k >= hw in the high half of
+// word k - hw (hw = half the slice), so consecutive keys of a sorted list hit
+// different words. The first increment of a word appends it to a touched
+// list (one shared atomic per warp and step), so flushing and clearing cost
+// what the slice touched; past the list's capacity the sweep scans the slice.
+// Counts must stay below 2^16 (the caller routes anchors of degree >= 65535
+// elsewhere).
+constexpr int DENSE_KEYS = 36864;               // keys per dense slice
+constexpr int DENSE_WORDS = DENSE_KEYS / 2;     // 18432 words (72 KB)
+constexpr int TOUCH_CAP = 8192;                 // touched-word list capacity
+
+struct DenseSlice {
+    uint32_t *cnt;     // DENSE_WORDS
+    uint16_t *tl;      // TOUCH_CAP
+    int *s_nt;         // shared scalar: touched words
+    int32_t hw;        // half of the current slice width (<= DENSE_WORDS)
+
+    static constexpr size_t bytes() { return (size_t)DENSE_WORDS * 4 + (size_t)TOUCH_CAP * 2; }
+    __device__ unsigned char *bind(unsigned char *base, int *nt) {
+        cnt = (uint32_t *)base;
+        tl = (uint16_t *)(cnt + DENSE_WORDS);
+        s_nt = nt;
+        hw = DENSE_WORDS;
+        return (unsigned char *)(tl + TOUCH_CAP);
+    }
+    __device__ void clear_all() {
+        for (int i = threadIdx.x; i < DENSE_WORDS / 4; i += blockDim.x)
+            ((uint4 *)cnt)[i] = make_uint4(0, 0, 0, 0);
+        if (threadIdx.x == 0) *s_nt = 0;
+    }
+    __device__ void set_width(int32_t w) { hw = (w + 1) >> 1; }
+    __device__ __forceinline__ void add(int32_t k) {
+        const bool hi = k >= hw;
+        const int32_t w = hi ? k - hw : k;
+        const uint32_t old = atomicAdd(&cnt[w], hi ? 0x10000u : 1u);
+        const unsigned m = __activemask();
+        const unsigned b = __ballot_sync(m, old == 0);
+        if (b) {
+            const int lane = threadIdx.x & 31;
+            const int leader = __ffs(b) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(s_nt, __popc(b));
+            base = __shfl_sync(m, base, leader);
+            if (old == 0) {
+                const int pos = base + __popc(b & lanemask_lt());
+                if (pos < TOUCH_CAP) tl[pos] = (uint16_t)w;
+            }
+        }
+    }
+    __device__ __forceinline__ uint32_t count(int32_t k) const {
+        const bool hi = k >= hw;
+        return (cnt[hi ? k - hw : k] >> (hi ? 16 : 0)) & 0xffffu;
+    }
+    // EMIT: emit(key, count) for every key with count >= 2; CLEAR: zero the
+    // touched words. The caller synchronises afterwards, then reset_scalars().
+    template <bool EMIT, bool CLEAR, class Emit>
+    __device__ void sweep(Emit &emit) {
+        const int nt = *(volatile int *)s_nt;
+        if (nt <= TOUCH_CAP) {
+            for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+                const int w = tl[i];
+                const uint32_t v = cnt[w];
+                if (CLEAR) cnt[w] = 0;
+                if (EMIT) {
+                    const uint32_t c0 = v & 0xffffu, c1 = v >> 16;
+                    if (c0 >= 2) emit(w, c0);
+                    if (c1 >= 2) emit(w + hw, c1);
+                }
+            }
+        } else {
+            const int hw4 = (hw + 3) >> 2;
+            for (int i = threadIdx.x; i < hw4; i += blockDim.x) {
+                uint4 v = ((uint4 *)cnt)[i];
+                if ((v.x | v.y | v.z | v.w) == 0) continue;
+                if (CLEAR) ((uint4 *)cnt)[i] = make_uint4(0, 0, 0, 0);
+                if (EMIT) {
+                    const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        const int w = 4 * i + e;
+                        const uint32_t c0 = vv[e] & 0xffffu, c1 = vv[e] >> 16;
+                        if (c0 >= 2) emit(w, c0);
+                        if (c1 >= 2) emit(w + hw, c1);
+                    }
+                }
+            }
+        }
+    }
+    __device__ void reset_scalars() {
+        if (threadIdx.x == 0) *s_nt = 0;
+    }
+};
 
 // ------------------------------------------------------------------
 // Global dense counters + touched list (one slot per CTA)
@@ -298,71 +435,88 @@ struct GlobalDense {
 // CTA traversal of one anchor's wedges
 // ------------------------------------------------------------------
 // Chunk staging in shared memory: up to MID_CHUNK middle vertices, their
-// segment starts and the exclusive prefix of segment lengths.
+// segment starts and lengths, and the exclusive prefix of their 32-wedge
+// piece counts.
 struct Chunk {
     int64_t *beg;    // MID_CHUNK
-    int32_t *pre;    // MID_CHUNK + 1
+    int32_t *pre;    // MID_CHUNK + 1: prefix of pieces
     int32_t *tmp;    // 33 (scan scratch)
+    int32_t *len;    // MID_CHUNK
 };
 
-constexpr size_t CHUNK_BYTES = MID_CHUNK * 8 + (MID_CHUNK + 1) * 4 + 33 * 4 + 12;
+constexpr size_t CHUNK_BYTES = MID_CHUNK * 8 + (MID_CHUNK + 1) * 4 + 33 * 4 + MID_CHUNK * 4 + 16;
 
-// Mids source contract:
-//   __device__ void seg(int64_t q, int64_t &beg, int32_t &len) const;
-// visit(k, key): k = mid index within the chunk, key = end point.
-// Returns the number of wedges walked. All threads of the CTA must call it.
+__device__ __forceinline__ int32_t *chunk_len_ptr(int32_t *tmp) { return tmp + 36; }
+
 struct NoChunkHook {
     __device__ void operator()(int64_t, int) {}
 };
 
+// Walks every wedge of one anchor: for q in [q0, q1) (middle vertices), the
+// segment M.seg(q) of `keys`. The segments of up to blockDim.x middle
+// vertices are staged at a time and cut into 32-wedge pieces; warps take
+// WALK_UNROLL consecutive pieces per step, locate each piece's segment once
+// (warp-uniform) and issue all their loads before visiting any key.
+// Mids source contract:
+//   __device__ void seg(int64_t q, int64_t &beg, int32_t &len) const;
+// visit(k, key): k = mid index within the chunk, key = end point.
+// Returns the number of wedges walked. All threads of the CTA must call it.
 template <class Mids, class Visit, class Hook = NoChunkHook>
 __device__ int64_t cta_walk(const Mids &M, int64_t q0, int64_t q1, const int32_t *__restrict__ keys,
                             Chunk &ch, Visit &visit, Hook *hook = nullptr) {
     int64_t walked = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int64_t c0 = q0; c0 < q1; c0 += blockDim.x) {
-        int nm = (int)imin64(blockDim.x, q1 - c0);
+        const int nm = (int)imin64(blockDim.x, q1 - c0);
         int64_t beg = 0;
         int32_t len = 0;
         if ((int)threadIdx.x < nm) M.seg(c0 + threadIdx.x, beg, len);
         int32_t total;
-        int32_t ex = block_exclusive_scan<int32_t>(len, ch.tmp, &total);
+        const int32_t pieces = (len + 31) >> 5;
+        int32_t ex = block_exclusive_scan<int32_t>(pieces, ch.tmp, &total);
         ch.beg[threadIdx.x] = beg;
+        ch.len[threadIdx.x] = len;
         ch.pre[threadIdx.x] = ex;
         if (threadIdx.x == 0) ch.pre[blockDim.x] = total;
+        int32_t wsum = len;
+        wsum = warp_sum(wsum);
         __syncthreads();
-        // Each warp takes WALK_UNROLL consecutive 32-wide slabs of the flat
-        // wedge index per step and issues all their loads before using any,
-        // so WALK_UNROLL independent L2 reads are in flight per warp.
-        for (int32_t base = warp * 32 * WALK_UNROLL; base < total;
-             base += nwarps * 32 * WALK_UNROLL) {
-            // largest k with pre[k] <= base (binary search, broadcast reads)
+        for (int32_t pb = warp * WALK_UNROLL; pb < total; pb += nwarps * WALK_UNROLL) {
+            // segment of piece pb: largest k with pre[k] <= pb (warp-uniform)
             int lo = 0, hi = nm - 1;
             while (lo < hi) {
                 int mid = (lo + hi + 1) >> 1;
-                if (ch.pre[mid] <= base)
+                if (ch.pre[mid] <= pb)
                     lo = mid;
                 else
                     hi = mid - 1;
             }
+            int k = lo;
             int kk[WALK_UNROLL];
             int32_t key[WALK_UNROLL];
-            int k = lo;
 #pragma unroll
             for (int u = 0; u < WALK_UNROLL; u++) {
-                int32_t j = base + u * 32 + lane;
+                const int32_t piece = pb + u;
                 kk[u] = -1;
-                if (j < total) {
-                    while (k + 1 < nm && ch.pre[k + 1] <= j) k++;
-                    kk[u] = k;
-                    key[u] = __ldg(keys + ch.beg[k] + (j - ch.pre[k]));
+                if (piece < total) {
+                    while (ch.pre[k + 1] <= piece) k++;
+                    const int32_t off = ((piece - ch.pre[k]) << 5) + lane;
+                    if (off < ch.len[k]) {
+                        kk[u] = k;
+                        key[u] = __ldg(keys + ch.beg[k] + off);
+                    }
                 }
             }
 #pragma unroll
             for (int u = 0; u < WALK_UNROLL; u++)
                 if (kk[u] >= 0) visit(kk[u], key[u]);
         }
-        walked += total;
+        // wedges of this chunk (sum of segment lengths)
+        if (lane == 0) ch.tmp[warp] = wsum;
+        __syncthreads();
+        int32_t cw = 0;
+        for (int w = 0; w < nwarps; w++) cw += ch.tmp[w];
+        walked += cw;
         __syncthreads();
         if (hook) {
             (*hook)(c0, nm);

@@ -195,31 +195,23 @@ struct FdVisit {
     }
 };
 
-__global__ void __launch_bounds__(FD_THREADS) k_fd_peel(FdArgs a, int32_t headn, int32_t bm_words) {
+__global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a, int32_t head_cap, int32_t bm_cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_t, s_used, s_over, s_nt, s_np, s_nk, s_nbig;
     __shared__ unsigned long long s_min[32];
     __shared__ int32_t s_tmp[33];
     CtaHybrid H;
-    size_t hw = (size_t)(((headn >> 1) + 3) & ~3);
-    H.head = (uint32_t *)smem;
-    H.bm = H.head + hw;
-    H.rkey = (int32_t *)(H.bm + bm_words);
-    H.rval = (uint32_t *)(H.rkey + REPEAT_SLOTS);
+    unsigned char *p = H.bind(smem, head_cap, bm_cap, &s_used, &s_over);
     Chunk ch;
-    ch.beg = (int64_t *)(H.rval + REPEAT_SLOTS);
+    ch.beg = (int64_t *)p;
     ch.pre = (int32_t *)(ch.beg + MID_CHUNK);
     ch.tmp = ch.pre + MID_CHUNK + 1;
+    ch.len = chunk_len_ptr(ch.tmp);
     // warp-private tables after the chunk staging
-    int32_t *wkey = (int32_t *)(((uintptr_t)(ch.tmp + 33) + 15) & ~(uintptr_t)15);
+    int32_t *wkey = (int32_t *)(((uintptr_t)(ch.len + MID_CHUNK) + 15) & ~(uintptr_t)15);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     WarpHash WH{wkey + warp * WARP_SLOTS, (uint32_t *)(wkey + nwarps * WARP_SLOTS) + warp * WARP_SLOTS};
     WH.clear(lane);
-    H.s_used = &s_used;
-    H.s_over = &s_over;
-    H.headn = headn;
-    H.bm_words = bm_words;
-    H.set_active((int64_t)headn + (int64_t)bm_words * 32);
     H.clear_all();
     GlobalDense G{a.gcnt ? a.gcnt + (size_t)blockIdx.x * a.gks : nullptr,
                   a.gtouch ? a.gtouch + (size_t)blockIdx.x * a.gks : nullptr, &s_nt};
@@ -251,9 +243,7 @@ __global__ void __launch_bounds__(FD_THREADS) k_fd_peel(FdArgs a, int32_t headn,
             alist[r] = r;
         }
         const bool small = ni <= a.cta_ks;
-        if (small) {
-            H.set_active(ni);
-        }
+        if (small) H.set_range((int32_t)imin64(head_cap, ni), ni);
         int32_t nalive = ni;
         unsigned long long level = 0;
         __syncthreads();
@@ -461,9 +451,9 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
     for (int i = 0; i < P; i++) maxn = std::max(maxn, hms[i + 1] - hms[i]);
     const size_t warp_tables = (size_t)(FD_THREADS / 32) * WARP_SLOTS * 8 + 16;
     const int64_t cta_ks = max_cta_keyspace(maxn, CHUNK_BYTES + warp_tables);
-    int32_t headn = 0, bmw = 0;
+    int32_t head_cap = 0, bm_cap = 0;
     size_t smem =
-        hybrid_bytes(std::max<int64_t>(cta_ks, 2), &headn, &bmw) + CHUNK_BYTES + warp_tables;
+        hybrid_bytes(std::max<int64_t>(cta_ks, 2), &head_cap, &bm_cap) + CHUNK_BYTES + warp_tables;
     RC_CUDA(cudaFuncSetAttribute(k_fd_peel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
     RC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fd_peel, FD_THREADS, smem));
@@ -486,7 +476,7 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
              D.init,        fsup.get(),  alive.get(),     alist.get(),  plist.get(), blist.get(),
              (unsigned long long *)d_tip, stats.get(),    sub_ns.get(), sub_lv.get(),
              gcnt.get(),    gtouch.get(), (int64_t)maxn, (int32_t)cta_ks};
-    k_fd_peel<<<grid, FD_THREADS, smem, s>>>(a, headn, bmw);
+    k_fd_peel<<<grid, FD_THREADS, smem, s>>>(a, head_cap, bm_cap);
     RC_LAUNCH();
     unsigned long long hs[2] = {0, 0};
     RC_CUDA(cudaMemcpyAsync(hs, stats.get(), sizeof(hs), cudaMemcpyDeviceToHost, s));
