@@ -164,6 +164,30 @@ receipt_status receipt_count_butterflies(receipt_graph *g, uint64_t *d_cnt_u,
                                          uint64_t *d_cnt_v, void *stream);
 
 /*
+ * receipt_count_butterflies without any device allocation. The paper has no
+ * counterpart: this entry point exists for callers that must not allocate
+ * device memory while they run -- for example a serving loop that reserved
+ * all of its memory at start-up, or a host framework whose own allocator owns
+ * the device -- because cudaMalloc/cudaFree can synchronise the device and
+ * fail under a fixed memory budget.
+ *   Same arguments, layout and results as receipt_count_butterflies; the
+ *   graph must have at most 65,536 vertices on each side and at most
+ *   1,048,576 edges (after duplicate removal), else RECEIPT_ERR_INVALID with
+ *   a message naming the limits.
+ *   Every temporary lives in one fixed array of about 11 MB inside the
+ *   library's device image, held on every GPU that loads the library until
+ *   the process exits. The first call on a device looks up that array's
+ *   device address; make that first call before any stream capture.
+ *   All calls share the array and it keeps the previous call's contents
+ *   (the call re-zeroes what must start at zero): calls that can overlap on
+ *   the GPU -- on different streams or from different threads -- race and
+ *   must be serialised by the caller. Enqueued on `stream` with no host
+ *   synchronisation; the graph's stats are not updated.
+ */
+receipt_status receipt_count_butterflies_noalloc(receipt_graph *g, uint64_t *d_cnt_u,
+                                                 uint64_t *d_cnt_v, void *stream);
+
+/*
  * Tip decomposition of one side (Algorithms 3 and 4): tip number theta_x of
  * every vertex x of `side`, i.e. the largest k such that x lies in a k-tip
  * (Definition 1).

@@ -91,6 +91,8 @@ def load(build_if_missing: bool = True):
         lib.receipt_graph_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                            ctypes.POINTER(i64)]
         lib.receipt_count_butterflies.argtypes = [vp, vp, vp, vp]
+        lib.receipt_count_butterflies_noalloc.argtypes = [vp, vp, vp, vp]
+        lib.receipt_count_butterflies_noalloc.restype = ctypes.c_int
         lib.receipt_tip_decompose.argtypes = [vp, ctypes.c_int, vp, ctypes.POINTER(Options), vp]
         lib.receipt_decompose_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int),
                                                 i32, ctypes.POINTER(vp), ctypes.POINTER(Options), vp]
@@ -168,6 +170,14 @@ def receipt_build_csr(eu, ev, nu: int, nv: int, dedup: bool = True, stream=None)
 def receipt_count_butterflies(handle, cnt_u, cnt_v, stream=None):
     _check(load().receipt_count_butterflies(handle, _dptr(cnt_u), _dptr(cnt_v),
                                             _stream_handle(stream)))
+
+
+def receipt_count_butterflies_noalloc(handle, cnt_u, cnt_v, stream=None):
+    """Butterfly counts into caller tensors without any device allocation
+    (graphs up to 65,536 vertices per side and 1,048,576 edges; calls that may
+    overlap on the GPU must be serialised by the caller)."""
+    _check(load().receipt_count_butterflies_noalloc(handle, _dptr(cnt_u), _dptr(cnt_v),
+                                                    _stream_handle(stream)))
 
 
 def receipt_tip_decompose(handle, side: int, tip, options=None, stream=None):

@@ -441,6 +441,16 @@ receipt_status receipt_count_butterflies(receipt_graph *g, uint64_t *d_cnt_u, ui
     });
 }
 
+receipt_status receipt_count_butterflies_noalloc(receipt_graph *g, uint64_t *d_cnt_u,
+                                                 uint64_t *d_cnt_v, void *stream) {
+    return guarded([&] {
+        if (!g) fail(RECEIPT_ERR_INVALID, "null graph");
+        DeviceGuard dg(g->device);
+        count_noalloc(g, (unsigned long long *)d_cnt_u, (unsigned long long *)d_cnt_v,
+                      (cudaStream_t)stream);
+    });
+}
+
 receipt_status receipt_tip_decompose(receipt_graph *g, receipt_side side, uint64_t *d_tip,
                                      const receipt_options *opt, void *stream) {
     return guarded([&] {

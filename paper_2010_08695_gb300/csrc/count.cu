@@ -17,6 +17,8 @@
 #include "internal.cuh"
 
 #include <algorithm>
+#include <mutex>
+#include <string>
 
 namespace receipt {
 
@@ -407,6 +409,153 @@ void scatter_to_original(const unsigned long long *local, const int32_t *new2old
     if (n <= 0) return;
     k_scatter_counts<<<ceil_div(n, 256), 256, 0, s>>>(local, new2old, n, out);
     RC_LAUNCH();
+}
+
+}  // namespace receipt
+
+// ---------------------------------------------------------------------
+// Butterfly counting that allocates no device memory
+// ---------------------------------------------------------------------
+// Every temporary of the counting pass (local counts, prefix lengths, tier
+// lists, work counters and the global-tier counter slots) is carved out of
+// one statically sized array in this library's device image, so the call
+// makes no cudaMalloc/cudaFree and no allocating library call. The array's
+// size fixes the largest graph it accepts.
+namespace receipt {
+
+namespace {
+
+constexpr int32_t NOALLOC_MAX_SIDE = 65536;   // vertices per side
+constexpr int64_t NOALLOC_MAX_M = 1 << 20;    // edges (after duplicate removal)
+constexpr int NOALLOC_GSLOTS = 8;             // CTAs of the global-counter tier
+
+constexpr size_t na_round(size_t b) { return (b + 255) & ~(size_t)255; }
+constexpr size_t NA_CNT = na_round(8 * (size_t)NOALLOC_MAX_SIDE);
+constexpr size_t NA_PLEN = na_round(4 * (size_t)NOALLOC_MAX_M);
+constexpr size_t NA_LIST = na_round(4 * (size_t)NOALLOC_MAX_SIDE);
+constexpr size_t NA_GLOB = na_round(4 * (size_t)NOALLOC_GSLOTS * NOALLOC_MAX_SIDE);
+constexpr size_t NA_MISC = 256;
+constexpr size_t NOALLOC_BYTES = 2 * NA_CNT + NA_PLEN + 4 * NA_LIST + 2 * NA_GLOB + NA_MISC;
+
+// ~11 MB per device, held from module load until the process exits.
+static __device__ __align__(256) unsigned char g_count_scratch[NOALLOC_BYTES];
+
+std::mutex g_na_mu;
+void *g_na_ptr[64] = {nullptr};
+
+// Device address of the scratch array for the current device; looked up once
+// per device (host code may not use the symbol itself as an address).
+unsigned char *noalloc_scratch() {
+    int d = 0;
+    RC_CUDA(cudaGetDevice(&d));
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    if (!g_na_ptr[d & 63]) {
+        void *p = nullptr;
+        RC_CUDA(cudaGetSymbolAddress(&p, g_count_scratch));
+        g_na_ptr[d & 63] = p;
+    }
+    return (unsigned char *)g_na_ptr[d & 63];
+}
+
+// Wedge count W(sp) of every start point summed directly from its prefix
+// lengths (one warp per start point), then the same tier split as above.
+__global__ void k_count_tiers_direct(const int64_t *__restrict__ offA, const int32_t *__restrict__ plen,
+                                     int32_t nA, int64_t cta_keyspace_max, int32_t *__restrict__ lw,
+                                     int32_t *__restrict__ lc, int32_t *__restrict__ lg,
+                                     int32_t *__restrict__ nl) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t sp = warp; sp < nA; sp += nwarps) {
+        const int64_t b = offA[sp], e = offA[sp + 1];
+        int64_t W = 0;
+        for (int64_t q = b + lane; q < e; q += 32) W += plen[q];
+        W = warp_sum(W);
+        if (lane == 0 && W > 0) {
+            const int64_t deg = e - b;
+            if (W <= WARP_MAX_W)
+                lw[atomicAdd(&nl[0], 1)] = (int32_t)sp;
+            else if (deg < 65535 && sp <= cta_keyspace_max)
+                lc[atomicAdd(&nl[1], 1)] = (int32_t)sp;
+            else
+                lg[atomicAdd(&nl[2], 1)] = (int32_t)sp;
+        }
+    }
+}
+
+}  // namespace
+
+void count_noalloc(const receipt_graph *g, unsigned long long *d_cnt_u,
+                   unsigned long long *d_cnt_v, cudaStream_t s) {
+    if (g->nu > NOALLOC_MAX_SIDE || g->nv > NOALLOC_MAX_SIDE || g->m > NOALLOC_MAX_M)
+        fail(RECEIPT_ERR_INVALID,
+             "graph exceeds the limits of receipt_count_butterflies_noalloc (at most " +
+                 std::to_string(NOALLOC_MAX_SIDE) + " vertices per side and " +
+                 std::to_string(NOALLOC_MAX_M) + " edges; got " + std::to_string(g->nu) + " x " +
+                 std::to_string(g->nv) + " with " + std::to_string(g->m) + " edges)");
+    unsigned char *base = noalloc_scratch();
+    unsigned long long *cnt[2] = {(unsigned long long *)base,
+                                  (unsigned long long *)(base + NA_CNT)};
+    unsigned char *p = base + 2 * NA_CNT;
+    int32_t *plen = (int32_t *)p;
+    p += NA_PLEN;
+    int32_t *lw = (int32_t *)p, *lc = (int32_t *)(p + NA_LIST), *lg = (int32_t *)(p + 2 * NA_LIST),
+            *lo = (int32_t *)(p + 3 * NA_LIST);
+    p += 4 * NA_LIST;
+    uint32_t *gcnt = (uint32_t *)p;
+    int32_t *gtouch = (int32_t *)(p + NA_GLOB);
+    p += 2 * NA_GLOB;
+    int32_t *ctr = (int32_t *)p;  // [8 * side + 0..7]
+    // the array keeps the previous call's contents: zero what must start at 0
+    RC_CUDA(cudaMemsetAsync(cnt[0], 0, 8 * (size_t)(g->nu > 0 ? g->nu : 1), s));
+    RC_CUDA(cudaMemsetAsync(cnt[1], 0, 8 * (size_t)(g->nv > 0 ? g->nv : 1), s));
+    RC_CUDA(cudaMemsetAsync(ctr, 0, 16 * sizeof(int32_t), s));
+    RC_CUDA(cudaMemsetAsync(gcnt, 0, NA_GLOB, s));
+    const int64_t m = g->m;
+    const int sms = num_sms();
+    if (m > 0) {
+        for (int A = 0; A < 2; A++) {
+            const Side &SA = g->side[A];
+            const Side &SB = g->side[1 - A];
+            const int32_t nA = SA.n;
+            if (nA == 0) continue;
+            int32_t *nl = ctr + 8 * A;  // [0] warp [1] cta [2] global [3] overflow, [4..7] work
+            k_prefix_len<<<ceil_div(m, 256), 256, 0, s>>>(SA.off, SA.adj, nA, SB.off, SB.adj,
+                                                          SB.below, m, plen);
+            RC_LAUNCH();
+            const int64_t cta_ks_max = max_cta_keyspace(nA, MID_CHUNK * 8 + CHUNK_BYTES);
+            int32_t head_cap = 0, bm_cap = 0;
+            size_t smem = cta_ks_max > 0 ? count_cta_smem(cta_ks_max, &head_cap, &bm_cap) : 0;
+            k_count_tiers_direct<<<std::min(ceil_div((int64_t)nA * 32, 256), sms * 16), 256, 0, s>>>(
+                SA.off, plen, nA, cta_ks_max, lw, lc, lg, nl);
+            RC_LAUNCH();
+            unsigned long long *cA = cnt[A], *cB = cnt[1 - A];
+            CountArgs a{SA.off, SA.adj, SB.off, SB.adj, plen, cA, cB, lw, nl + 0, nl + 4};
+            k_count_warp<<<sms * 8, 256, 0, s>>>(a);
+            RC_LAUNCH();
+            if (cta_ks_max > 0) {
+                RC_CUDA(cudaFuncSetAttribute(k_count_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem));
+                CountArgs c = a;
+                c.list = lc;
+                c.nlist = nl + 1;
+                c.work = nl + 5;
+                k_count_cta<<<sms, CTA_THREADS, smem, s>>>(c, head_cap, bm_cap, lo, nl + 3);
+                RC_LAUNCH();
+            }
+            CountArgs c = a;
+            c.list = lg;
+            c.nlist = nl + 2;
+            c.work = nl + 6;
+            const size_t gsm = MID_CHUNK * 8 + CHUNK_BYTES;
+            RC_CUDA(cudaFuncSetAttribute(k_count_global, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)gsm));
+            k_count_global<<<NOALLOC_GSLOTS, CTA_THREADS, gsm, s>>>(c, lo, nl + 3, gcnt, gtouch, nA);
+            RC_LAUNCH();
+        }
+    }
+    if (d_cnt_u) scatter_to_original(cnt[0], g->side[0].new2old, g->nu, d_cnt_u, s);
+    if (d_cnt_v) scatter_to_original(cnt[1], g->side[1].new2old, g->nv, d_cnt_v, s);
 }
 
 }  // namespace receipt

@@ -14,6 +14,9 @@ uint64_t count_local(const receipt_graph *g, unsigned long long *cnt_u, unsigned
                      cudaStream_t s);
 void scatter_to_original(const unsigned long long *local, const int32_t *new2old, int32_t n,
                          unsigned long long *out, cudaStream_t s);
+// Counting with every temporary in a static device array (no allocation).
+void count_noalloc(const receipt_graph *g, unsigned long long *d_cnt_u,
+                   unsigned long long *d_cnt_v, cudaStream_t s);
 
 // Largest key space whose CtaHybrid engine plus `extra` bytes fits in the
 // opt-in shared memory of one CTA (capped at `want`); 0 if none.
