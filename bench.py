@@ -328,6 +328,139 @@ def run_ours(args):
     return 0
 
 
+def _gen_spec(spec):
+    import synth
+    eu, ev = synth.graph_from_spec(spec)
+    return eu, ev
+
+
+def _generate(specs, workers=None):
+    """Draws the graphs of a batch/serving spec list in parallel host processes."""
+    import multiprocessing as mp
+    workers = workers or max(1, min(16, os.cpu_count() or 1))
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(_gen_spec, specs, chunksize=4)
+
+
+def run_batch(args):
+    """Batched workload: 4,096 graphs (seed 4), U side, one packed
+    decomposition versus one decomposition per graph on the same GPU."""
+    import torch
+    import synth
+    specs = synth.batch_specs(args.batch_graphs, seed=4)
+    graphs = _generate(specs)
+    import paper_2010_08695_gb300 as R
+    R.load()
+    built = [R.Graph(eu, ev, s.nu, s.nv) for (eu, ev), s in zip(graphs, specs)]
+    sides = [0] * len(built)
+    torch.cuda.synchronize()
+    edges = sum(g.m for g in built)
+    wedges = 0
+    for (eu, ev), s in zip(graphs, specs):
+        dv = np.bincount(ev, minlength=s.nv).astype(np.int64)
+        wedges += int((dv * (dv - 1)).sum())
+    outs = R.receipt_decompose_batch(built, sides)  # warm-up
+    torch.cuda.synchronize()
+    tb = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        outs = R.receipt_decompose_batch(built, sides, outs=outs)
+        torch.cuda.synchronize()
+        tb.append(time.perf_counter() - t0)
+    batch_stats = built[0].stats()
+    alone = [torch.empty_like(o) for o in outs]
+    for g, o in zip(built[:64], alone[:64]):  # warm-up
+        g.tip_decompose(0, out=o)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for g, o in zip(built, alone):
+        g.tip_decompose(0, out=o)
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    same = all(torch.equal(a, b) for a, b in zip(outs, alone))
+    import oracle
+    sample = list(range(0, len(built), max(1, len(built) // 16)))
+    oracle_ok = all(np.array_equal(R.as_u64(outs[i]), oracle.bup(graphs[i][0], graphs[i][1],
+                                                                  specs[i].nu, specs[i].nv, 0)[0])
+                    for i in sample)
+    tbm = statistics.median(tb)
+    line = {"metric": "graphs/s (batched tip decomposition)", "value": len(built) / tbm,
+            "unit": "graphs/s", "n_gpus": 1, "steps": args.steps, "higher_is_better": True,
+            "config": {"workload": f"{len(built)} Chung-Lu graphs, seed 4, U side",
+                       "edges": edges, "wedges_bup": wedges},
+            "seconds_batched": tbm, "seconds_one_graph_per_launch": t_plain,
+            "graphs_per_s_one_graph_per_launch": len(built) / t_plain,
+            "speedup_vs_one_graph_per_launch": t_plain / tbm,
+            "wedges_per_s_batched": wedges / tbm,
+            "rounds_cd": batch_stats["rounds_cd"], "subsets": batch_stats["p_eff"],
+            "batch_equals_alone": same, "oracle_sample_ok": oracle_ok,
+            "oracle_sample": len(sample)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Serving workload: a bounded prefix of the seed-5 request stream
+    (Poisson arrivals at 0.8x the measured one-at-a-time throughput, and a
+    flood with every request at t=0), latency p50/p99 and graphs/s."""
+    import torch
+    import synth
+    specs = synth.serve_specs(args.serve_requests, seed=5)
+    graphs = _generate(specs)
+    import paper_2010_08695_gb300 as R
+    R.load()
+    reqs = [(eu, ev, s.nu, s.nv, s.side) for (eu, ev), s in zip(graphs, specs)]
+    edges = sum(len(r[0]) for r in reqs)
+    # plain path: one request at a time through the host-buffer entry point
+    calib = reqs[: min(len(reqs), args.serve_calib)]
+    R.receipt_tip_decompose_host(*calib[0])
+    t0 = time.perf_counter()
+    for r in calib:
+        R.receipt_tip_decompose_host(*r)
+    plain_rate = len(calib) / (time.perf_counter() - t0)
+    results = {}
+    for mode in ("poisson", "flood"):
+        sv = R.Server(max_inflight=args.serve_slots)
+        arrivals = (synth.poisson_arrivals(len(reqs), 0.8 * plain_rate, seed=5)
+                    if mode == "poisson" else np.zeros(len(reqs)))
+        start = time.perf_counter()
+        ids = []
+        for r, t_arr in zip(reqs, arrivals):
+            dt = start + t_arr - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            ids.append(sv.submit(*r)[0])
+        outs = [sv.wait(i)[0] for i in ids]
+        st = sv.stats()
+        sv.close()
+        results[mode] = (st, outs)
+    st_p, outs_p = results["poisson"]
+    st_f, outs_f = results["flood"]
+    same = all(np.array_equal(a, b) for a, b in zip(outs_p, outs_f))
+    alone_idx = list(range(0, len(reqs), max(1, len(reqs) // 20)))
+    alone_ok = all(np.array_equal(outs_p[i], R.receipt_tip_decompose_host(*reqs[i]))
+                   for i in alone_idx)
+    import oracle
+    small = [i for i in range(len(reqs)) if len(reqs[i][0]) <= 200000][:10]
+    oracle_ok = all(np.array_equal(outs_p[i], oracle.bup(*reqs[i])[0]) for i in small)
+
+    def pick(st):
+        return {k: st[k] for k in ("p50_ms", "p99_ms", "mean_ms", "max_ms", "graphs_per_s",
+                                   "completed", "batches", "packed_requests", "peak_inflight",
+                                   "peak_inflight_bytes")}
+    line = {"metric": "graphs/s and p50/p99 latency (serving)", "value": st_p["graphs_per_s"],
+            "unit": "graphs/s", "n_gpus": 1, "higher_is_better": True,
+            "config": {"workload": f"first {len(reqs)} requests of the seed-5 stream",
+                       "edges": edges, "slots": args.serve_slots,
+                       "arrival_rate_per_s": 0.8 * plain_rate},
+            "plain_one_at_a_time_graphs_per_s": plain_rate,
+            "poisson": pick(st_p), "flood": pick(st_f),
+            "mix_equals_alone_sample": alone_ok, "poisson_equals_flood": same,
+            "oracle_sample_ok": oracle_ok, "oracle_sample": len(small)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -337,9 +470,20 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--trace", default=None,
                     help="write the per-round trace of the last timed step to this JSON file")
+    ap.add_argument("--workload", choices=["single", "batch", "serve"], default="single",
+                    help="single: the 10M-edge graph (default); batch: 4,096 graphs packed "
+                         "vs one per launch; serve: the serving stream prefix")
+    ap.add_argument("--batch-graphs", type=int, default=4096)
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-calib", type=int, default=40)
+    ap.add_argument("--serve-slots", type=int, default=4)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

@@ -222,6 +222,72 @@ receipt_status receipt_tip_decompose_host(const int32_t *h_eu, const int32_t *h_
                                           uint64_t *h_tip, const receipt_options *opt,
                                           void *stream);
 
+/* ---------------------------------------------------------------------
+ * Serving engine (continuous batching). Not in the paper: it serves many
+ * independent decompositions as they arrive. Requests are admitted in
+ * arrival order while the device-memory estimate of what is running fits the
+ * budget (the oldest request is always admitted when nothing runs); each
+ * admitted unit runs on one of `max_inflight` worker streams, so requests
+ * that arrive while others are on the GPU overlap with them; requests with at
+ * most `batch_max_edges` edges that are waiting together are packed into one
+ * disjoint-union decomposition (receipt_decompose_batch). A request's graph
+ * and supports stay resident on the device only while it runs.
+ * --------------------------------------------------------------------- */
+typedef struct receipt_server receipt_server;
+
+typedef struct {
+    int32_t max_inflight;     /* worker streams (units running at once); 0 = 4        */
+    int32_t P;                /* subsets per decomposition; 0 = 150                   */
+    int64_t mem_budget_bytes; /* device bytes admitted units may hold; 0 = 80% of the
+                                 free memory when the server is created              */
+    int32_t batch_max_edges;  /* requests with at most this many edges may be packed;
+                                 0 = never pack (default 200,000)                      */
+    int32_t batch_max_graphs; /* at most this many requests per packed unit (64)      */
+} receipt_server_config;
+
+typedef struct {
+    int64_t submitted, completed, failed;
+    int64_t batches;          /* packed units of more than one request                */
+    int64_t packed_requests;  /* requests that ran inside such units                  */
+    int32_t peak_inflight;    /* most units running at once                           */
+    int32_t reserved;
+    int64_t peak_inflight_bytes, budget_bytes;
+    double p50_ms, p99_ms, mean_ms, max_ms; /* submit -> tips in the caller's buffer  */
+    double graphs_per_s;      /* completed / (last completion - first submit)         */
+} receipt_server_stats;
+
+/* Fills the defaults (max_inflight 4, P 150, budget 0 = 80% of free memory,
+ * batch_max_edges 200,000, batch_max_graphs 64). */
+void receipt_server_config_default(receipt_server_config *cfg);
+
+/* Creates a server on the current device and starts its worker threads. */
+receipt_status receipt_server_create(const receipt_server_config *cfg, receipt_server **out);
+
+/*
+ * Queues one decomposition and returns at once with its id. h_eu/h_ev (m
+ * int32 edges, original ids) and h_tip (uint64[n_side] output by original id)
+ * are the caller's host buffers and must stay valid until receipt_server_wait
+ * returns for this id. RECEIPT_ERR_BUSY once the server is shutting down.
+ */
+receipt_status receipt_server_submit(receipt_server *sv, const int32_t *h_eu, const int32_t *h_ev,
+                                     int64_t m, int32_t nu, int32_t nv, receipt_side side,
+                                     uint64_t *h_tip, int64_t *request_id);
+
+/*
+ * Waits for a request (timeout_s <= 0: no limit; on timeout returns
+ * RECEIPT_ERR_TIMEOUT and the request keeps running), then reports its own
+ * status and its latency from submit to completion and forgets the id.
+ */
+receipt_status receipt_server_wait(receipt_server *sv, int64_t request_id, double timeout_s,
+                                   int32_t *request_status, double *latency_ms);
+
+/* Latency percentiles, throughput and admission counters so far. */
+receipt_status receipt_server_get_stats(receipt_server *sv, receipt_server_stats *out);
+
+/* Stops the workers after the units they are running; unstarted requests are
+ * dropped. */
+receipt_status receipt_server_destroy(receipt_server *sv);
+
 /* Counters of the last count/decompose call on g. */
 receipt_status receipt_get_stats(const receipt_graph *g, receipt_stats *out);
 

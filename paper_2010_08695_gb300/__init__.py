@@ -67,6 +67,22 @@ class Round(ctypes.Structure):
                 ("ms", ctypes.c_float * 4)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("max_inflight", ctypes.c_int32), ("P", ctypes.c_int32),
+                ("mem_budget_bytes", ctypes.c_int64), ("batch_max_edges", ctypes.c_int32),
+                ("batch_max_graphs", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("packed_requests", ctypes.c_int64), ("peak_inflight", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("peak_inflight_bytes", ctypes.c_int64),
+                ("budget_bytes", ctypes.c_int64), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("graphs_per_s", ctypes.c_double)]
+
+
 def lib_path() -> str:
     return _LIB_PATH
 
@@ -104,6 +120,17 @@ def load(build_if_missing: bool = True):
         lib.receipt_kernel_launches.restype = ctypes.c_uint64
         lib.receipt_get_trace.argtypes = [vp, ctypes.POINTER(Round), i32, ctypes.POINTER(i32)]
         lib.receipt_get_trace.restype = ctypes.c_int
+        lib.receipt_server_config_default.argtypes = [ctypes.POINTER(ServerConfig)]
+        lib.receipt_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
+        lib.receipt_server_submit.argtypes = [vp, vp, vp, i64, i32, i32, ctypes.c_int, vp,
+                                              ctypes.POINTER(i64)]
+        lib.receipt_server_wait.argtypes = [vp, i64, ctypes.c_double, ctypes.POINTER(i32),
+                                            ctypes.POINTER(ctypes.c_double)]
+        lib.receipt_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+        lib.receipt_server_destroy.argtypes = [vp]
+        for f in ("receipt_server_create", "receipt_server_submit", "receipt_server_wait",
+                  "receipt_server_get_stats", "receipt_server_destroy"):
+            getattr(lib, f).restype = ctypes.c_int
         for f in ("receipt_build_csr", "receipt_graph_destroy", "receipt_graph_info",
                   "receipt_count_butterflies", "receipt_tip_decompose",
                   "receipt_decompose_batch", "receipt_tip_decompose_host", "receipt_get_stats"):
@@ -310,3 +337,61 @@ def receipt_tip_decompose_host(eu, ev, nu: int, nv: int, side: int, P: int = 150
 def as_u64(t) -> np.ndarray:
     """Device int64 tensor of exact counts -> host numpy uint64 (same bits)."""
     return t.cpu().numpy().view(np.uint64)
+
+
+class Server:
+    """Continuous-batching serving engine (receipt_server_*): submit host
+    edge lists as requests arrive, wait for their tip numbers."""
+
+    def __init__(self, max_inflight=4, P=150, mem_budget_bytes=0, batch_max_edges=200000,
+                 batch_max_graphs=64):
+        lib = load()
+        cfg = ServerConfig()
+        lib.receipt_server_config_default(ctypes.byref(cfg))
+        cfg.max_inflight, cfg.P = int(max_inflight), int(P)
+        cfg.mem_budget_bytes = int(mem_budget_bytes)
+        cfg.batch_max_edges, cfg.batch_max_graphs = int(batch_max_edges), int(batch_max_graphs)
+        self._h = ctypes.c_void_p()
+        _check(lib.receipt_server_create(ctypes.byref(cfg), ctypes.byref(self._h)))
+        self._keep = {}
+
+    def submit(self, eu, ev, nu: int, nv: int, side: int):
+        """Queues a decomposition; returns (request id, host output array)."""
+        eu = np.ascontiguousarray(eu, dtype=np.int32)
+        ev = np.ascontiguousarray(ev, dtype=np.int32)
+        out = np.zeros(nu if side == SIDE_U else nv, np.uint64)
+        rid = ctypes.c_int64()
+        _check(load().receipt_server_submit(self._h, eu.ctypes.data_as(ctypes.c_void_p),
+                                            ev.ctypes.data_as(ctypes.c_void_p), len(eu), int(nu),
+                                            int(nv), int(side),
+                                            out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(rid)))
+        self._keep[rid.value] = (eu, ev, out)
+        return rid.value, out
+
+    def wait(self, rid: int, timeout_s: float = 0.0):
+        """Waits for a request; returns (tips, latency_ms). Raises on failure."""
+        st = ctypes.c_int32()
+        lat = ctypes.c_double()
+        _check(load().receipt_server_wait(self._h, int(rid), float(timeout_s), ctypes.byref(st),
+                                          ctypes.byref(lat)))
+        eu, ev, out = self._keep.pop(rid)
+        if st.value != RECEIPT_OK:
+            raise ReceiptError(st.value, receipt_last_error())
+        return out, lat.value
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(load().receipt_server_get_stats(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_ if k != "reserved"}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().receipt_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

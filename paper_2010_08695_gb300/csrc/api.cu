@@ -6,6 +6,8 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <set>
+#include <utility>
 
 #include "internal.cuh"
 
@@ -60,8 +62,45 @@ DevInfo &dev_info() {
 }
 }  // namespace
 
+namespace {
+struct PinnedTLS {
+    void *p = nullptr;
+    size_t n = 0;
+    ~PinnedTLS() {
+        if (p) cudaFreeHost(p);
+    }
+};
+thread_local PinnedTLS g_pinned;
+}  // namespace
+
+void *pinned_scratch(size_t bytes) {
+    if (g_pinned.n < bytes) {
+        if (g_pinned.p) cudaFreeHost(g_pinned.p);
+        g_pinned.p = nullptr;
+        g_pinned.n = 0;
+        size_t want = bytes < 4096 ? 4096 : bytes;
+        RC_CUDA(cudaMallocHost(&g_pinned.p, want));
+        g_pinned.n = want;
+    }
+    return g_pinned.p;
+}
+
 int num_sms() { return dev_info().sms; }
 int max_smem_optin() { return dev_info().smem_optin - 1024; }
+void allow_max_smem(const void *kernel) {
+    static std::mutex mu;
+    static std::set<std::pair<int, const void *>> done;
+    const int optin = dev_info().smem_optin;
+    int d = 0;
+    RC_CUDA(cudaGetDevice(&d));
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count({d, kernel})) return;
+    cudaFuncAttributes fa;
+    RC_CUDA(cudaFuncGetAttributes(&fa, kernel));
+    RC_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)fa.sharedSizeBytes));
+    done.insert({d, kernel});
+}
 
 void compute_wfull(const Side &S, const Side &O, int64_t m, unsigned long long *wfull,
                    cudaStream_t s);
@@ -138,6 +177,7 @@ void tip_decompose_impl(receipt_graph *g, int side, uint64_t *d_tip, const recei
     D.n = n;
     D.m = g->m;
     D.timing = opt.timing != 0;
+    D.max_deg_s = g->max_deg[side];
     DevBuf<unsigned long long> cu(g->nu, s), cv(g->nv, s), init(n, s), wfull(n, s);
     DevBuf<int32_t> sub(n, s);
     DevBuf<unsigned long long> wbup(1, s);

@@ -618,8 +618,7 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
         RC_LAUNCH();
     }
     const size_t smem_slice = DenseSlice::bytes() + CHUNK_BYTES;
-    RC_CUDA(cudaFuncSetAttribute(k_cd_update_slice, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_slice));
+    allow_max_smem((const void *)k_cd_update_slice);
     int occ_s = 1;
     RC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, k_cd_update_slice, SLICE_THREADS,
                                                           smem_slice));
@@ -630,24 +629,20 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
     const bool cta_ok = max_cta_keyspace(n, chunk_extra) >= n;
     size_t smem_cta = cta_ok ? hybrid_bytes(n, &head_cap, &bm_cap) + chunk_extra : 0;
     if (cta_ok)
-        RC_CUDA(cudaFuncSetAttribute(k_cd_update_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem_cta));
-    const int gblocks = std::max(1, sms / 2);
-    DevBuf<uint32_t> gcnt((size_t)gblocks * n, s);
-    DevBuf<int32_t> gtouch((size_t)gblocks * n, s);
+        allow_max_smem((const void *)k_cd_update_cta);
+    // global-counter slots only exist if the side has a hub whose counts can
+    // exceed 16 bits (degree >= 65535)
+    const bool hubs = D.max_deg_s >= 65535;
+    const int gblocks = hubs ? std::max(1, sms / 2) : 1;
+    DevBuf<uint32_t> gcnt((size_t)gblocks * (hubs ? n : 1), s);
+    DevBuf<int32_t> gtouch((size_t)gblocks * (hubs ? n : 1), s);
     gcnt.zero();
     const size_t smem_glob = chunk_extra;
-    RC_CUDA(cudaFuncSetAttribute(k_cd_update_global, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_glob));
-    unsigned long long *hpin = nullptr;
-    RC_CUDA(cudaMallocHost((void **)&hpin, 64 + sizeof(CdDev)));
+    allow_max_smem((const void *)k_cd_update_global);
+    unsigned long long *hpin = (unsigned long long *)pinned_scratch(64 + sizeof(CdDev));
     CdDev *hst = reinterpret_cast<CdDev *>(hpin + 8);
     const size_t hdr = offsetof(CdDev, hist_w);
     unsigned long long prev_w[4] = {0, 0, 0, 0}, prev_a[4] = {0, 0, 0, 0};
-    struct PinGuard {
-        void *p;
-        ~PinGuard() { cudaFreeHost(p); }
-    } pg{hpin};
     int32_t *hi32 = reinterpret_cast<int32_t *>(hpin);
 
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -702,9 +697,11 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
                 D.tier_launches[1]++;
             }
             if (D.timing) RC_CUDA(cudaEventRecord(ev[2], s));
-            k_cd_update_global<<<gblocks, CTA_THREADS, smem_glob, s>>>(a, gcnt.get(), gtouch.get(),
-                                                                      n);
-            RC_LAUNCH();
+            if (hubs) {
+                k_cd_update_global<<<gblocks, CTA_THREADS, smem_glob, s>>>(a, gcnt.get(),
+                                                                          gtouch.get(), n);
+                RC_LAUNCH();
+            }
             if (D.timing) RC_CUDA(cudaEventRecord(ev[3], s));
             k_cd_update_slice<<<sblocks, SLICE_THREADS, smem_slice, s>>>(a, n);
             RC_LAUNCH();

@@ -33,6 +33,11 @@ void count_launch();
 
 int num_sms();
 int max_smem_optin();
+// Sets a kernel's MaxDynamicSharedMemorySize to all the shared memory the
+// device allows it (opt-in limit minus its static shared memory), once per
+// device and kernel. The value never depends on a call's sizes, so
+// concurrent callers cannot lower it under one another's launches.
+void allow_max_smem(const void *kernel);
 
 // Stream-ordered device buffer (cudaMallocAsync / cudaFreeAsync on one stream).
 template <typename T>

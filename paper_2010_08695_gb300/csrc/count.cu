@@ -368,8 +368,7 @@ uint64_t count_local(const receipt_graph *g, unsigned long long *cnt_u,
         k_count_warp<<<sms * 8, 256, 0, s>>>(a);
         RC_LAUNCH();
         if (cta_ks_max > 0) {
-            RC_CUDA(cudaFuncSetAttribute(k_count_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
+            allow_max_smem((const void *)k_count_cta);
             CountArgs c = a;
             c.list = lc.get();
             c.nlist = nl + 1;
@@ -391,8 +390,7 @@ uint64_t count_local(const receipt_graph *g, unsigned long long *cnt_u,
             c.nlist = nl + 2;
             c.work = nl + 6;
             size_t gsm = MID_CHUNK * 8 + CHUNK_BYTES;
-            RC_CUDA(cudaFuncSetAttribute(k_count_global, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)gsm));
+            allow_max_smem((const void *)k_count_global);
             k_count_global<<<gblocks, CTA_THREADS, gsm, s>>>(c, lo.get(), nl + 3, gcnt.get(),
                                                              gtouch.get(), nA);
             RC_LAUNCH();
@@ -534,8 +532,7 @@ void count_noalloc(const receipt_graph *g, unsigned long long *d_cnt_u,
             k_count_warp<<<sms * 8, 256, 0, s>>>(a);
             RC_LAUNCH();
             if (cta_ks_max > 0) {
-                RC_CUDA(cudaFuncSetAttribute(k_count_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem));
+                allow_max_smem((const void *)k_count_cta);
                 CountArgs c = a;
                 c.list = lc;
                 c.nlist = nl + 1;
@@ -548,8 +545,7 @@ void count_noalloc(const receipt_graph *g, unsigned long long *d_cnt_u,
             c.nlist = nl + 2;
             c.work = nl + 6;
             const size_t gsm = MID_CHUNK * 8 + CHUNK_BYTES;
-            RC_CUDA(cudaFuncSetAttribute(k_count_global, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)gsm));
+            allow_max_smem((const void *)k_count_global);
             k_count_global<<<NOALLOC_GSLOTS, CTA_THREADS, gsm, s>>>(c, lo, nl + 3, gcnt, gtouch, nA);
             RC_LAUNCH();
         }

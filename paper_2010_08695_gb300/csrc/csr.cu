@@ -211,7 +211,7 @@ receipt_graph *build_graph(const int32_t *d_eu, const int32_t *d_ev, int64_t m, 
     g->m = mu;
     RC_CUDA(cudaGetDevice(&g->device));
     char *base = nullptr;
-    if (cudaMalloc((void **)&base, total) != cudaSuccess) {
+    if (cudaMallocAsync((void **)&base, total, s) != cudaSuccess) {
         cudaGetLastError();
         delete g;
         fail(RECEIPT_ERR_OOM, "graph allocation failed");
@@ -291,16 +291,25 @@ receipt_graph *build_graph(const int32_t *d_eu, const int32_t *d_ev, int64_t m, 
         RC_CUDA(cudaStreamSynchronize(s));
     } catch (...) {
         cudaStreamSynchronize(s);
-        cudaFree(g->owned);
+        cudaFreeAsync(g->owned, s);
         delete g;
         throw;
     }
     return g;
 }
 
+// The graph's memory goes back to the stream-ordered pool without a device
+// synchronisation. Every entry point has finished its work on the graph when
+// it returns, so ordering the free on the legacy stream is safe.
 void destroy_graph(receipt_graph *g) {
     if (!g) return;
-    if (g->owned) cudaFree(g->owned);
+    if (g->owned) {
+        int prev = -1;
+        cudaGetDevice(&prev);
+        if (prev != g->device) cudaSetDevice(g->device);
+        cudaFreeAsync(g->owned, 0);
+        if (prev >= 0 && prev != g->device) cudaSetDevice(prev);
+    }
     delete g;
 }
 

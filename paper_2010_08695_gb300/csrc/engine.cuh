@@ -326,6 +326,7 @@ struct DenseSlice {
     uint16_t *tl;      // TOUCH_CAP
     int *s_nt;         // shared scalar: touched words
     int32_t hw;        // half of the current slice width (<= DENSE_WORDS)
+    bool wide;         // 32-bit counters, one key per word (slices of DENSE_WORDS keys)
 
     static constexpr size_t bytes() { return (size_t)DENSE_WORDS * 4 + (size_t)TOUCH_CAP * 2; }
     __device__ unsigned char *bind(unsigned char *base, int *nt) {
@@ -333,6 +334,7 @@ struct DenseSlice {
         tl = (uint16_t *)(cnt + DENSE_WORDS);
         s_nt = nt;
         hw = DENSE_WORDS;
+        wide = false;
         return (unsigned char *)(tl + TOUCH_CAP);
     }
     __device__ void clear_all() {
@@ -340,9 +342,14 @@ struct DenseSlice {
             ((uint4 *)cnt)[i] = make_uint4(0, 0, 0, 0);
         if (threadIdx.x == 0) *s_nt = 0;
     }
-    __device__ void set_width(int32_t w) { hw = (w + 1) >> 1; }
+    // Slice of w keys: 16-bit counters (w <= DENSE_KEYS), or 32-bit counters
+    // when counts may reach 2^16 (w <= DENSE_WORDS).
+    __device__ void set_width(int32_t w, bool wide_counts = false) {
+        wide = wide_counts;
+        hw = wide ? w : (w + 1) >> 1;
+    }
     __device__ __forceinline__ void add(int32_t k) {
-        const bool hi = k >= hw;
+        const bool hi = !wide && k >= hw;
         const int32_t w = hi ? k - hw : k;
         const uint32_t old = atomicAdd(&cnt[w], hi ? 0x10000u : 1u);
         const unsigned m = __activemask();
@@ -360,6 +367,7 @@ struct DenseSlice {
         }
     }
     __device__ __forceinline__ uint32_t count(int32_t k) const {
+        if (wide) return cnt[k];
         const bool hi = k >= hw;
         return (cnt[hi ? k - hw : k] >> (hi ? 16 : 0)) & 0xffffu;
     }
@@ -374,9 +382,13 @@ struct DenseSlice {
                 const uint32_t v = cnt[w];
                 if (CLEAR) cnt[w] = 0;
                 if (EMIT) {
-                    const uint32_t c0 = v & 0xffffu, c1 = v >> 16;
-                    if (c0 >= 2) emit(w, c0);
-                    if (c1 >= 2) emit(w + hw, c1);
+                    if (wide) {
+                        if (v >= 2) emit(w, v);
+                    } else {
+                        const uint32_t c0 = v & 0xffffu, c1 = v >> 16;
+                        if (c0 >= 2) emit(w, c0);
+                        if (c1 >= 2) emit(w + hw, c1);
+                    }
                 }
             }
         } else {
@@ -390,6 +402,10 @@ struct DenseSlice {
 #pragma unroll
                     for (int e = 0; e < 4; e++) {
                         const int w = 4 * i + e;
+                        if (wide) {
+                            if (vv[e] >= 2) emit(w, vv[e]);
+                            continue;
+                        }
                         const uint32_t c0 = vv[e] & 0xffffu, c1 = vv[e] >> 16;
                         if (c0 >= 2) emit(w, c0);
                         if (c1 >= 2) emit(w + hw, c1);

@@ -163,10 +163,6 @@ struct FdArgs {
     unsigned long long *stats; // [0] wedges, [1] levels
     unsigned long long *sub_ns;     // per subset: nanoseconds spent
     unsigned long long *sub_levels; // per subset: peeling levels
-    uint32_t *gcnt;            // global engine, per CTA slot
-    int32_t *gtouch;
-    int64_t gks;               // global engine key space per slot
-    int32_t cta_ks;            // largest subset the shared-memory engine takes
 };
 
 struct FdMids {
@@ -186,6 +182,39 @@ struct FdEmit {
     }
 };
 
+// Ranks of one slice [base, end) of the subset's rank space: the run of a
+// middle vertex is sorted by rank, so the slice is a sub-run found by two
+// binary searches.
+struct FdSliceMids {
+    const int64_t *fd_beg;
+    const int32_t *fd_len;
+    const int32_t *fd_adj;
+    int32_t base, end;
+    __device__ __forceinline__ void seg(int64_t q, int64_t &beg, int32_t &len) const {
+        const int64_t b = fd_beg[q];
+        const int32_t l = fd_len[q];
+        const int64_t lo = lower_bound_i32(fd_adj + b, l, base);
+        const int64_t hi = lo + lower_bound_i32(fd_adj + b + lo, l - lo, end);
+        beg = b + lo;
+        len = (int32_t)(hi - lo);
+    }
+};
+
+struct FdSliceVisit {
+    DenseSlice *eng;
+    int32_t base;  // first rank of the slice
+    int32_t self;  // the anchor's own rank
+    __device__ __forceinline__ void operator()(int, int32_t key) {
+        if (key != self) eng->add(key - base);
+    }
+};
+
+struct FdSliceEmit {
+    FdEmit *e;
+    int32_t base;
+    __device__ __forceinline__ void operator()(int32_t k, uint32_t c) { (*e)(k + base, c); }
+};
+
 template <class Eng>
 struct FdVisit {
     Eng *eng;
@@ -195,13 +224,13 @@ struct FdVisit {
     }
 };
 
-__global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a, int32_t head_cap, int32_t bm_cap) {
+__global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_t, s_used, s_over, s_nt, s_np, s_nk, s_nbig;
+    __shared__ int s_t, s_dn, s_np, s_nk, s_nbig;
     __shared__ unsigned long long s_min[32];
     __shared__ int32_t s_tmp[33];
-    CtaHybrid H;
-    unsigned char *p = H.bind(smem, head_cap, bm_cap, &s_used, &s_over);
+    DenseSlice H;
+    unsigned char *p = H.bind(smem, &s_dn);
     Chunk ch;
     ch.beg = (int64_t *)p;
     ch.pre = (int32_t *)(ch.beg + MID_CHUNK);
@@ -213,8 +242,6 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a, int32_t hea
     WarpHash WH{wkey + warp * WARP_SLOTS, (uint32_t *)(wkey + nwarps * WARP_SLOTS) + warp * WARP_SLOTS};
     WH.clear(lane);
     H.clear_all();
-    GlobalDense G{a.gcnt ? a.gcnt + (size_t)blockIdx.x * a.gks : nullptr,
-                  a.gtouch ? a.gtouch + (size_t)blockIdx.x * a.gks : nullptr, &s_nt};
     FdMids M{a.fd_beg, a.fd_len};
     unsigned long long wedges = 0, levels = 0;
     __syncthreads();
@@ -242,8 +269,6 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a, int32_t hea
             alive[r] = 1;
             alist[r] = r;
         }
-        const bool small = ni <= a.cta_ks;
-        if (small) H.set_range((int32_t)imin64(head_cap, ni), ni);
         int32_t nalive = ni;
         unsigned long long level = 0;
         __syncthreads();
@@ -344,32 +369,36 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a, int32_t hea
             }
             __syncthreads();
             const int nbig = s_nbig;
-            // Phase B: the whole CTA per peeled vertex with a bigger update
+            // Phase B: the whole CTA per peeled vertex with a bigger update,
+            // aggregating over slices of the subset's rank space with dense
+            // counters (32-bit counters for an anchor of degree >= 65535)
             for (int pi = 0; pi < nbig; pi++) {
                 const int32_t r = blist[pi];
                 const int32_t x = mem[r];
                 const int64_t q0 = a.off_s[x], q1 = a.off_s[x + 1];
+                const bool wide = q1 - q0 >= 65535;
+                const int32_t SWk = wide ? DENSE_WORDS : DENSE_KEYS;
+                const int32_t C = (ni + SWk - 1) / SWk;
                 FdEmit emit{fsup, alive};
-                if (small && q1 - q0 < 65535) {
-                    FdVisit<CtaHybrid> v{&H, r};
-                    wedges += cta_walk(M, q0, q1, a.fd_adj, ch, v);
-                    const bool over = s_over;
-                    if (!over)
-                        H.flush_clear<true>(emit);
-                    else
-                        H.flush_clear<false>(emit);
+                for (int32_t j = 0; j < C; j++) {
+                    const int32_t base = j * SWk;
+                    const int32_t w = (int32_t)imin64(SWk, (int64_t)ni - base);
+                    H.set_width(w, wide);
+                    FdSliceVisit v{&H, base, r};
+                    int64_t walked;
+                    if (C == 1) {
+                        walked = cta_walk(M, q0, q1, a.fd_adj, ch, v);
+                    } else {
+                        FdSliceMids MS{a.fd_beg, a.fd_len, a.fd_adj, base, base + w};
+                        walked = cta_walk(MS, q0, q1, a.fd_adj, ch, v);
+                    }
+                    wedges += walked;
+                    if (walked == 0) continue;
+                    FdSliceEmit em{&emit, base};
+                    H.sweep<true, true>(em);
                     __syncthreads();
                     H.reset_scalars();
-                    if (!over) continue;
                 }
-                if (threadIdx.x == 0) s_nt = 0;
-                __syncthreads();
-                FdVisit<GlobalDense> v{&G, r};
-                cta_walk(M, q0, q1, a.fd_adj, ch, v);
-                G.flush(emit);
-                __syncthreads();
-                G.clear();
-                __syncthreads();
             }
         }
         __syncthreads();
@@ -450,19 +479,11 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
     int32_t maxn = 0;
     for (int i = 0; i < P; i++) maxn = std::max(maxn, hms[i + 1] - hms[i]);
     const size_t warp_tables = (size_t)(FD_THREADS / 32) * WARP_SLOTS * 8 + 16;
-    const int64_t cta_ks = max_cta_keyspace(maxn, CHUNK_BYTES + warp_tables);
-    int32_t head_cap = 0, bm_cap = 0;
-    size_t smem =
-        hybrid_bytes(std::max<int64_t>(cta_ks, 2), &head_cap, &bm_cap) + CHUNK_BYTES + warp_tables;
-    RC_CUDA(cudaFuncSetAttribute(k_fd_peel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const size_t smem = DenseSlice::bytes() + CHUNK_BYTES + warp_tables;
+    allow_max_smem((const void *)k_fd_peel);
     int occ = 0;
     RC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fd_peel, FD_THREADS, smem));
     const int grid = std::max(1, std::min(num_sms() * std::max(occ, 1), P));
-    // global engine slots: subsets above the shared-memory key space, hub
-    // anchors (degree >= 2^16) and anchors whose repeat table overflowed
-    DevBuf<uint32_t> gcnt((size_t)grid * maxn, s);
-    DevBuf<int32_t> gtouch((size_t)grid * maxn, s);
-    gcnt.zero();
     DevBuf<unsigned long long> fsup(n, s);
     DevBuf<uint8_t> alive(n, s);
     DevBuf<int32_t> alist(n, s), plist(n, s), blist(n, s), qhead(1, s);
@@ -474,9 +495,8 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
     FdArgs a{queue.get(),   P,           qhead.get(),     mstart.get(), members.get(),
              S.off,         fd_beg.get(), fd_len.get(),   fd_adj.get(), S.new2old,
              D.init,        fsup.get(),  alive.get(),     alist.get(),  plist.get(), blist.get(),
-             (unsigned long long *)d_tip, stats.get(),    sub_ns.get(), sub_lv.get(),
-             gcnt.get(),    gtouch.get(), (int64_t)maxn, (int32_t)cta_ks};
-    k_fd_peel<<<grid, FD_THREADS, smem, s>>>(a, head_cap, bm_cap);
+             (unsigned long long *)d_tip, stats.get(),    sub_ns.get(), sub_lv.get()};
+    k_fd_peel<<<grid, FD_THREADS, smem, s>>>(a);
     RC_LAUNCH();
     unsigned long long hs[2] = {0, 0};
     RC_CUDA(cudaMemcpyAsync(hs, stats.get(), sizeof(hs), cudaMemcpyDeviceToHost, s));
@@ -484,8 +504,9 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
     D.wedges_fd = hs[0];
     D.levels = (int64_t)hs[1];
     std::vector<unsigned long long> hns(P), hlv(P);
-    RC_CUDA(cudaMemcpy(hns.data(), sub_ns.get(), 8 * P, cudaMemcpyDeviceToHost));
-    RC_CUDA(cudaMemcpy(hlv.data(), sub_lv.get(), 8 * P, cudaMemcpyDeviceToHost));
+    RC_CUDA(cudaMemcpyAsync(hns.data(), sub_ns.get(), 8 * P, cudaMemcpyDeviceToHost, s));
+    RC_CUDA(cudaMemcpyAsync(hlv.data(), sub_lv.get(), 8 * P, cudaMemcpyDeviceToHost, s));
+    RC_CUDA(cudaStreamSynchronize(s));
     int worst = 0;
     for (int i = 1; i < P; i++)
         if (hns[i] > hns[worst]) worst = i;

@@ -18,6 +18,10 @@ void scatter_to_original(const unsigned long long *local, const int32_t *new2old
 void count_noalloc(const receipt_graph *g, unsigned long long *d_cnt_u,
                    unsigned long long *d_cnt_v, cudaStream_t s);
 
+// Page-locked host buffer of at least `bytes`, owned by the calling thread
+// and reused across calls (no allocation per call).
+void *pinned_scratch(size_t bytes);
+
 // Largest key space whose CtaHybrid engine plus `extra` bytes fits in the
 // opt-in shared memory of one CTA (capped at `want`); 0 if none.
 int64_t max_cta_keyspace(int64_t want, size_t extra);
@@ -37,6 +41,7 @@ struct Decomp {
     const Side *O = nullptr;  // other side
     int32_t n = 0;
     int64_t m = 0;
+    int32_t max_deg_s = 0;                // largest degree on side s
     unsigned long long *sup = nullptr;    // raw supports
     unsigned long long *init = nullptr;   // support when the vertex's range began
     int32_t *sub = nullptr;               // subset index, -1 while remaining

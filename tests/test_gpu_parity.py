@@ -99,6 +99,9 @@ def test_sliced_tier_over_several_key_slices(R):
         assert st["peel_anchors"][3] > 0
     t = R.as_u64(g.tip_decompose(0, warp_max_w=32))
     assert np.array_equal(t, want)
+    # one subset of 150k ranks: the fine-grained step aggregates rank slices
+    t = R.as_u64(g.tip_decompose(0, P=1))
+    assert np.array_equal(t, want)
 
 
 def test_hub_with_degree_above_16_bits(R):
