@@ -273,8 +273,9 @@ def run_ours(args):
 
     # roofline of the dominant peel kernel (tier with the most device time)
     st = stats[-1]
-    names = ["k_cd_update_warp", "k_cd_update_cta", "k_cd_update_global", "k_cd_update_slice"]
-    tier = max(range(4), key=lambda t: st["ms_peel"][t])
+    names = ["k_cd_update_warp", "k_cd_update_cta", "k_cd_update_global", "k_cd_update_slice",
+             "k_cd_update_dense"]
+    tier = max(range(5), key=lambda t: st["ms_peel"][t])
     lau = max(1, st["peel_launches"][tier])
     alg_bytes = (4 * st["peel_wedges"][tier] + 16 * st["peel_mids"][tier]
                  + 24 * st["peel_anchors"][tier]) / lau
@@ -364,10 +365,13 @@ def run_batch(args):
     tb = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        outs = R.receipt_decompose_batch(built, sides, outs=outs)
+        outs = R.receipt_decompose_batch(built, sides, outs=outs, timing=True)
         torch.cuda.synchronize()
         tb.append(time.perf_counter() - t0)
     batch_stats = built[0].stats()
+    if args.trace:
+        with open(args.trace, "w") as f:
+            json.dump(built[0].trace(), f)
     alone = [torch.empty_like(o) for o in outs]
     for g, o in zip(built[:64], alone[:64]):  # warm-up
         g.tip_decompose(0, out=o)
@@ -393,6 +397,13 @@ def run_batch(args):
             "speedup_vs_one_graph_per_launch": t_plain / tbm,
             "wedges_per_s_batched": wedges / tbm,
             "rounds_cd": batch_stats["rounds_cd"], "subsets": batch_stats["p_eff"],
+            "phase_ms": {"count": batch_stats["ms_count"], "cd": batch_stats["ms_cd"],
+                         "fd": batch_stats["ms_fd"], "peel_tiers": batch_stats["ms_peel"]},
+            "fd_slowest_subset": {"ms": batch_stats["ms_fd_max_subset"],
+                                  "n": batch_stats["fd_max_subset_n"],
+                                  "levels": batch_stats["fd_max_subset_levels"]},
+            "walked_wedges": {"count": batch_stats["wedges_count"], "cd": batch_stats["wedges_cd"],
+                              "fd": batch_stats["wedges_fd"]},
             "batch_equals_alone": same, "oracle_sample_ok": oracle_ok,
             "oracle_sample": len(sample)}
     print(json.dumps(line), flush=True)

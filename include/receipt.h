@@ -101,15 +101,16 @@ typedef struct {
     int32_t reserved;
     float ms_csr, ms_count, ms_cd, ms_fd, ms_total; /* only if timing != 0   */
     /* Batched peel update of the coarse-grained step, per aggregation tier
-     * (0 = warp table, 1 = shared-memory hybrid over the whole side,
-     * 2 = global dense counters for hubs, 3 = hybrid over key slices):
+     * (0 = warp table, 1 = shared-memory hybrid over the anchor's key window,
+     * 2 = global dense counters for hubs, 3 = dense counters over key slices,
+     * 4 = dense counters over a key window of at most 36,864 keys):
      * wedges walked, middle vertices (edge visits), anchors (peeled vertices
      * with updates), kernel launches and device time (only if timing != 0). */
-    uint64_t peel_wedges[4];
-    uint64_t peel_mids[4];
-    uint64_t peel_anchors[4];
-    int64_t peel_launches[4];
-    float ms_peel[4];
+    uint64_t peel_wedges[5];
+    uint64_t peel_mids[5];
+    uint64_t peel_anchors[5];
+    int64_t peel_launches[5];
+    float ms_peel[5];
     /* Slowest subset of the fine-grained step: device time, size, levels. */
     float ms_fd_max_subset;
     int32_t fd_max_subset_n;
@@ -121,9 +122,9 @@ typedef struct {
     int32_t range;        /* 0-based subset index the round belongs to        */
     int32_t frontier;     /* activeSet size (vertices peeled this round)      */
     uint64_t hi;          /* upper bound theta(range + 2) of the range        */
-    uint64_t anchors[4];  /* peeled vertices with updates, per peel tier      */
-    uint64_t wedges[4];   /* wedges walked, per peel tier                     */
-    float ms[4];          /* device time per peel tier (only if timing != 0)  */
+    uint64_t anchors[5];  /* peeled vertices with updates, per peel tier      */
+    uint64_t wedges[5];   /* wedges walked, per peel tier                     */
+    float ms[5];          /* device time per peel tier (only if timing != 0)  */
 } receipt_round;
 
 /* Fills `opt` with the defaults (P = 150, nothing optional). */

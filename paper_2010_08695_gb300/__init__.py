@@ -55,16 +55,16 @@ class Stats(ctypes.Structure):
                 ("p_eff", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("ms_csr", ctypes.c_float), ("ms_count", ctypes.c_float), ("ms_cd", ctypes.c_float),
                 ("ms_fd", ctypes.c_float), ("ms_total", ctypes.c_float),
-                ("peel_wedges", ctypes.c_uint64 * 4), ("peel_mids", ctypes.c_uint64 * 4),
-                ("peel_anchors", ctypes.c_uint64 * 4), ("peel_launches", ctypes.c_int64 * 4),
-                ("ms_peel", ctypes.c_float * 4), ("ms_fd_max_subset", ctypes.c_float),
+                ("peel_wedges", ctypes.c_uint64 * 5), ("peel_mids", ctypes.c_uint64 * 5),
+                ("peel_anchors", ctypes.c_uint64 * 5), ("peel_launches", ctypes.c_int64 * 5),
+                ("ms_peel", ctypes.c_float * 5), ("ms_fd_max_subset", ctypes.c_float),
                 ("fd_max_subset_n", ctypes.c_int32), ("fd_max_subset_levels", ctypes.c_int64)]
 
 
 class Round(ctypes.Structure):
     _fields_ = [("range", ctypes.c_int32), ("frontier", ctypes.c_int32), ("hi", ctypes.c_uint64),
-                ("anchors", ctypes.c_uint64 * 4), ("wedges", ctypes.c_uint64 * 4),
-                ("ms", ctypes.c_float * 4)]
+                ("anchors", ctypes.c_uint64 * 5), ("wedges", ctypes.c_uint64 * 5),
+                ("ms", ctypes.c_float * 5)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -304,7 +304,7 @@ class Graph:
         return receipt_get_trace(self._h)
 
 
-def receipt_decompose_batch(graphs, sides, outs=None, P: int = 150, stream=None):
+def receipt_decompose_batch(graphs, sides, outs=None, P: int = 150, stream=None, timing=False):
     """Tip numbers of many graphs in one pass (disjoint-union packing)."""
     import torch
     n = len(graphs)
@@ -314,7 +314,7 @@ def receipt_decompose_batch(graphs, sides, outs=None, P: int = 150, stream=None)
         outs = [torch.empty(g.nu if s == 0 else g.nv, dtype=torch.int64, device=g.device)
                 for g, s in zip(graphs, sides)]
     ps = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
-    o, keep = _options(P)
+    o, keep = _options(P, timing=timing)
     _check(load().receipt_decompose_batch(hs, ss, n, ps, ctypes.byref(o), _stream_handle(stream)))
     return outs
 

@@ -222,7 +222,7 @@ void tip_decompose_impl(receipt_graph *g, int side, uint64_t *d_tip, const recei
     st.ms_fd_max_subset = D.fd_max_ms;
     st.fd_max_subset_n = D.fd_max_n;
     st.fd_max_subset_levels = D.fd_max_levels;
-    for (int t = 0; t < 4; t++) {
+    for (int t = 0; t < 5; t++) {
         st.peel_wedges[t] = D.tier_wedges[t];
         st.peel_mids[t] = D.tier_mids[t];
         st.peel_anchors[t] = D.tier_anchors[t];

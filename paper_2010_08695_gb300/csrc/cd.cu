@@ -32,7 +32,8 @@ namespace receipt {
 
 namespace {
 
-constexpr int NBUCKET = 1920;  // 32 exact buckets + 58 octaves x 32 mantissa steps
+constexpr int NBUCKET = 1920;
+constexpr int NTIER = 5;  // warp, hybrid, global, sliced, dense window  // 32 exact buckets + 58 octaves x 32 mantissa steps
 
 __device__ __forceinline__ int bucket_of(unsigned long long k) {
     if (k < 32) return (int)k;
@@ -50,14 +51,15 @@ __device__ __forceinline__ unsigned long long bucket_top(int b) {
 
 struct CdDev {
     unsigned long long hi;
-    int32_t nF, nNext, nLw, nLc, nLg, nLo, nLs, pad2;
-    int32_t work[4];
+    int32_t nF, nNext, nLw, nLc, nLg, nLo, nLs, nLb, nLd, pad2;
+    int32_t work[6];
+    unsigned long long work64;  // item counter of the sliced tier
     int32_t n_remaining;
     int32_t pad;
     unsigned long long wrem_prev;
     double tgt_prev;
     unsigned long long wedges;
-    unsigned long long tier_w[4], tier_m[4], tier_a[4];  // per-tier wedges, mids, anchors
+    unsigned long long tier_w[NTIER], tier_m[NTIER], tier_a[NTIER];  // per tier: wedges, mids, anchors
     unsigned long long hist_w[NBUCKET];
     uint32_t hist_c[NBUCKET];
 };
@@ -218,9 +220,7 @@ __device__ __forceinline__ void warp_append(bool take, int32_t x, int32_t *cnt, 
 __global__ void k_cd_prepare(const int32_t *__restrict__ F, CdDev *st, int32_t range,
                              int32_t *__restrict__ sub, const unsigned long long *__restrict__ sup,
                              const unsigned long long *__restrict__ wfull,
-                             const int64_t *__restrict__ off, int cta_ok, int32_t *__restrict__ Lw,
-                             int32_t *__restrict__ Lc, int32_t *__restrict__ Lg,
-                             int32_t *__restrict__ Ls, int32_t warp_max_w, int32_t slice_min_w) {
+                             int32_t *__restrict__ Lw, int32_t *__restrict__ Lb, int32_t warp_max_w) {
     const int32_t nF = st->nF;
     unsigned long long wsum = 0;
     for (int32_t base = blockIdx.x * blockDim.x; base < nF; base += gridDim.x * blockDim.x) {
@@ -232,25 +232,77 @@ __global__ void k_cd_prepare(const int32_t *__restrict__ F, CdDev *st, int32_t r
             sub[x] = range;
             if (sup[x] > 0) {
                 unsigned long long W = wfull[x];
-                int64_t deg = off[x + 1] - off[x];
                 wsum += W;
-                if (W <= (unsigned long long)warp_max_w)
-                    tier = 0;
-                else if (deg >= 65535)
-                    tier = 2;
-                else if (cta_ok && W <= (unsigned long long)slice_min_w)
-                    tier = 1;
-                else
-                    tier = 3;
+                tier = W <= (unsigned long long)warp_max_w ? 0 : 1;
             }
         }
         warp_append(tier == 0, x, &st->nLw, Lw);
-        warp_append(tier == 1, x, &st->nLc, Lc);
-        warp_append(tier == 2, x, &st->nLg, Lg);
-        warp_append(tier == 3, x, &st->nLs, Ls);
+        warp_append(tier == 1, x, &st->nLb, Lb);
     }
     wsum = warp_sum(wsum);
     if ((threadIdx.x & 31) == 0 && wsum) atomicAdd(&st->wedges, wsum);
+}
+
+// Routes the anchors with more than warp_max_w wedges (one warp each): the
+// keys their wedges can reach lie in the window [kmin, kmax] spanned by the
+// first and last entries of their middle vertices' lists (in a disjoint union
+// that is the anchor's own graph). Window of at most DENSE_KEYS keys -> one
+// dense-counter item over the window; degree >= 65535 -> global counters;
+// window within the hybrid's key space and at most slice_min_w wedges ->
+// hybrid; otherwise -> key slices that meet the window.
+__global__ void k_cd_route(CdDev *st, const int32_t *__restrict__ Lb,
+                           const int64_t *__restrict__ off_s, const int32_t *__restrict__ adj_s,
+                           const int64_t *__restrict__ off_o, const int32_t *__restrict__ adj_o,
+                           const unsigned long long *__restrict__ wfull, int64_t cta_keys,
+                           int32_t slice_min_w, int32_t SW, int32_t *__restrict__ Lc,
+                           int32_t *__restrict__ Lc_k, int32_t *__restrict__ Lc_w,
+                           int32_t *__restrict__ Ld,
+                           int32_t *__restrict__ Ld_k, int32_t *__restrict__ Lg,
+                           int32_t *__restrict__ Ls, int32_t *__restrict__ Ls_lo,
+                           int32_t *__restrict__ Ls_hi) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int32_t nb = st->nLb;
+    for (int64_t i = warp; i < nb; i += nwarps) {
+        const int32_t x = Lb[i];
+        const int64_t q0 = off_s[x], q1 = off_s[x + 1];
+        int32_t kmin = INT32_MAX, kmax = -1;
+        for (int64_t q = q0 + lane; q < q1; q += 32) {
+            const int32_t y = adj_s[q];
+            const int64_t b = off_o[y], e = off_o[y + 1];
+            if (e > b) {
+                kmin = min(kmin, adj_o[b]);
+                kmax = max(kmax, adj_o[e - 1]);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+            kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+        }
+        if (lane == 0) {
+            const int64_t ww = (int64_t)kmax - kmin + 1;
+            int p;
+            if (q1 - q0 >= 65535) {
+                Lg[atomicAdd(&st->nLg, 1)] = x;
+            } else if (ww <= DENSE_KEYS) {
+                p = atomicAdd(&st->nLd, 1);
+                Ld[p] = x;
+                Ld_k[p] = kmin;
+            } else if (ww <= cta_keys && wfull[x] <= (unsigned long long)slice_min_w) {
+                p = atomicAdd(&st->nLc, 1);
+                Lc[p] = x;
+                Lc_k[p] = kmin;
+                Lc_w[p] = (int32_t)ww;
+            } else {
+                p = atomicAdd(&st->nLs, 1);
+                Ls[p] = x;
+                Ls_lo[p] = kmin / SW;
+                Ls_hi[p] = kmax / SW;
+            }
+        }
+    }
 }
 
 // Support decrement of one (x, x') pair with crossing detection.
@@ -278,6 +330,40 @@ struct PeelMids {
     }
 };
 
+// Segment of a middle vertex restricted to key slice j.
+struct SlicedMids {
+    const int32_t *adj_s;
+    const int64_t *off_o;
+    const int32_t *soff;
+    int32_t C1;  // C + 1
+    int32_t j;
+    __device__ __forceinline__ void seg(int64_t q, int64_t &beg, int32_t &len) const {
+        int32_t y = adj_s[q];
+        const int32_t *so = soff + (size_t)y * C1 + j;
+        int32_t b = so[0], e = so[1];
+        beg = off_o[y] + b;
+        len = e - b;
+    }
+};
+
+// Keys of slice j shifted to the slice's local key space.
+template <class Eng>
+struct SliceVisit {
+    Eng *eng;
+    int32_t self_local;  // anchor's own key in this slice's frame (or -1)
+    int32_t base;
+    __device__ __forceinline__ void operator()(int, int32_t key) {
+        int32_t k = key - base;
+        if (k != self_local) eng->add(k);
+    }
+};
+
+struct SliceEmit {
+    CdEmit *e;
+    int32_t base;
+    __device__ __forceinline__ void operator()(int32_t k, uint32_t c) { (*e)(k + base, c); }
+};
+
 struct PeelArgs {
     const int64_t *off_s;
     const int32_t *adj_s;
@@ -289,9 +375,16 @@ struct PeelArgs {
     const int32_t *Lw, *Lc, *Lg;
     int32_t *Ls;           // sliced anchors (the hybrid tier appends its overflows)
     int32_t *next;
+    int32_t *Lc_k;         // hybrid anchors: first key and width of their window
+    int32_t *Lc_w;
+    int32_t *Ls_lo;        // sliced anchors: first and last key slice of their window
+    int32_t *Ls_hi;
+    const int32_t *Ld;     // dense-window anchors and their first key
+    const int32_t *Ld_k;
     const int32_t *soff;   // per other-side vertex: C + 1 slice starts within its list
     int32_t C;             // key slices
     int32_t SW;            // keys per slice
+    int32_t n_keys;        // keys of the side
 };
 
 __global__ void __launch_bounds__(256) k_cd_update_warp(PeelArgs a) {
@@ -384,15 +477,25 @@ __global__ void __launch_bounds__(CTA_THREADS) k_cd_update_cta(PeelArgs a, int32
         int idx = s_idx;
         if (idx >= n) break;
         const int32_t x = a.Lc[idx];
-        PeelVisit<CtaHybrid> v{&H, x};
+        const int32_t kb = a.Lc_k[idx];
+        const int32_t kw = a.Lc_w[idx];
+        H.set_range((int32_t)imin64(H.head_cap, kw), kw);
+        SliceVisit<CtaHybrid> v{&H, x - kb, kb};
         cw += cta_walk(M, a.off_s[x], a.off_s[x + 1], a.adj_o, ch, v);
         cm += (unsigned long long)(a.off_s[x + 1] - a.off_s[x]);
         ca++;
+        SliceEmit em{&emit, kb};
         if (!s_over) {
-            H.flush_clear<true>(emit);
+            H.flush_clear<true>(em);
         } else {
-            H.flush_clear<false>(emit);
-            if (threadIdx.x == 0) a.Ls[atomicAdd(&a.st->nLs, 1)] = x;
+            H.flush_clear<false>(em);
+            if (threadIdx.x == 0) {
+                // redo through the key slices that meet the window
+                const int p = atomicAdd(&a.st->nLs, 1);
+                a.Ls[p] = x;
+                a.Ls_lo[p] = kb / a.SW;
+                a.Ls_hi[p] = (kb + kw - 1) / a.SW;
+            }
         }
         __syncthreads();
         H.reset_scalars();
@@ -443,47 +546,14 @@ __global__ void __launch_bounds__(CTA_THREADS) k_cd_update_global(PeelArgs a, ui
     }
 }
 
-// Segment of a middle vertex restricted to key slice j.
-struct SlicedMids {
-    const int32_t *adj_s;
-    const int64_t *off_o;
-    const int32_t *soff;
-    int32_t C1;  // C + 1
-    int32_t j;
-    __device__ __forceinline__ void seg(int64_t q, int64_t &beg, int32_t &len) const {
-        int32_t y = adj_s[q];
-        const int32_t *so = soff + (size_t)y * C1 + j;
-        int32_t b = so[0], e = so[1];
-        beg = off_o[y] + b;
-        len = e - b;
-    }
-};
-
-// Keys of slice j shifted to the slice's local key space.
-template <class Eng>
-struct SliceVisit {
-    Eng *eng;
-    int32_t self_local;  // anchor's own key in this slice's frame (or -1)
-    int32_t base;
-    __device__ __forceinline__ void operator()(int, int32_t key) {
-        int32_t k = key - base;
-        if (k != self_local) eng->add(k);
-    }
-};
-
-struct SliceEmit {
-    CdEmit *e;
-    int32_t base;
-    __device__ __forceinline__ void operator()(int32_t k, uint32_t c) { (*e)(k + base, c); }
-};
-
 // Anchors with many wedges: the key space is cut into C slices of SW keys and
 // every (anchor, slice) pair is one work item, so the slices of a heavy
 // anchor run on different CTAs. Each item aggregates its slice with dense
 // 16-bit counters in shared memory.
 __global__ void __launch_bounds__(SLICE_THREADS, 2) k_cd_update_slice(PeelArgs a, int32_t n) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_idx, s_nt;
+    __shared__ long long s_idx;
+    __shared__ int s_nt;
     DenseSlice H;
     unsigned char *p = H.bind(smem, &s_nt);
     Chunk ch;
@@ -497,14 +567,26 @@ __global__ void __launch_bounds__(SLICE_THREADS, 2) k_cd_update_slice(PeelArgs a
     unsigned long long cw = 0, cm = 0, ca = 0;
     const int64_t items = (int64_t)a.st->nLs * a.C;
     for (;;) {
-        if (threadIdx.x == 0) s_idx = atomicAdd(&a.st->work[3], 1);
+        // next (anchor, slice) item whose slice meets the anchor's window
+        if (threadIdx.x == 0) {
+            int64_t it;
+            for (;;) {
+                it = atomicAdd((unsigned long long *)&a.st->work64, 1ull);
+                if (it >= items) break;
+                const int64_t ai = it / a.C;
+                const int32_t jj = (int32_t)(it % a.C);
+                if (jj >= a.Ls_lo[ai] && jj <= a.Ls_hi[ai]) break;
+            }
+            s_idx = it < items ? it : -1;
+        }
         __syncthreads();
         const int64_t idx = s_idx;
-        if (idx >= items) break;
-        const int32_t x = a.Ls[idx / a.C];
+        if (idx < 0) break;
+        const int64_t ai = idx / a.C;
+        const int32_t x = a.Ls[ai];
         const int32_t j = (int32_t)(idx % a.C);
         const int64_t q0 = a.off_s[x], q1 = a.off_s[x + 1];
-        if (j == 0) {
+        if (j == a.Ls_lo[ai]) {
             cm += (unsigned long long)(q1 - q0);
             ca++;
         }
@@ -531,6 +613,50 @@ __global__ void __launch_bounds__(SLICE_THREADS, 2) k_cd_update_slice(PeelArgs a
     }
 }
 
+// Anchors whose keys fit one window of at most DENSE_KEYS keys: one CTA per
+// anchor aggregates the window with dense 16-bit counters (exact, no
+// overflow path).
+__global__ void __maxnreg__(64) k_cd_update_dense(PeelArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_idx, s_nt;
+    DenseSlice H;
+    unsigned char *p = H.bind(smem, &s_nt);
+    Chunk ch;
+    ch.beg = (int64_t *)p;
+    ch.pre = (int32_t *)(ch.beg + MID_CHUNK);
+    ch.tmp = ch.pre + MID_CHUNK + 1;
+    ch.len = chunk_len_ptr(ch.tmp);
+    H.clear_all();
+    __syncthreads();
+    CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext};
+    PeelMids M{a.adj_s, a.off_o};
+    unsigned long long cw = 0, cm = 0, ca = 0;
+    const int32_t n = a.st->nLd;
+    for (;;) {
+        if (threadIdx.x == 0) s_idx = atomicAdd(&a.st->work[4], 1);
+        __syncthreads();
+        const int idx = s_idx;
+        if (idx >= n) break;
+        const int32_t x = a.Ld[idx];
+        const int32_t kb = a.Ld_k[idx];
+        const int64_t q0 = a.off_s[x], q1 = a.off_s[x + 1];
+        H.set_width(DENSE_KEYS);
+        SliceVisit<DenseSlice> v{&H, x - kb, kb};
+        cw += cta_walk(M, q0, q1, a.adj_o, ch, v);
+        cm += (unsigned long long)(q1 - q0);
+        ca++;
+        SliceEmit em{&emit, kb};
+        H.sweep<true, true>(em);
+        __syncthreads();
+        H.reset_scalars();
+    }
+    if (threadIdx.x == 0 && ca) {
+        atomicAdd(&a.st->tier_w[4], cw);
+        atomicAdd(&a.st->tier_m[4], cm);
+        atomicAdd(&a.st->tier_a[4], ca);
+    }
+}
+
 // soff[y * (C + 1) + j] = number of entries of N_y below j * SW (j = 0..C).
 __global__ void k_slice_table(const int64_t *__restrict__ off_o, const int32_t *__restrict__ adj_o,
                               int32_t n_o, int32_t C, int32_t SW, int32_t *__restrict__ soff) {
@@ -546,14 +672,16 @@ __global__ void k_slice_table(const int64_t *__restrict__ off_o, const int32_t *
 __global__ void k_cd_advance(CdDev *st) {
     st->nF = st->nNext;
     st->nNext = 0;
-    st->nLw = st->nLc = st->nLg = st->nLo = st->nLs = 0;
-    st->work[0] = st->work[1] = st->work[2] = st->work[3] = 0;
+    st->nLw = st->nLc = st->nLg = st->nLo = st->nLs = st->nLb = st->nLd = 0;
+    for (int i = 0; i < 6; i++) st->work[i] = 0;
+    st->work64 = 0;
 }
 
 __global__ void k_cd_new_range(CdDev *st) {
     st->nF = st->nNext = 0;
-    st->nLw = st->nLc = st->nLg = st->nLo = st->nLs = 0;
-    st->work[0] = st->work[1] = st->work[2] = st->work[3] = 0;
+    st->nLw = st->nLc = st->nLg = st->nLo = st->nLs = st->nLb = st->nLd = 0;
+    for (int i = 0; i < 6; i++) st->work[i] = 0;
+    st->work64 = 0;
     for (int b = 0; b < NBUCKET; b++) {
         st->hist_w[b] = 0;
         st->hist_c[b] = 0;
@@ -604,7 +732,8 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
     }
     DevBuf<CdDev> st(1, s);
     st.zero();
-    DevBuf<int32_t> F(n, s), Nx(n, s), Lw(n, s), Lc(n, s), Lg(n, s), Ls(n, s);
+    DevBuf<int32_t> F(n, s), Nx(n, s), Lw(n, s), Lc(n, s), Lg(n, s), Ls(n, s), Lb(n, s), Ld(n, s);
+    DevBuf<int32_t> Lc_k(n, s), Lc_w(n, s), Ld_k(n, s), Ls_lo(n, s), Ls_hi(n, s);
     const int32_t warp_max_w =
         opt.warp_max_w > 0 ? std::min(opt.warp_max_w, WARP_MAX_W) : WARP_MAX_W;
     const int32_t slice_min_w = opt.slice_min_w > 0 ? opt.slice_min_w : SLICE_MIN_W;
@@ -626,10 +755,16 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
     // tiers available for peel anchors (key space = whole side)
     const size_t chunk_extra = CHUNK_BYTES;
     int32_t head_cap = 0, bm_cap = 0;
-    const bool cta_ok = max_cta_keyspace(n, chunk_extra) >= n;
-    size_t smem_cta = cta_ok ? hybrid_bytes(n, &head_cap, &bm_cap) + chunk_extra : 0;
-    if (cta_ok)
-        allow_max_smem((const void *)k_cd_update_cta);
+    // the hybrid engine covers windows of up to cta_keys keys
+    const int64_t cta_keys = max_cta_keyspace(n, chunk_extra);
+    const bool cta_ok = cta_keys > DENSE_KEYS;
+    size_t smem_cta = cta_ok ? hybrid_bytes(cta_keys, &head_cap, &bm_cap) + chunk_extra : 0;
+    if (cta_ok) allow_max_smem((const void *)k_cd_update_cta);
+    allow_max_smem((const void *)k_cd_update_dense);
+    int occ_d = 1;
+    RC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_d, k_cd_update_dense, SLICE_THREADS,
+                                                          DenseSlice::bytes() + CHUNK_BYTES));
+    const int dblocks = sms * std::max(1, occ_d);
     // global-counter slots only exist if the side has a hub whose counts can
     // exceed 16 bits (degree >= 65535)
     const bool hubs = D.max_deg_s >= 65535;
@@ -642,19 +777,19 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
     unsigned long long *hpin = (unsigned long long *)pinned_scratch(64 + sizeof(CdDev));
     CdDev *hst = reinterpret_cast<CdDev *>(hpin + 8);
     const size_t hdr = offsetof(CdDev, hist_w);
-    unsigned long long prev_w[4] = {0, 0, 0, 0}, prev_a[4] = {0, 0, 0, 0};
+    unsigned long long prev_w[NTIER] = {}, prev_a[NTIER] = {};
     int32_t *hi32 = reinterpret_cast<int32_t *>(hpin);
 
-    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[NTIER + 1] = {};
     struct EvGuard {
         cudaEvent_t *e;
         ~EvGuard() {
-            for (int i = 0; i < 5; i++)
+            for (int i = 0; i <= NTIER; i++)
                 if (e[i]) cudaEventDestroy(e[i]);
         }
     } eg{ev};
     if (D.timing)
-        for (int i = 0; i < 5; i++) RC_CUDA(cudaEventCreate(&ev[i]));
+        for (int i = 0; i <= NTIER; i++) RC_CUDA(cudaEventCreate(&ev[i]));
     k_init_state<<<ceil_div(n, 256), 256, 0, s>>>(D.sub, n);
     RC_LAUNCH();
     const int nb = std::min(ceil_div(n, 512), sms * 4);
@@ -681,31 +816,42 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
         k_cd_frontier<<<nb, 512, 0, s>>>(n, D.sub, D.sup, st.get(), cur);
         RC_LAUNCH();
         for (;;) {
-            k_cd_prepare<<<nb, 512, 0, s>>>(cur, st.get(), range, D.sub, D.sup, D.wfull, S.off,
-                                            cta_ok ? 1 : 0, Lw.get(), Lc.get(), Lg.get(),
-                                            Ls.get(), warp_max_w, slice_min_w);
+            k_cd_prepare<<<nb, 512, 0, s>>>(cur, st.get(), range, D.sub, D.sup, D.wfull, Lw.get(),
+                                            Lb.get(), warp_max_w);
             RC_LAUNCH();
-            PeelArgs a{S.off, S.adj, O.off, O.adj, D.sup, D.sub, st.get(), Lw.get(), Lc.get(),
-                       Lg.get(), Ls.get(), nxt, soff.get(), C, SW};
+            k_cd_route<<<sms * 8, 256, 0, s>>>(st.get(), Lb.get(), S.off, S.adj, O.off, O.adj,
+                                               D.wfull, cta_ok ? cta_keys : 0, slice_min_w, SW,
+                                               Lc.get(), Lc_k.get(), Lc_w.get(), Ld.get(),
+                                               Ld_k.get(), Lg.get(), Ls.get(), Ls_lo.get(),
+                                               Ls_hi.get());
+            RC_LAUNCH();
+            PeelArgs a{S.off,     S.adj,      O.off,       O.adj,       D.sup,    D.sub,
+                       st.get(),  Lw.get(),   Lc.get(),    Lg.get(),    Ls.get(), nxt,
+                       Lc_k.get(), Lc_w.get(), Ls_lo.get(), Ls_hi.get(), Ld.get(), Ld_k.get(),
+                       soff.get(), C,         SW,          n};
             if (D.timing) RC_CUDA(cudaEventRecord(ev[0], s));
             k_cd_update_warp<<<sms * 8, 256, 0, s>>>(a);
             RC_LAUNCH();
             if (D.timing) RC_CUDA(cudaEventRecord(ev[1], s));
+            k_cd_update_dense<<<dblocks, SLICE_THREADS, DenseSlice::bytes() + CHUNK_BYTES, s>>>(a);
+            RC_LAUNCH();
+            if (D.timing) RC_CUDA(cudaEventRecord(ev[2], s));
             if (cta_ok) {
                 k_cd_update_cta<<<sms, CTA_THREADS, smem_cta, s>>>(a, head_cap, bm_cap);
                 RC_LAUNCH();
                 D.tier_launches[1]++;
             }
-            if (D.timing) RC_CUDA(cudaEventRecord(ev[2], s));
+            if (D.timing) RC_CUDA(cudaEventRecord(ev[3], s));
             if (hubs) {
                 k_cd_update_global<<<gblocks, CTA_THREADS, smem_glob, s>>>(a, gcnt.get(),
                                                                           gtouch.get(), n);
                 RC_LAUNCH();
             }
-            if (D.timing) RC_CUDA(cudaEventRecord(ev[3], s));
+            if (D.timing) RC_CUDA(cudaEventRecord(ev[4], s));
             k_cd_update_slice<<<sblocks, SLICE_THREADS, smem_slice, s>>>(a, n);
             RC_LAUNCH();
-            if (D.timing) RC_CUDA(cudaEventRecord(ev[4], s));
+            if (D.timing) RC_CUDA(cudaEventRecord(ev[5], s));
+            D.tier_launches[4]++;
             D.tier_launches[0]++;
             D.tier_launches[2]++;
             D.tier_launches[3]++;
@@ -716,18 +862,20 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
             rr.range = range;
             rr.frontier = hst->nF;
             rr.hi = hi;
-            for (int t = 0; t < 4; t++) {
+            for (int t = 0; t < NTIER; t++) {
                 rr.anchors[t] = hst->tier_a[t] - prev_a[t];
                 rr.wedges[t] = hst->tier_w[t] - prev_w[t];
                 prev_a[t] = hst->tier_a[t];
                 prev_w[t] = hst->tier_w[t];
             }
             if (D.timing) {
-                for (int t = 0; t < 4; t++) {
+                // launch order: warp, dense window, hybrid, global, sliced
+                static const int tier_of_gap[NTIER] = {0, 4, 1, 2, 3};
+                for (int gp = 0; gp < NTIER; gp++) {
                     float ms = 0;
-                    RC_CUDA(cudaEventElapsedTime(&ms, ev[t], ev[t + 1]));
-                    D.tier_ms[t] += ms;
-                    rr.ms[t] = ms;
+                    RC_CUDA(cudaEventElapsedTime(&ms, ev[gp], ev[gp + 1]));
+                    D.tier_ms[tier_of_gap[gp]] += ms;
+                    rr.ms[tier_of_gap[gp]] = ms;
                 }
             }
             D.trace.push_back(rr);
@@ -745,17 +893,17 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
     RC_LAUNCH();
     int hany = 0;
     RC_CUDA(cudaMemcpyAsync(&hany, any.get(), 4, cudaMemcpyDeviceToHost, s));
-    unsigned long long hw = 0, ht[12];
+    unsigned long long hw = 0, ht[3 * NTIER];
     RC_CUDA(cudaMemcpyAsync(&hw, &st.get()->wedges, 8, cudaMemcpyDeviceToHost, s));
     RC_CUDA(cudaMemcpyAsync(ht, st.get()->tier_w, sizeof(ht), cudaMemcpyDeviceToHost, s));
     RC_CUDA(cudaStreamSynchronize(s));
     D.p_eff = range + (hany ? 1 : 0);
     if (hany) D.bounds.push_back(~0ull);
     D.wedges_cd = hw;
-    for (int t = 0; t < 4; t++) {
+    for (int t = 0; t < NTIER; t++) {
         D.tier_wedges[t] = ht[t];
-        D.tier_mids[t] = ht[4 + t];
-        D.tier_anchors[t] = ht[8 + t];
+        D.tier_mids[t] = ht[NTIER + t];
+        D.tier_anchors[t] = ht[2 * NTIER + t];
     }
 }
 

@@ -51,10 +51,10 @@ struct Decomp {
     uint64_t wedges_cd = 0, wedges_fd = 0;
     int64_t rounds = 0, levels = 0;
     bool timing = false;
-    uint64_t tier_wedges[4] = {0, 0, 0, 0}, tier_mids[4] = {0, 0, 0, 0};
-    uint64_t tier_anchors[4] = {0, 0, 0, 0};
-    int64_t tier_launches[4] = {0, 0, 0, 0};
-    float tier_ms[4] = {0, 0, 0, 0};
+    uint64_t tier_wedges[5] = {}, tier_mids[5] = {};
+    uint64_t tier_anchors[5] = {};
+    int64_t tier_launches[5] = {};
+    float tier_ms[5] = {};
     std::vector<receipt_round> trace;
     float fd_max_ms = 0;         // slowest subset of the fine-grained step
     int32_t fd_max_n = 0;        // its size
