@@ -86,6 +86,10 @@ typedef struct {
      * change speed only, never results. */
     int32_t warp_max_w;
     int32_t slice_min_w;
+    /* Non-zero turns off dynamic graph maintenance (Sec. 4.2: between ranges
+     * the coarse-grained step drops peeled vertices from a working copy of
+     * the adjacency lists). Speed only; results are the same. */
+    int32_t no_dgm;
 } receipt_options;
 
 /* Counters of the last call on a graph (Sec. 5: wedges and rounds). */

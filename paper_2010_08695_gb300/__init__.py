@@ -45,7 +45,8 @@ class Options(ctypes.Structure):
                 ("n_bounds", ctypes.c_int32), ("d_subset", ctypes.c_void_p),
                 ("h_bounds_out", ctypes.POINTER(ctypes.c_uint64)), ("h_bounds_cap", ctypes.c_int32),
                 ("h_p_eff", ctypes.POINTER(ctypes.c_int32)), ("timing", ctypes.c_int32),
-                ("warp_max_w", ctypes.c_int32), ("slice_min_w", ctypes.c_int32)]
+                ("warp_max_w", ctypes.c_int32), ("slice_min_w", ctypes.c_int32),
+                ("no_dgm", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -159,10 +160,11 @@ def _dptr(t):
 
 
 def _options(P=150, bounds=None, subset=None, bounds_out=None, p_eff=None, timing=False,
-             warp_max_w=0, slice_min_w=0):
+             warp_max_w=0, slice_min_w=0, dgm=True):
     o = Options()
     load().receipt_options_default(ctypes.byref(o))
     o.P = int(P)
+    o.no_dgm = 0 if dgm else 1
     o.warp_max_w = int(warp_max_w)
     o.slice_min_w = int(slice_min_w)
     keep = []
@@ -281,7 +283,7 @@ class Graph:
         return cu, cv
 
     def tip_decompose(self, side: int = SIDE_U, P: int = 150, bounds=None, subsets=False,
-                      timing=False, out=None, stream=None, warp_max_w=0, slice_min_w=0):
+                      timing=False, out=None, stream=None, warp_max_w=0, slice_min_w=0, dgm=True):
         """Tip numbers of ``side`` (Algorithms 3 and 4). With ``subsets=True``
         returns ``(tips, subset_of_vertex, range_bounds)``."""
         import torch
@@ -291,7 +293,7 @@ class Graph:
         bout = np.zeros(P + (len(bounds) if bounds is not None else 0) + 4, np.uint64) \
             if subsets else None
         peff = ctypes.c_int32(0)
-        o, keep = _options(P, bounds, sub, bout, peff, timing, warp_max_w, slice_min_w)
+        o, keep = _options(P, bounds, sub, bout, peff, timing, warp_max_w, slice_min_w, dgm)
         receipt_tip_decompose(self._h, side, tip, o, stream)
         if subsets:
             return tip, sub, bout[: peff.value + 1]

@@ -33,7 +33,8 @@ namespace receipt {
 namespace {
 
 constexpr int NBUCKET = 1920;
-constexpr int NTIER = 5;  // warp, hybrid, global, sliced, dense window  // 32 exact buckets + 58 octaves x 32 mantissa steps
+constexpr int NTIER = 5;  // warp, hybrid, global, sliced, dense window
+constexpr double DGM_FRAC = 0.125;  // stale share of live entries that triggers a compaction  // 32 exact buckets + 58 octaves x 32 mantissa steps
 
 __device__ __forceinline__ int bucket_of(unsigned long long k) {
     if (k < 32) return (int)k;
@@ -54,6 +55,7 @@ struct CdDev {
     int32_t nF, nNext, nLw, nLc, nLg, nLo, nLs, nLb, nLd, pad2;
     int32_t work[6];
     unsigned long long work64;  // item counter of the sliced tier
+    unsigned long long peeled_edges;  // adjacency entries of assigned vertices (for DGM)
     int32_t n_remaining;
     int32_t pad;
     unsigned long long wrem_prev;
@@ -220,9 +222,10 @@ __device__ __forceinline__ void warp_append(bool take, int32_t x, int32_t *cnt, 
 __global__ void k_cd_prepare(const int32_t *__restrict__ F, CdDev *st, int32_t range,
                              int32_t *__restrict__ sub, const unsigned long long *__restrict__ sup,
                              const unsigned long long *__restrict__ wfull,
-                             int32_t *__restrict__ Lw, int32_t *__restrict__ Lb, int32_t warp_max_w) {
+                             const int64_t *__restrict__ off_s, int32_t *__restrict__ Lw,
+                             int32_t *__restrict__ Lb, int32_t warp_max_w) {
     const int32_t nF = st->nF;
-    unsigned long long wsum = 0;
+    unsigned long long wsum = 0, esum = 0;
     for (int32_t base = blockIdx.x * blockDim.x; base < nF; base += gridDim.x * blockDim.x) {
         int32_t i = base + threadIdx.x;
         int32_t x = -1;
@@ -230,6 +233,7 @@ __global__ void k_cd_prepare(const int32_t *__restrict__ F, CdDev *st, int32_t r
         if (i < nF) {
             x = F[i];
             sub[x] = range;
+            esum += (unsigned long long)(off_s[x + 1] - off_s[x]);
             if (sup[x] > 0) {
                 unsigned long long W = wfull[x];
                 wsum += W;
@@ -240,7 +244,11 @@ __global__ void k_cd_prepare(const int32_t *__restrict__ F, CdDev *st, int32_t r
         warp_append(tier == 1, x, &st->nLb, Lb);
     }
     wsum = warp_sum(wsum);
-    if ((threadIdx.x & 31) == 0 && wsum) atomicAdd(&st->wedges, wsum);
+    esum = warp_sum(esum);
+    if ((threadIdx.x & 31) == 0) {
+        if (wsum) atomicAdd(&st->wedges, wsum);
+        if (esum) atomicAdd(&st->peeled_edges, esum);
+    }
 }
 
 // Routes the anchors with more than warp_max_w wedges (one warp each): the
@@ -252,7 +260,8 @@ __global__ void k_cd_prepare(const int32_t *__restrict__ F, CdDev *st, int32_t r
 // hybrid; otherwise -> key slices that meet the window.
 __global__ void k_cd_route(CdDev *st, const int32_t *__restrict__ Lb,
                            const int64_t *__restrict__ off_s, const int32_t *__restrict__ adj_s,
-                           const int64_t *__restrict__ off_o, const int32_t *__restrict__ adj_o,
+                           const int64_t *__restrict__ off_o, const int32_t *__restrict__ len_o,
+                           const int32_t *__restrict__ adj_o,
                            const unsigned long long *__restrict__ wfull, int64_t cta_keys,
                            int32_t slice_min_w, int32_t SW, int32_t *__restrict__ Lc,
                            int32_t *__restrict__ Lc_k, int32_t *__restrict__ Lc_w,
@@ -270,7 +279,7 @@ __global__ void k_cd_route(CdDev *st, const int32_t *__restrict__ Lb,
         int32_t kmin = INT32_MAX, kmax = -1;
         for (int64_t q = q0 + lane; q < q1; q += 32) {
             const int32_t y = adj_s[q];
-            const int64_t b = off_o[y], e = off_o[y + 1];
+            const int64_t b = off_o[y], e = b + len_o[y];
             if (e > b) {
                 kmin = min(kmin, adj_o[b]);
                 kmax = max(kmax, adj_o[e - 1]);
@@ -320,27 +329,44 @@ struct CdEmit {
     }
 };
 
+// Middle vertex y's list as it stands: the first len_o[y] entries from
+// off_o[y] (dynamic graph maintenance drops peeled vertices from the lists).
 struct PeelMids {
     const int32_t *adj_s;
     const int64_t *off_o;
+    const int32_t *len_o;
     __device__ __forceinline__ void seg(int64_t q, int64_t &beg, int32_t &len) const {
         int32_t y = adj_s[q];
         beg = off_o[y];
-        len = (int32_t)(off_o[y + 1] - beg);
+        len = len_o[y];
     }
 };
 
 // Segment of a middle vertex restricted to key slice j.
+// With a slice table, two loads give the bounds; without one (many slices),
+// two binary searches in the sorted list do.
 struct SlicedMids {
     const int32_t *adj_s;
     const int64_t *off_o;
-    const int32_t *soff;
+    const int32_t *soff;   // null: search the list
+    const int32_t *len_o;
+    const int32_t *adj_o;
     int32_t C1;  // C + 1
     int32_t j;
+    int32_t SW;
     __device__ __forceinline__ void seg(int64_t q, int64_t &beg, int32_t &len) const {
         int32_t y = adj_s[q];
-        const int32_t *so = soff + (size_t)y * C1 + j;
-        int32_t b = so[0], e = so[1];
+        int32_t b, e;
+        if (soff) {
+            const int32_t *so = soff + (size_t)y * C1 + j;
+            b = so[0];
+            e = so[1];
+        } else {
+            const int32_t *L = adj_o + off_o[y];
+            const int32_t l = len_o[y];
+            b = (int32_t)lower_bound_i32(L, l, j * SW);
+            e = b + (int32_t)lower_bound_i32(L + b, l - b, (j + 1) * SW);
+        }
         beg = off_o[y] + b;
         len = e - b;
     }
@@ -368,7 +394,8 @@ struct PeelArgs {
     const int64_t *off_s;
     const int32_t *adj_s;
     const int64_t *off_o;
-    const int32_t *adj_o;
+    const int32_t *len_o;  // current list lengths (dynamic graph maintenance)
+    const int32_t *adj_o;  // working copy of the other side's lists
     unsigned long long *sup;
     const int32_t *sub;
     CdDev *st;
@@ -413,7 +440,7 @@ __global__ void __launch_bounds__(256) k_cd_update_warp(PeelArgs a) {
             if (q < q1) {
                 int32_t y = a.adj_s[q];
                 beg = a.off_o[y];
-                len = (int32_t)(a.off_o[y + 1] - beg);
+                len = a.len_o[y];
             }
             int cnt = (int)imin64(32, q1 - qb);
             for (int t = 0; t < cnt; t++) {
@@ -454,7 +481,7 @@ struct PeelVisit {
     }
 };
 
-__global__ void __launch_bounds__(CTA_THREADS) k_cd_update_cta(PeelArgs a, int32_t head_cap,
+__global__ void __maxnreg__(64) k_cd_update_cta(PeelArgs a, int32_t head_cap,
                                                             int32_t bm_cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_idx, s_used, s_over;
@@ -469,7 +496,7 @@ __global__ void __launch_bounds__(CTA_THREADS) k_cd_update_cta(PeelArgs a, int32
     __syncthreads();
     const int32_t n = a.st->nLc;
     CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext};
-    PeelMids M{a.adj_s, a.off_o};
+    PeelMids M{a.adj_s, a.off_o, a.len_o};
     unsigned long long cw = 0, cm = 0, ca = 0;
     for (;;) {
         if (threadIdx.x == 0) s_idx = atomicAdd(&a.st->work[1], 1);
@@ -507,7 +534,7 @@ __global__ void __launch_bounds__(CTA_THREADS) k_cd_update_cta(PeelArgs a, int32
     }
 }
 
-__global__ void __launch_bounds__(CTA_THREADS) k_cd_update_global(PeelArgs a, uint32_t *gcnt,
+__global__ void __maxnreg__(64) k_cd_update_global(PeelArgs a, uint32_t *gcnt,
                                                                int32_t *gtouch, int64_t keyspace) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_idx, s_nt;
@@ -519,7 +546,7 @@ __global__ void __launch_bounds__(CTA_THREADS) k_cd_update_global(PeelArgs a, ui
     GlobalDense G{gcnt + (size_t)blockIdx.x * keyspace, gtouch + (size_t)blockIdx.x * keyspace, &s_nt};
     const int32_t n1 = a.st->nLg, n2 = 0;
     CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext};
-    PeelMids M{a.adj_s, a.off_o};
+    PeelMids M{a.adj_s, a.off_o, a.len_o};
     unsigned long long cw = 0, cm = 0, ca = 0;
     for (;;) {
         if (threadIdx.x == 0) {
@@ -593,7 +620,7 @@ __global__ void __launch_bounds__(SLICE_THREADS, 2) k_cd_update_slice(PeelArgs a
         const int32_t base = j * a.SW;
         const int32_t w = (int32_t)imin64(a.SW, (int64_t)n - base);
         H.set_width(w);
-        SlicedMids M{a.adj_s, a.off_o, a.soff, a.C + 1, j};
+        SlicedMids M{a.adj_s, a.off_o, a.soff, a.len_o, a.adj_o, a.C + 1, j, a.SW};
         const int32_t self = (x >= base && x < base + w) ? x - base : -1;
         SliceVisit<DenseSlice> v{&H, self, base};
         int64_t walked = cta_walk(M, q0, q1, a.adj_o, ch, v);
@@ -629,7 +656,7 @@ __global__ void __maxnreg__(64) k_cd_update_dense(PeelArgs a) {
     H.clear_all();
     __syncthreads();
     CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext};
-    PeelMids M{a.adj_s, a.off_o};
+    PeelMids M{a.adj_s, a.off_o, a.len_o};
     unsigned long long cw = 0, cm = 0, ca = 0;
     const int32_t n = a.st->nLd;
     for (;;) {
@@ -657,14 +684,52 @@ __global__ void __maxnreg__(64) k_cd_update_dense(PeelArgs a) {
     }
 }
 
+// Dynamic graph maintenance (Sec. 4.2): drops the vertices already assigned
+// to a subset from every list of the working copy, keeping each list sorted
+// (one warp per list, ballot compaction in place; the write position never
+// passes the read position).
+__global__ void k_dgm_compact(const int64_t *__restrict__ off_o, int32_t *__restrict__ len_o,
+                              int32_t *__restrict__ adj_w, int32_t n_o,
+                              const int32_t *__restrict__ sub) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t y = warp; y < n_o; y += nwarps) {
+        const int64_t b = off_o[y];
+        const int32_t l = len_o[y];
+        int32_t w = 0;
+        for (int32_t r0 = 0; r0 < l; r0 += 32) {
+            const int32_t r = r0 + lane;
+            int32_t x = -1;
+            bool keep = false;
+            if (r < l) {
+                x = adj_w[b + r];
+                keep = sub[x] < 0;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            __syncwarp();
+            if (keep) adj_w[b + w + __popc(bal & lanemask_lt())] = x;
+            w += __popc(bal);
+            __syncwarp();
+        }
+        if (lane == 0) len_o[y] = w;
+    }
+}
+
+__global__ void k_list_lengths(const int64_t *__restrict__ off, int32_t n, int32_t *__restrict__ len) {
+    int32_t y = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y < n) len[y] = (int32_t)(off[y + 1] - off[y]);
+}
+
 // soff[y * (C + 1) + j] = number of entries of N_y below j * SW (j = 0..C).
-__global__ void k_slice_table(const int64_t *__restrict__ off_o, const int32_t *__restrict__ adj_o,
-                              int32_t n_o, int32_t C, int32_t SW, int32_t *__restrict__ soff) {
+__global__ void k_slice_table(const int64_t *__restrict__ off_o, const int32_t *__restrict__ len_o,
+                              const int32_t *__restrict__ adj_o, int32_t n_o, int32_t C, int32_t SW,
+                              int32_t *__restrict__ soff) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t tot = (int64_t)n_o * (C + 1);
     if (i >= tot) return;
     int32_t y = (int32_t)(i / (C + 1)), j = (int32_t)(i % (C + 1));
-    int64_t b = off_o[y], e = off_o[y + 1];
+    int64_t b = off_o[y], e = b + len_o[y];
     soff[i] = j == C ? (int32_t)(e - b) : (int32_t)lower_bound_i32(adj_o + b, e - b, j * SW);
 }
 
@@ -740,11 +805,23 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
     // key slices for anchors with many wedges
     const int32_t SW = SLICE_KEYS;
     const int32_t C = std::max(1, ceil_div(n, SW));
-    DevBuf<int32_t> soff((size_t)O.n * (C + 1), s);
+    // slice table (C + 1 starts per list) only while slices are few
+    const bool table = C <= 64;
+    DevBuf<int32_t> soff(table ? (size_t)O.n * (C + 1) : 1, s);
+    // working copy of the other side's lists, compacted between ranges
+    DevBuf<int32_t> adj_w(D.m, s), len_w(O.n, s);
+    if (D.m > 0)
+        RC_CUDA(cudaMemcpyAsync(adj_w.get(), O.adj, sizeof(int32_t) * D.m, cudaMemcpyDeviceToDevice, s));
+    const bool dgm = !opt.no_dgm;
+    uint64_t peeled_at_dgm = 0;
     if (O.n > 0) {
-        k_slice_table<<<ceil_div((int64_t)O.n * (C + 1), 256), 256, 0, s>>>(O.off, O.adj, O.n, C,
-                                                                          SW, soff.get());
+        k_list_lengths<<<ceil_div(O.n, 256), 256, 0, s>>>(O.off, O.n, len_w.get());
         RC_LAUNCH();
+        if (table) {
+            k_slice_table<<<ceil_div((int64_t)O.n * (C + 1), 256), 256, 0, s>>>(
+                O.off, len_w.get(), adj_w.get(), O.n, C, SW, soff.get());
+            RC_LAUNCH();
+        }
     }
     const size_t smem_slice = DenseSlice::bytes() + CHUNK_BYTES;
     allow_max_smem((const void *)k_cd_update_slice);
@@ -816,19 +893,19 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
         k_cd_frontier<<<nb, 512, 0, s>>>(n, D.sub, D.sup, st.get(), cur);
         RC_LAUNCH();
         for (;;) {
-            k_cd_prepare<<<nb, 512, 0, s>>>(cur, st.get(), range, D.sub, D.sup, D.wfull, Lw.get(),
-                                            Lb.get(), warp_max_w);
+            k_cd_prepare<<<nb, 512, 0, s>>>(cur, st.get(), range, D.sub, D.sup, D.wfull, S.off,
+                                            Lw.get(), Lb.get(), warp_max_w);
             RC_LAUNCH();
-            k_cd_route<<<sms * 8, 256, 0, s>>>(st.get(), Lb.get(), S.off, S.adj, O.off, O.adj,
-                                               D.wfull, cta_ok ? cta_keys : 0, slice_min_w, SW,
+            k_cd_route<<<sms * 8, 256, 0, s>>>(st.get(), Lb.get(), S.off, S.adj, O.off, len_w.get(),
+                                               adj_w.get(), D.wfull, cta_ok ? cta_keys : 0, slice_min_w, SW,
                                                Lc.get(), Lc_k.get(), Lc_w.get(), Ld.get(),
                                                Ld_k.get(), Lg.get(), Ls.get(), Ls_lo.get(),
                                                Ls_hi.get());
             RC_LAUNCH();
-            PeelArgs a{S.off,     S.adj,      O.off,       O.adj,       D.sup,    D.sub,
+            PeelArgs a{S.off,     S.adj,      O.off,       len_w.get(), adj_w.get(), D.sup, D.sub,
                        st.get(),  Lw.get(),   Lc.get(),    Lg.get(),    Ls.get(), nxt,
                        Lc_k.get(), Lc_w.get(), Ls_lo.get(), Ls_hi.get(), Ld.get(), Ld_k.get(),
-                       soff.get(), C,         SW,          n};
+                       table ? soff.get() : nullptr, C, SW, n};
             if (D.timing) RC_CUDA(cudaEventRecord(ev[0], s));
             k_cd_update_warp<<<sms * 8, 256, 0, s>>>(a);
             RC_LAUNCH();
@@ -885,6 +962,23 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
             std::swap(cur, nxt);
         }
         D.bounds.push_back(hi);
+        // dynamic graph maintenance: once the vertices assigned since the last
+        // compaction hold DGM_FRAC of the live adjacency entries, drop them
+        // from the lists
+        const uint64_t peeled_now = hst->peeled_edges;
+        if (dgm && O.n > 0 && range + 1 < nranges &&
+            (double)(peeled_now - peeled_at_dgm) >= DGM_FRAC * (double)(D.m - peeled_at_dgm)) {
+            k_dgm_compact<<<std::min(ceil_div((int64_t)O.n * 32, 256), sms * 32), 256, 0, s>>>(
+                O.off, len_w.get(), adj_w.get(), O.n, D.sub);
+            RC_LAUNCH();
+            if (table) {
+                k_slice_table<<<ceil_div((int64_t)O.n * (C + 1), 256), 256, 0, s>>>(
+                    O.off, len_w.get(), adj_w.get(), O.n, C, SW, soff.get());
+                RC_LAUNCH();
+            }
+            peeled_at_dgm = peeled_now;
+            D.dgm_passes++;
+        }
     }
     // leftover subset with an open range
     DevBuf<int> any(1, s);

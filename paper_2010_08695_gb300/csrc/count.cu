@@ -221,7 +221,7 @@ __device__ unsigned long long block_sum_u64(unsigned long long v, unsigned long 
     return r;
 }
 
-__global__ void __launch_bounds__(CTA_THREADS) k_count_cta(CountArgs a, int32_t head_cap,
+__global__ void __maxnreg__(64) k_count_cta(CountArgs a, int32_t head_cap,
                                                         int32_t bm_cap, int32_t *over_list,
                                                         int32_t *n_over) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(CTA_THREADS) k_count_cta(CountArgs a, int32_t 
     }
 }
 
-__global__ void __launch_bounds__(CTA_THREADS) k_count_global(CountArgs a, const int32_t *over_list,
+__global__ void __maxnreg__(64) k_count_global(CountArgs a, const int32_t *over_list,
                                                            const int32_t *n_over, uint32_t *gcnt,
                                                            int32_t *gtouch, int64_t keyspace) {
     extern __shared__ __align__(16) unsigned char smem[];

@@ -450,14 +450,14 @@ struct GlobalDense {
 // ------------------------------------------------------------------
 // CTA traversal of one anchor's wedges
 // ------------------------------------------------------------------
-// Chunk staging in shared memory: up to MID_CHUNK middle vertices, their
-// segment starts and lengths, and the exclusive prefix of their 32-wedge
-// piece counts.
+// Chunk staging in shared memory: up to MID_CHUNK middle vertices with
+// non-empty segments, compacted: segment start, exclusive prefix of segment
+// lengths, and the mid's index within the chunk.
 struct Chunk {
     int64_t *beg;    // MID_CHUNK
-    int32_t *pre;    // MID_CHUNK + 1: prefix of pieces
-    int32_t *tmp;    // 33 (scan scratch)
-    int32_t *len;    // MID_CHUNK
+    int32_t *pre;    // MID_CHUNK + 1
+    int32_t *tmp;    // 36 (scan scratch)
+    int32_t *len;    // MID_CHUNK: chunk-local mid index of compacted segment k
 };
 
 constexpr size_t CHUNK_BYTES = MID_CHUNK * 8 + (MID_CHUNK + 1) * 4 + 33 * 4 + MID_CHUNK * 4 + 16;
@@ -469,10 +469,14 @@ struct NoChunkHook {
 };
 
 // Walks every wedge of one anchor: for q in [q0, q1) (middle vertices), the
-// segment M.seg(q) of `keys`. The segments of up to blockDim.x middle
-// vertices are staged at a time and cut into 32-wedge pieces; warps take
-// WALK_UNROLL consecutive pieces per step, locate each piece's segment once
-// (warp-uniform) and issue all their loads before visiting any key.
+// segment M.seg(q) of `keys`. The non-empty segments of up to blockDim.x
+// middle vertices are staged at a time; the flat list of their wedges is cut
+// into 32-wedge groups and each warp takes WALK_UNROLL consecutive groups per
+// step. In a group, lane i fetches the start of the i-th segment after the
+// group's first one; one OR-reduction of those starts gives every lane the
+// segment its wedge falls in (a population count), so every lane loads a key
+// even when segments are short, and all loads of a step are issued before any
+// key is visited.
 // Mids source contract:
 //   __device__ void seg(int64_t q, int64_t &beg, int32_t &len) const;
 // visit(k, key): k = mid index within the chunk, key = end point.
@@ -482,44 +486,51 @@ __device__ int64_t cta_walk(const Mids &M, int64_t q0, int64_t q1, const int32_t
                             Chunk &ch, Visit &visit, Hook *hook = nullptr) {
     int64_t walked = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const unsigned lanes_le = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
     for (int64_t c0 = q0; c0 < q1; c0 += blockDim.x) {
         const int nm = (int)imin64(blockDim.x, q1 - c0);
         int64_t beg = 0;
         int32_t len = 0;
         if ((int)threadIdx.x < nm) M.seg(c0 + threadIdx.x, beg, len);
-        int32_t total;
-        const int32_t pieces = (len + 31) >> 5;
-        int32_t ex = block_exclusive_scan<int32_t>(pieces, ch.tmp, &total);
-        ch.beg[threadIdx.x] = beg;
-        ch.len[threadIdx.x] = len;
-        ch.pre[threadIdx.x] = ex;
-        if (threadIdx.x == 0) ch.pre[blockDim.x] = total;
-        int32_t wsum = len;
-        wsum = warp_sum(wsum);
+        int32_t total, nnz;
+        const int32_t ex = block_exclusive_scan<int32_t>(len, ch.tmp, &total);
+        const int32_t slot = block_exclusive_scan<int32_t>(len > 0 ? 1 : 0, ch.tmp, &nnz);
+        if (len > 0) {
+            ch.beg[slot] = beg;
+            ch.pre[slot] = ex;
+            ch.len[slot] = threadIdx.x;
+        }
+        if (threadIdx.x == 0) ch.pre[nnz] = total;
         __syncthreads();
-        for (int32_t pb = warp * WALK_UNROLL; pb < total; pb += nwarps * WALK_UNROLL) {
-            // segment of piece pb: largest k with pre[k] <= pb (warp-uniform)
-            int lo = 0, hi = nm - 1;
+        const int32_t groups = (total + 31) >> 5;
+        for (int32_t gb = warp * WALK_UNROLL; gb < groups; gb += nwarps * WALK_UNROLL) {
+            // segment of the first wedge of group gb (warp-uniform search)
+            int lo = 0, hi = nnz - 1;
+            const int32_t b0 = gb << 5;
             while (lo < hi) {
                 int mid = (lo + hi + 1) >> 1;
-                if (ch.pre[mid] <= pb)
+                if (ch.pre[mid] <= b0)
                     lo = mid;
                 else
                     hi = mid - 1;
             }
-            int k = lo;
+            int k0 = lo;
             int kk[WALK_UNROLL];
             int32_t key[WALK_UNROLL];
 #pragma unroll
             for (int u = 0; u < WALK_UNROLL; u++) {
-                const int32_t piece = pb + u;
+                const int32_t base = (gb + u) << 5;
                 kk[u] = -1;
-                if (piece < total) {
-                    while (ch.pre[k + 1] <= piece) k++;
-                    const int32_t off = ((piece - ch.pre[k]) << 5) + lane;
-                    if (off < ch.len[k]) {
-                        kk[u] = k;
-                        key[u] = __ldg(keys + ch.beg[k] + off);
+                if (base < total) {
+                    while (ch.pre[k0 + 1] <= base) k0++;
+                    const int kn = k0 + 1 + lane;
+                    const int32_t bnd = kn < nnz ? ch.pre[kn] - base : 32;
+                    const unsigned m = __reduce_or_sync(0xffffffffu, bnd < 32 ? (1u << bnd) : 0u);
+                    const int k = k0 + __popc(m & lanes_le);
+                    const int32_t j = base + lane;
+                    if (j < total) {
+                        kk[u] = ch.len[k];
+                        key[u] = __ldg(keys + ch.beg[k] + (j - ch.pre[k]));
                     }
                 }
             }
@@ -527,12 +538,7 @@ __device__ int64_t cta_walk(const Mids &M, int64_t q0, int64_t q1, const int32_t
             for (int u = 0; u < WALK_UNROLL; u++)
                 if (kk[u] >= 0) visit(kk[u], key[u]);
         }
-        // wedges of this chunk (sum of segment lengths)
-        if (lane == 0) ch.tmp[warp] = wsum;
-        __syncthreads();
-        int32_t cw = 0;
-        for (int w = 0; w < nwarps; w++) cw += ch.tmp[w];
-        walked += cw;
+        walked += total;
         __syncthreads();
         if (hook) {
             (*hook)(c0, nm);

@@ -50,6 +50,7 @@ struct Decomp {
     std::vector<uint64_t> bounds;         // theta(1..p_eff+1)
     uint64_t wedges_cd = 0, wedges_fd = 0;
     int64_t rounds = 0, levels = 0;
+    int32_t dgm_passes = 0;
     bool timing = false;
     uint64_t tier_wedges[5] = {}, tier_mids[5] = {};
     uint64_t tier_anchors[5] = {};

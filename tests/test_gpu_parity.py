@@ -183,6 +183,8 @@ def test_any_P_and_injected_ranges_give_same_tips(R):
         lo = bounds[sub]
         hi = bounds[sub + 1]
         assert (lo <= t).all() and (t < hi).all(), f"P={P}"
+    t = R.as_u64(g.tip_decompose(0, dgm=False))  # without dynamic graph maintenance
+    assert np.array_equal(t, want)
     rng = np.random.default_rng(3)
     top = int(want.max()) + 2
     for trial in range(4):
