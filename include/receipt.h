@@ -159,6 +159,10 @@ receipt_status receipt_graph_destroy(receipt_graph *g);
 receipt_status receipt_graph_info(const receipt_graph *g, int32_t *nu, int32_t *nv,
                                   int64_t *m);
 
+/* Largest degree on each side of a built graph. Any pointer may be NULL. */
+receipt_status receipt_graph_max_degree(const receipt_graph *g, int32_t *max_deg_u,
+                                        int32_t *max_deg_v);
+
 /*
  * Per-vertex butterfly counts of both sides (Algorithm 1, pvBcnt).
  *   d_cnt_u : device uint64[nu] or NULL; d_cnt_v : device uint64[nv] or NULL.

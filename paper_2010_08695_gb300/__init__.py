@@ -108,6 +108,8 @@ def load(build_if_missing: bool = True):
         lib.receipt_graph_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                            ctypes.POINTER(i64)]
         lib.receipt_count_butterflies.argtypes = [vp, vp, vp, vp]
+        lib.receipt_graph_max_degree.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        lib.receipt_graph_max_degree.restype = ctypes.c_int
         lib.receipt_count_butterflies_noalloc.argtypes = [vp, vp, vp, vp]
         lib.receipt_count_butterflies_noalloc.restype = ctypes.c_int
         lib.receipt_tip_decompose.argtypes = [vp, ctypes.c_int, vp, ctypes.POINTER(Options), vp]
@@ -258,6 +260,14 @@ class Graph:
         _check(load().receipt_graph_info(self._h, ctypes.byref(nu_), ctypes.byref(nv_),
                                          ctypes.byref(m_)))
         self.m = int(m_.value)
+        du, dv = ctypes.c_int32(), ctypes.c_int32()
+        _check(load().receipt_graph_max_degree(self._h, ctypes.byref(du), ctypes.byref(dv)))
+        self.max_degree = (int(du.value), int(dv.value))
+
+    def shape_class(self, side: int) -> str:
+        """Key of this graph in the autotuner's table."""
+        from . import autotune
+        return autotune.shape_class(self.nu, self.nv, self.m, side, self.max_degree[1 - side])
 
     @property
     def handle(self):
@@ -293,6 +303,11 @@ class Graph:
         bout = np.zeros(P + (len(bounds) if bounds is not None else 0) + 4, np.uint64) \
             if subsets else None
         peff = ctypes.c_int32(0)
+        if not warp_max_w and not slice_min_w:
+            from . import autotune
+            tuned = autotune.lookup(self.shape_class(side))
+            if tuned:
+                warp_max_w, slice_min_w = tuned["warp_max_w"], tuned["slice_min_w"]
         o, keep = _options(P, bounds, sub, bout, peff, timing, warp_max_w, slice_min_w, dgm)
         receipt_tip_decompose(self._h, side, tip, o, stream)
         if subsets:

@@ -464,6 +464,15 @@ receipt_status receipt_graph_info(const receipt_graph *g, int32_t *nu, int32_t *
     });
 }
 
+receipt_status receipt_graph_max_degree(const receipt_graph *g, int32_t *max_deg_u,
+                                        int32_t *max_deg_v) {
+    return guarded([&] {
+        if (!g) fail(RECEIPT_ERR_INVALID, "null graph");
+        if (max_deg_u) *max_deg_u = g->max_deg[0];
+        if (max_deg_v) *max_deg_v = g->max_deg[1];
+    });
+}
+
 receipt_status receipt_count_butterflies(receipt_graph *g, uint64_t *d_cnt_u, uint64_t *d_cnt_v,
                                          void *stream) {
     return guarded([&] {

@@ -1,0 +1,28 @@
+"""Autotuner table logic on the CPU: shape classes and lookups."""
+import json
+
+from paper_2010_08695_gb300 import autotune
+
+
+def test_shape_class_buckets_by_powers_of_two():
+    a = autotune.shape_class(1_000_000, 200_000, 10_000_000, 0, 43649)
+    b = autotune.shape_class(1_050_000, 190_000, 10_400_000, 0, 45000)
+    assert a == b == "s20-o18-m23-d15"
+    assert autotune.shape_class(200_000, 1_000_000, 10_000_000, 1, 43649) == a
+
+
+def test_lookup_reads_the_table(tmp_path, monkeypatch):
+    path = tmp_path / "t.json"
+    path.write_text(json.dumps({"s1-o1-m1-d1": {"warp_max_w": 64, "slice_min_w": 5}}))
+    monkeypatch.setenv("RECEIPT_TUNING", str(path))
+    monkeypatch.setattr(autotune, "_table", None)
+    assert autotune.lookup("s1-o1-m1-d1")["slice_min_w"] == 5
+    assert autotune.lookup("nope") is None
+    monkeypatch.setattr(autotune, "_table", None)
+
+
+def test_shipped_table_is_valid():
+    with open(autotune.SHIPPED) as f:
+        table = json.load(f)
+    for key, rec in table.items():
+        assert 0 < rec["warp_max_w"] <= 256 and rec["slice_min_w"] > 0
