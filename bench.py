@@ -292,12 +292,17 @@ def run_ours(args):
         gold = json.load(open(gpath))
         gold_ok = hashlib.sha256(tips.astype("<u8").tobytes()).hexdigest() == gold["tips_sha256"]
 
+    from paper_2010_08695_gb300 import autotune
+    g0 = R.Graph(eu_d, ev_d, nu, nv, stream=stream)
+    tuned = autotune.lookup(g0.shape_class(side)) or {}
+    g0.close()
     line = {"metric": METRIC, "value": value, "unit": "wedges/s", "n_gpus": world,
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "nu": nu, "nv": nv, "m": int(len(eu)), "side": "U",
-                       "P": 150, "wedges_bup": wedges, "parallelism": "replicas" if world > 1
+                       "P": tuned.get("P", 150), "tuning": tuned or "defaults",
+                       "wedges_bup": wedges, "parallelism": "replicas" if world > 1
                        else "single", "l2": "flushed between steps (256 MiB write)"},
             "seconds_per_step": ms / 1e3,
             "bit_exact_vs_oracle": gold_ok,

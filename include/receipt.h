@@ -90,6 +90,10 @@ typedef struct {
      * the coarse-grained step drops peeled vertices from a working copy of
      * the adjacency lists). Speed only; results are the same. */
     int32_t no_dgm;
+    /* Share of the live adjacency entries that must belong to assigned
+     * vertices before the lists are compacted again, in 1/1024 units
+     * (0 = 128, i.e. 1/8). Speed only. */
+    int32_t dgm_frac_1024;
 } receipt_options;
 
 /* Counters of the last call on a graph (Sec. 5: wedges and rounds). */

@@ -46,7 +46,7 @@ class Options(ctypes.Structure):
                 ("h_bounds_out", ctypes.POINTER(ctypes.c_uint64)), ("h_bounds_cap", ctypes.c_int32),
                 ("h_p_eff", ctypes.POINTER(ctypes.c_int32)), ("timing", ctypes.c_int32),
                 ("warp_max_w", ctypes.c_int32), ("slice_min_w", ctypes.c_int32),
-                ("no_dgm", ctypes.c_int32)]
+                ("no_dgm", ctypes.c_int32), ("dgm_frac_1024", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -162,10 +162,11 @@ def _dptr(t):
 
 
 def _options(P=150, bounds=None, subset=None, bounds_out=None, p_eff=None, timing=False,
-             warp_max_w=0, slice_min_w=0, dgm=True):
+             warp_max_w=0, slice_min_w=0, dgm=True, dgm_frac_1024=0):
     o = Options()
     load().receipt_options_default(ctypes.byref(o))
     o.P = int(P)
+    o.dgm_frac_1024 = int(dgm_frac_1024)
     o.no_dgm = 0 if dgm else 1
     o.warp_max_w = int(warp_max_w)
     o.slice_min_w = int(slice_min_w)
@@ -292,23 +293,31 @@ class Graph:
         receipt_count_butterflies(self._h, cu, cv, stream)
         return cu, cv
 
-    def tip_decompose(self, side: int = SIDE_U, P: int = 150, bounds=None, subsets=False,
-                      timing=False, out=None, stream=None, warp_max_w=0, slice_min_w=0, dgm=True):
-        """Tip numbers of ``side`` (Algorithms 3 and 4). With ``subsets=True``
+    def tip_decompose(self, side: int = SIDE_U, P: int = 0, bounds=None, subsets=False,
+                      timing=False, out=None, stream=None, warp_max_w=0, slice_min_w=0, dgm=True,
+                      dgm_frac_1024=0):
+        """Tip numbers of ``side`` (Algorithms 3 and 4). P = 0 takes the tuned
+        value for this graph's shape class, else 150. With ``subsets=True``
         returns ``(tips, subset_of_vertex, range_bounds)``."""
         import torch
         n = self.nu if side == SIDE_U else self.nv
+        tuned = None
+        if not (warp_max_w and slice_min_w and P):
+            from . import autotune
+            tuned = autotune.lookup(self.shape_class(side))
+        if tuned:
+            warp_max_w = warp_max_w or tuned["warp_max_w"]
+            slice_min_w = slice_min_w or tuned["slice_min_w"]
+            P = P or tuned.get("P", 150)
+            dgm_frac_1024 = dgm_frac_1024 or tuned.get("dgm_frac_1024", 0)
+        P = P or 150
         tip = out if out is not None else torch.empty(n, dtype=torch.int64, device=self.device)
         sub = torch.empty(n, dtype=torch.int32, device=self.device) if subsets else None
         bout = np.zeros(P + (len(bounds) if bounds is not None else 0) + 4, np.uint64) \
             if subsets else None
         peff = ctypes.c_int32(0)
-        if not warp_max_w and not slice_min_w:
-            from . import autotune
-            tuned = autotune.lookup(self.shape_class(side))
-            if tuned:
-                warp_max_w, slice_min_w = tuned["warp_max_w"], tuned["slice_min_w"]
-        o, keep = _options(P, bounds, sub, bout, peff, timing, warp_max_w, slice_min_w, dgm)
+        o, keep = _options(P, bounds, sub, bout, peff, timing, warp_max_w, slice_min_w, dgm,
+                           dgm_frac_1024)
         receipt_tip_decompose(self._h, side, tip, o, stream)
         if subsets:
             return tip, sub, bout[: peff.value + 1]

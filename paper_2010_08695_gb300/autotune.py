@@ -4,8 +4,9 @@ The coarse-grained peel update sends each peeled vertex (anchor) to one of
 several aggregation tiers by its wedge count: a warp with a private table (at
 most `warp_max_w` wedges), one CTA with the hybrid shared-memory engine over
 the anchor's key window, or (more than `slice_min_w` wedges) CTAs that each
-aggregate one key slice. The best thresholds depend on the graph's degree
-distribution. `tune()` times every candidate pair on a built graph with CUDA
+aggregate one key slice. The number of subsets P (the paper's Fig. 4 sweeps
+it) and how often dynamic graph maintenance compacts the lists are tuned the
+same way. The best values depend on the graph's degree distribution. `tune()` times every candidate pair on a built graph with CUDA
 events and records the fastest under a shape class of the graph (powers of
 two of the side sizes, the edge count and the largest degree of the other
 side); `lookup()` returns the recorded thresholds for a graph of the same
@@ -25,7 +26,9 @@ import threading
 _HERE = os.path.dirname(os.path.abspath(__file__))
 SHIPPED = os.path.join(_HERE, "tuned.json")
 WARP_MAX_W = (64, 128, 256)
-SLICE_MIN_W = (32768, 49152, 98304, 196608, 393216, 1 << 30)
+SLICE_MIN_W = (49152, 98304, 196608, 1 << 30)
+P_CANDIDATES = (100, 150, 300, 600)
+DGM_FRAC_1024 = (32, 64, 128, 256)
 _lock = threading.Lock()
 _table = None
 
@@ -58,29 +61,48 @@ def lookup(key: str):
     return _load().get(key)
 
 
-def tune(graph, side: int, key: str, P: int = 150, reps: int = 1, save: bool = True,
-         candidates=None):
-    """Times each candidate (warp_max_w, slice_min_w) on `graph` and records
-    the fastest under `key`. Returns (best, all timings in ms)."""
+def _time(graph, side, out, reps, **kw):
     import torch
-    cands = candidates or [(w, s) for w in WARP_MAX_W for s in SLICE_MIN_W]
+    best = float("inf")
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        graph.tip_decompose(side, out=out, **kw)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def tune(graph, side: int, key: str, reps: int = 1, save: bool = True):
+    """Coordinate search on `graph`: the tier thresholds (warp_max_w,
+    slice_min_w) at P = 150, then P, then the compaction trigger of dynamic
+    graph maintenance. Records the fastest setting under `key` and returns
+    (best, all timings in ms)."""
+    import torch
     n = graph.nu if side == 0 else graph.nv
     out = torch.empty(n, dtype=torch.int64, device=graph.device)
-    graph.tip_decompose(side, P=P, out=out)  # warm-up
+    base = dict(P=150, dgm_frac_1024=128)
+    graph.tip_decompose(side, out=out, warp_max_w=256, slice_min_w=SLICE_MIN_W[1], **base)
     times = {}
-    for w, s in cands:
-        best = float("inf")
-        for _ in range(reps):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            graph.tip_decompose(side, P=P, out=out, warp_max_w=w, slice_min_w=s)
-            e1.record()
-            e1.synchronize()
-            best = min(best, e0.elapsed_time(e1))
-        times[f"{w},{s}"] = best
-    w, s = map(int, min(times, key=times.get).split(","))
-    rec = {"warp_max_w": w, "slice_min_w": s, "ms": times[f"{w},{s}"]}
+    for w in WARP_MAX_W:
+        for s in SLICE_MIN_W:
+            times[f"w{w},s{s},P150,f128"] = _time(graph, side, out, reps, warp_max_w=w,
+                                                  slice_min_w=s, **base)
+    best = min(times, key=times.get)
+    w, s = (int(t[1:]) for t in best.split(",")[:2])
+    for P in P_CANDIDATES:
+        times[f"w{w},s{s},P{P},f128"] = _time(graph, side, out, reps, warp_max_w=w, slice_min_w=s,
+                                              P=P, dgm_frac_1024=128)
+    best = min(times, key=times.get)
+    P = int(best.split(",")[2][1:])
+    for f in DGM_FRAC_1024:
+        times[f"w{w},s{s},P{P},f{f}"] = _time(graph, side, out, reps, warp_max_w=w,
+                                              slice_min_w=s, P=P, dgm_frac_1024=f)
+    best = min(times, key=times.get)
+    w, s, P, f = (int(t[1:]) for t in best.split(","))
+    rec = {"warp_max_w": w, "slice_min_w": s, "P": P, "dgm_frac_1024": f, "ms": times[best]}
     if save:
         table = dict(_load())
         table[key] = rec

@@ -813,6 +813,7 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
     if (D.m > 0)
         RC_CUDA(cudaMemcpyAsync(adj_w.get(), O.adj, sizeof(int32_t) * D.m, cudaMemcpyDeviceToDevice, s));
     const bool dgm = !opt.no_dgm;
+    const double dgm_frac = opt.dgm_frac_1024 > 0 ? opt.dgm_frac_1024 / 1024.0 : DGM_FRAC;
     uint64_t peeled_at_dgm = 0;
     if (O.n > 0) {
         k_list_lengths<<<ceil_div(O.n, 256), 256, 0, s>>>(O.off, O.n, len_w.get());
@@ -967,7 +968,7 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
         // from the lists
         const uint64_t peeled_now = hst->peeled_edges;
         if (dgm && O.n > 0 && range + 1 < nranges &&
-            (double)(peeled_now - peeled_at_dgm) >= DGM_FRAC * (double)(D.m - peeled_at_dgm)) {
+            (double)(peeled_now - peeled_at_dgm) >= dgm_frac * (double)(D.m - peeled_at_dgm)) {
             k_dgm_compact<<<std::min(ceil_div((int64_t)O.n * 32, 256), sms * 32), 256, 0, s>>>(
                 O.off, len_w.get(), adj_w.get(), O.n, D.sub);
             RC_LAUNCH();
