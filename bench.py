@@ -47,9 +47,12 @@ METRIC = "wedges/s and end-to-end tip-decomp seconds on 1 GB300 (bit-exact); HBM
 WORKLOAD = "chung-lu |U|=1M |V|=200k m=10M gamma 2.5/2.1 seed 2, U side"
 CPU_SAMPLE_WEDGES = 1_500_000_000  # peel wedges per oracle sample (~10-20 s on one core)
 
-# DRAM bytes per launch of the dominant kernel from an ncu capture, keyed by
-# kernel name; valid only while the kernel sources hash to the same digest.
-NCU_TRAFFIC = {}
+# DRAM traffic of the dominant kernel from one full-size ncu capture, as DRAM
+# bytes per algorithmic byte of the captured launch (scaled to the average
+# launch of the timed step), keyed by kernel name; valid only while the kernel
+# sources hash to the recorded digest. k_cd_update_cta: CD round 4 of the
+# 10M-edge Chung-Lu workload, 49.13 MB of DRAM for ~971 MB algorithmic.
+NCU_TRAFFIC = {"k_cd_update_cta": {"src": "5e444b0c3464412d", "dram_per_alg_byte": 0.0506}}
 
 
 def _rank_env():
@@ -285,7 +288,7 @@ def run_ours(args):
     traffic = None
     tr = NCU_TRAFFIC.get(names[tier])
     if tr and tr.get("src") == _src_digest():
-        traffic = tr["bytes_per_launch"]
+        traffic = int(tr["dram_per_alg_byte"] * alg_bytes)
     gold_ok = None
     gpath = os.path.join(ROOT, "tests", "golden", "cfg2.json")
     if os.path.exists(gpath):
