@@ -316,6 +316,8 @@ def run_ours(args):
             "rounds_cd": st["rounds_cd"], "levels_fd": st["levels_fd"], "subsets": st["p_eff"],
             "fd_slowest_subset": {"ms": st["ms_fd_max_subset"], "n": st["fd_max_subset_n"],
                                   "levels": st["fd_max_subset_levels"]},
+            "fd_heavy": {"subsets": st["fd_heavy_subsets"], "ms": st["ms_fd_heavy"],
+                         "levels": st["levels_fd_heavy"]},
             "peel_tier_wedges": st["peel_wedges"], "peel_tier_anchors": st["peel_anchors"],
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": names[tier],

@@ -94,6 +94,12 @@ typedef struct {
      * vertices before the lists are compacted again, in 1/1024 units
      * (0 = 128, i.e. 1/8). Speed only. */
     int32_t dgm_frac_1024;
+    /* Fine-grained step (Algorithm 4): subsets whose wedge count (the LPT key
+     * of Sec. 3.2.1, sum of L(L-1) over the runs L of G_i) is at least this
+     * are peeled by all CTAs level by level instead of by one CTA of the
+     * persistent queue. 0 = automatic (8 times the mean share of one CTA and
+     * at least 2^23), -1 = never. Speed only. */
+    int64_t fd_heavy_w;
 } receipt_options;
 
 /* Counters of the last call on a graph (Sec. 5: wedges and rounds). */
@@ -123,6 +129,11 @@ typedef struct {
     float ms_fd_max_subset;
     int32_t fd_max_subset_n;
     int64_t fd_max_subset_levels;
+    /* Subsets peeled by all CTAs level by level (see fd_heavy_w), their
+     * summed device time (globaltimer) and levels. */
+    int32_t fd_heavy_subsets;
+    float ms_fd_heavy;
+    int64_t levels_fd_heavy;
 } receipt_stats;
 
 /* One synchronisation round of the coarse-grained step (Algorithm 3). */
@@ -134,6 +145,16 @@ typedef struct {
     uint64_t wedges[5];   /* wedges walked, per peel tier                     */
     float ms[5];          /* device time per peel tier (only if timing != 0)  */
 } receipt_round;
+
+/* One subset of the fine-grained step (Algorithm 4, Sec. 3.2.1). */
+typedef struct {
+    int32_t n;             /* vertices in U_i                                  */
+    int32_t heavy;         /* 1: peeled by all CTAs level by level             */
+    int64_t levels;        /* peeling levels                                   */
+    uint64_t wedges_est;   /* LPT key: sum of L(L-1) over the runs L of G_i    */
+    float ms;              /* device time (globaltimer)                        */
+    int32_t pad;
+} receipt_subset;
 
 /* Fills `opt` with the defaults (P = 150, nothing optional). */
 void receipt_options_default(receipt_options *opt);
@@ -308,6 +329,12 @@ receipt_status receipt_get_stats(const receipt_graph *g, receipt_stats *out);
  * records to `out` (host array) and the number of rounds to *n_rounds. */
 receipt_status receipt_get_trace(const receipt_graph *g, receipt_round *out, int32_t cap,
                                  int32_t *n_rounds);
+
+/* Subsets of the last tip decomposition on g (one record per subset, in
+ * subset order): copies up to `cap` records to `out` (host array) and the
+ * number of subsets to *n_subsets. */
+receipt_status receipt_get_subsets(const receipt_graph *g, receipt_subset *out, int32_t cap,
+                                   int32_t *n_subsets);
 
 /* Thread-local text of the last error on the calling thread ("" if none). */
 const char *receipt_last_error(void);

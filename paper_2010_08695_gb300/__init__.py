@@ -46,7 +46,8 @@ class Options(ctypes.Structure):
                 ("h_bounds_out", ctypes.POINTER(ctypes.c_uint64)), ("h_bounds_cap", ctypes.c_int32),
                 ("h_p_eff", ctypes.POINTER(ctypes.c_int32)), ("timing", ctypes.c_int32),
                 ("warp_max_w", ctypes.c_int32), ("slice_min_w", ctypes.c_int32),
-                ("no_dgm", ctypes.c_int32), ("dgm_frac_1024", ctypes.c_int32)]
+                ("no_dgm", ctypes.c_int32), ("dgm_frac_1024", ctypes.c_int32),
+                ("fd_heavy_w", ctypes.c_int64)]
 
 
 class Stats(ctypes.Structure):
@@ -59,13 +60,20 @@ class Stats(ctypes.Structure):
                 ("peel_wedges", ctypes.c_uint64 * 5), ("peel_mids", ctypes.c_uint64 * 5),
                 ("peel_anchors", ctypes.c_uint64 * 5), ("peel_launches", ctypes.c_int64 * 5),
                 ("ms_peel", ctypes.c_float * 5), ("ms_fd_max_subset", ctypes.c_float),
-                ("fd_max_subset_n", ctypes.c_int32), ("fd_max_subset_levels", ctypes.c_int64)]
+                ("fd_max_subset_n", ctypes.c_int32), ("fd_max_subset_levels", ctypes.c_int64),
+                ("fd_heavy_subsets", ctypes.c_int32), ("ms_fd_heavy", ctypes.c_float),
+                ("levels_fd_heavy", ctypes.c_int64)]
 
 
 class Round(ctypes.Structure):
     _fields_ = [("range", ctypes.c_int32), ("frontier", ctypes.c_int32), ("hi", ctypes.c_uint64),
                 ("anchors", ctypes.c_uint64 * 5), ("wedges", ctypes.c_uint64 * 5),
                 ("ms", ctypes.c_float * 5)]
+
+
+class Subset(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("heavy", ctypes.c_int32), ("levels", ctypes.c_int64),
+                ("wedges_est", ctypes.c_uint64), ("ms", ctypes.c_float), ("pad", ctypes.c_int32)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -123,6 +131,8 @@ def load(build_if_missing: bool = True):
         lib.receipt_kernel_launches.restype = ctypes.c_uint64
         lib.receipt_get_trace.argtypes = [vp, ctypes.POINTER(Round), i32, ctypes.POINTER(i32)]
         lib.receipt_get_trace.restype = ctypes.c_int
+        lib.receipt_get_subsets.argtypes = [vp, ctypes.POINTER(Subset), i32, ctypes.POINTER(i32)]
+        lib.receipt_get_subsets.restype = ctypes.c_int
         lib.receipt_server_config_default.argtypes = [ctypes.POINTER(ServerConfig)]
         lib.receipt_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
         lib.receipt_server_submit.argtypes = [vp, vp, vp, i64, i32, i32, ctypes.c_int, vp,
@@ -162,10 +172,11 @@ def _dptr(t):
 
 
 def _options(P=150, bounds=None, subset=None, bounds_out=None, p_eff=None, timing=False,
-             warp_max_w=0, slice_min_w=0, dgm=True, dgm_frac_1024=0):
+             warp_max_w=0, slice_min_w=0, dgm=True, dgm_frac_1024=0, fd_heavy_w=0):
     o = Options()
     load().receipt_options_default(ctypes.byref(o))
     o.P = int(P)
+    o.fd_heavy_w = int(fd_heavy_w)
     o.dgm_frac_1024 = int(dgm_frac_1024)
     o.no_dgm = 0 if dgm else 1
     o.warp_max_w = int(warp_max_w)
@@ -241,6 +252,17 @@ def receipt_get_trace(handle) -> list:
              "wedges": list(r.wedges), "ms": list(r.ms)} for r in buf[: n.value]]
 
 
+def receipt_get_subsets(handle) -> list:
+    """Per-subset records of the last decomposition (fine-grained step)."""
+    lib = load()
+    n = ctypes.c_int32(0)
+    _check(lib.receipt_get_subsets(handle, None, 0, ctypes.byref(n)))
+    buf = (Subset * max(1, n.value))()
+    _check(lib.receipt_get_subsets(handle, buf, n.value, ctypes.byref(n)))
+    return [{"n": r.n, "heavy": bool(r.heavy), "levels": r.levels, "wedges_est": r.wedges_est,
+             "ms": r.ms} for r in buf[: n.value]]
+
+
 def receipt_kernel_launches() -> int:
     """Kernels launched by libreceipt in this process so far."""
     return int(load().receipt_kernel_launches())
@@ -295,7 +317,7 @@ class Graph:
 
     def tip_decompose(self, side: int = SIDE_U, P: int = 0, bounds=None, subsets=False,
                       timing=False, out=None, stream=None, warp_max_w=0, slice_min_w=0, dgm=True,
-                      dgm_frac_1024=0):
+                      dgm_frac_1024=0, fd_heavy_w=0):
         """Tip numbers of ``side`` (Algorithms 3 and 4). P = 0 takes the tuned
         value for this graph's shape class, else 150. With ``subsets=True``
         returns ``(tips, subset_of_vertex, range_bounds)``."""
@@ -317,7 +339,7 @@ class Graph:
             if subsets else None
         peff = ctypes.c_int32(0)
         o, keep = _options(P, bounds, sub, bout, peff, timing, warp_max_w, slice_min_w, dgm,
-                           dgm_frac_1024)
+                           dgm_frac_1024, fd_heavy_w)
         receipt_tip_decompose(self._h, side, tip, o, stream)
         if subsets:
             return tip, sub, bout[: peff.value + 1]
@@ -328,6 +350,9 @@ class Graph:
 
     def trace(self) -> list:
         return receipt_get_trace(self._h)
+
+    def subsets(self) -> list:
+        return receipt_get_subsets(self._h)
 
 
 def receipt_decompose_batch(graphs, sides, outs=None, P: int = 150, stream=None, timing=False):

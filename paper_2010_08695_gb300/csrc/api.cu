@@ -178,6 +178,7 @@ void tip_decompose_impl(receipt_graph *g, int side, uint64_t *d_tip, const recei
     D.m = g->m;
     D.timing = opt.timing != 0;
     D.max_deg_s = g->max_deg[side];
+    D.fd_heavy_w = opt.fd_heavy_w;
     DevBuf<unsigned long long> cu(g->nu, s), cv(g->nv, s), init(n, s), wfull(n, s);
     DevBuf<int32_t> sub(n, s);
     DevBuf<unsigned long long> wbup(1, s);
@@ -222,6 +223,10 @@ void tip_decompose_impl(receipt_graph *g, int side, uint64_t *d_tip, const recei
     st.ms_fd_max_subset = D.fd_max_ms;
     st.fd_max_subset_n = D.fd_max_n;
     st.fd_max_subset_levels = D.fd_max_levels;
+    st.fd_heavy_subsets = D.fd_heavy;
+    st.ms_fd_heavy = D.fd_heavy_ms;
+    st.levels_fd_heavy = D.fd_heavy_levels;
+    g->subsets = std::move(D.subsets);
     for (int t = 0; t < 5; t++) {
         st.peel_wedges[t] = D.tier_wedges[t];
         st.peel_mids[t] = D.tier_mids[t];
@@ -388,6 +393,7 @@ void decompose_batch_impl(receipt_graph *const *gs, const receipt_side *sides, i
     }
     gs[0]->stats = U.stats;
     gs[0]->trace = std::move(U.trace);
+    gs[0]->subsets = std::move(U.subsets);
 }
 
 }  // namespace receipt
@@ -566,6 +572,17 @@ receipt_status receipt_get_trace(const receipt_graph *g, receipt_round *out, int
         const int32_t n = (int32_t)g->trace.size();
         for (int32_t i = 0; i < n && i < cap; i++) out[i] = g->trace[i];
         if (n_rounds) *n_rounds = n;
+    });
+}
+
+receipt_status receipt_get_subsets(const receipt_graph *g, receipt_subset *out, int32_t cap,
+                                   int32_t *n_subsets) {
+    return guarded([&] {
+        if (!g) fail(RECEIPT_ERR_INVALID, "null graph");
+        if (cap > 0 && !out) fail(RECEIPT_ERR_INVALID, "null output with cap > 0");
+        const int32_t n = (int32_t)g->subsets.size();
+        for (int32_t i = 0; i < n && i < cap; i++) out[i] = g->subsets[i];
+        if (n_subsets) *n_subsets = n;
     });
 }
 

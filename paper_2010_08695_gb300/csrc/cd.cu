@@ -206,17 +206,6 @@ __global__ void k_cd_frontier(int32_t n, const int32_t *__restrict__ sub,
     }
 }
 
-__device__ __forceinline__ void warp_append(bool take, int32_t x, int32_t *cnt, int32_t *list) {
-    unsigned bal = __ballot_sync(0xffffffffu, take);
-    if (!bal) return;
-    const int lane = threadIdx.x & 31;
-    int leader = __ffs(bal) - 1;
-    int pos = 0;
-    if (lane == leader) pos = atomicAdd(cnt, __popc(bal));
-    pos = __shfl_sync(0xffffffffu, pos, leader);
-    if (take) list[pos + __popc(bal & lanemask_lt())] = x;
-}
-
 // Assigns the activeSet to subset `range` and splits the vertices that have
 // updates to make into the three engine tiers.
 __global__ void k_cd_prepare(const int32_t *__restrict__ F, CdDev *st, int32_t range,

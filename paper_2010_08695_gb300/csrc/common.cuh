@@ -111,6 +111,7 @@ struct receipt_graph {
     receipt::Side side[2];
     receipt_stats stats{};
     std::vector<receipt_round> trace;  // rounds of the last decomposition
+    std::vector<receipt_subset> subsets;  // fine-grained subsets of the last decomposition
     void *owned = nullptr;  // device allocation holding every array above
 };
 
@@ -140,6 +141,19 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned r;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
     return r;
+}
+
+// Appends x to list[] for every lane with take set: one atomic per warp on
+// *cnt, positions in lane order. All lanes of the warp must call it.
+__device__ __forceinline__ void warp_append(bool take, int32_t x, int32_t *cnt, int32_t *list) {
+    unsigned bal = __ballot_sync(0xffffffffu, take);
+    if (!bal) return;
+    const int lane = threadIdx.x & 31;
+    int leader = __ffs(bal) - 1;
+    int pos = 0;
+    if (lane == leader) pos = atomicAdd(cnt, __popc(bal));
+    pos = __shfl_sync(0xffffffffu, pos, leader);
+    if (take) list[pos + __popc(bal & lanemask_lt())] = x;
 }
 
 // Number of entries of the ascending list a[0..n) that are < key.

@@ -30,6 +30,10 @@ namespace receipt {
 namespace {
 
 constexpr int FD_THREADS = 512;
+// heavy subsets: automatic threshold and levels enqueued per alive check
+constexpr unsigned long long HEAVY_MIN_W = 1ull << 23;
+constexpr unsigned long long HEAVY_SHARE = 8;
+constexpr int HEAVY_LEVELS_PER_CHECK = 4;
 
 __global__ void k_sub_keys(const int32_t *__restrict__ sub, int32_t n, uint64_t *__restrict__ key,
                            uint32_t *__restrict__ val, int32_t *__restrict__ cnt) {
@@ -156,7 +160,8 @@ struct FdArgs {
     const unsigned long long *init;
     unsigned long long *fsup;  // by member position
     uint8_t *alive;            // by member position
-    int32_t *alist;            // by member position
+    int32_t *alist;            // by member position: alive members (two buffers)
+    int32_t *alist2;
     int32_t *plist;            // by member position
     int32_t *blist;            // by member position: peeled vertices with big updates
     unsigned long long *tip;   // output, original ids
@@ -215,34 +220,147 @@ struct FdSliceEmit {
     __device__ __forceinline__ void operator()(int32_t k, uint32_t c) { (*e)(k + base, c); }
 };
 
-template <class Eng>
-struct FdVisit {
-    Eng *eng;
-    int32_t self;
-    __device__ __forceinline__ void operator()(int, int32_t key) {
-        if (key != self) eng->add(key);
+// Several anchors of one level aggregated in one pass: anchor slot a of the
+// batch owns keys [a * ni, (a + 1) * ni) of the dense counters. The batch's
+// edges form one virtual list of middle vertices; the thread that stages a
+// middle vertex records its anchor slot for the visits.
+constexpr int FD_BATCH = 32;
+
+struct FdBatchMids {
+    const int64_t *fd_beg;
+    const int32_t *fd_len;
+    const int64_t *bq0;   // first edge of each anchor (shared memory)
+    const int32_t *bpre;  // prefix of the anchors' degrees (nb + 1 entries)
+    int32_t nb;
+    uint8_t *slot;        // anchor slot of the middle vertex staged by each thread
+    __device__ __forceinline__ void seg(int64_t q, int64_t &beg, int32_t &len) const {
+        int lo = 0, hi = nb - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (bpre[mid] <= q)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const int64_t e = bq0[lo] + (q - bpre[lo]);
+        beg = fd_beg[e];
+        len = fd_len[e];
+        slot[threadIdx.x] = (uint8_t)lo;
     }
 };
 
-__global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_t, s_dn, s_np, s_nk, s_nbig;
-    __shared__ unsigned long long s_min[32];
-    __shared__ int32_t s_tmp[33];
-    DenseSlice H;
-    unsigned char *p = H.bind(smem, &s_dn);
-    Chunk ch;
+struct FdBatchVisit {
+    DenseSlice *eng;
+    const uint8_t *slot;
+    const int32_t *bself;  // rank of each anchor
+    int32_t ni;
+    __device__ __forceinline__ void operator()(int k, int32_t key) {
+        const int a = slot[k];
+        if (key != bself[a]) eng->add(a * ni + key);
+    }
+};
+
+struct FdBatchEmit {
+    FdEmit *e;
+    int32_t ni;
+    __device__ __forceinline__ void operator()(int32_t w, uint32_t c) { (*e)(w % ni, c); }
+};
+
+// Update of one peeled member r (anchor x, edges [q0, q1) of side s) whose
+// walk has at most WARP_MAX_W wedges: one warp with its private table.
+__device__ __forceinline__ void fd_update_warp(WarpHash &WH, const FdMids &M,
+                                               const int32_t *__restrict__ fd_adj, int64_t q0,
+                                               int64_t q1, int32_t r, int lane, FdEmit &emit) {
+    for (int64_t qb = q0; qb < q1; qb += 32) {
+        const int64_t q = qb + lane;
+        int64_t beg = 0;
+        int32_t len = 0;
+        if (q < q1) M.seg(q, beg, len);
+        const int cnt = (int)imin64(32, q1 - qb);
+        for (int t2 = 0; t2 < cnt; t2++) {
+            const int64_t b = __shfl_sync(0xffffffffu, beg, t2);
+            const int32_t l = __shfl_sync(0xffffffffu, len, t2);
+            for (int p = lane; p < l; p += 32) {
+                const int32_t k = fd_adj[b + p];
+                if (k != r) WH.add(k);
+            }
+        }
+    }
+    __syncwarp();
+    for (int sl = lane; sl < WARP_SLOTS; sl += 32) {
+        const int32_t k = WH.key[sl];
+        if (k != EMPTY_KEY) {
+            const uint32_t c = WH.val[sl];
+            if (c >= 2) emit(k, c);
+            WH.key[sl] = EMPTY_KEY;
+            WH.val[sl] = 0;
+        }
+    }
+    __syncwarp();
+}
+
+// Update of one peeled member r with a bigger walk: the whole CTA aggregates
+// slice by slice of the subset's rank space (ni ranks) with dense counters,
+// 32-bit ones when the anchor's degree lets a count reach 2^16. Returns the
+// wedges walked (the same value in every thread). All threads must call it.
+__device__ int64_t fd_update_cta(DenseSlice &H, Chunk &ch, const int64_t *__restrict__ fd_beg,
+                                 const int32_t *__restrict__ fd_len,
+                                 const int32_t *__restrict__ fd_adj, int64_t q0, int64_t q1,
+                                 int32_t r, int32_t ni, FdEmit &emit) {
+    const bool wide = q1 - q0 >= 65535;
+    const int32_t SWk = wide ? DENSE_WORDS : DENSE_KEYS;
+    const int32_t C = (ni + SWk - 1) / SWk;
+    int64_t wedges = 0;
+    for (int32_t j = 0; j < C; j++) {
+        const int32_t base = j * SWk;
+        const int32_t w = (int32_t)imin64(SWk, (int64_t)ni - base);
+        H.set_width(w, wide);
+        FdSliceVisit v{&H, base, r};
+        int64_t walked;
+        if (C == 1) {
+            FdMids M{fd_beg, fd_len};
+            walked = cta_walk(M, q0, q1, fd_adj, ch, v);
+        } else {
+            FdSliceMids MS{fd_beg, fd_len, fd_adj, base, base + w};
+            walked = cta_walk(MS, q0, q1, fd_adj, ch, v);
+        }
+        wedges += walked;
+        if (walked == 0) continue;
+        FdSliceEmit em{&emit, base};
+        H.sweep<true, true>(em);
+        __syncthreads();
+        H.reset_scalars();
+    }
+    return wedges;
+}
+
+__device__ __forceinline__ unsigned char *fd_bind_smem(unsigned char *smem, int *s_dn, DenseSlice &H,
+                                                       Chunk &ch) {
+    unsigned char *p = H.bind(smem, s_dn);
     ch.beg = (int64_t *)p;
     ch.pre = (int32_t *)(ch.beg + MID_CHUNK);
     ch.tmp = ch.pre + MID_CHUNK + 1;
     ch.len = chunk_len_ptr(ch.tmp);
+    return (unsigned char *)(((uintptr_t)(ch.len + MID_CHUNK) + 15) & ~(uintptr_t)15);
+}
+
+__global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_t, s_dn, s_np, s_nk, s_nbig, s_nwide;
+    __shared__ unsigned long long s_min[32];
+    __shared__ int64_t s_bq0[FD_BATCH];
+    __shared__ int32_t s_bpre[FD_BATCH + 1], s_bself[FD_BATCH];
+    __shared__ uint8_t s_slot[FD_THREADS];
+    DenseSlice H;
+    Chunk ch;
     // warp-private tables after the chunk staging
-    int32_t *wkey = (int32_t *)(((uintptr_t)(ch.len + MID_CHUNK) + 15) & ~(uintptr_t)15);
+    int32_t *wkey = (int32_t *)fd_bind_smem(smem, &s_dn, H, ch);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     WarpHash WH{wkey + warp * WARP_SLOTS, (uint32_t *)(wkey + nwarps * WARP_SLOTS) + warp * WARP_SLOTS};
     WH.clear(lane);
     H.clear_all();
     FdMids M{a.fd_beg, a.fd_len};
+    // per warp (lane 0): wedges walked; thread 0 also counts levels
     unsigned long long wedges = 0, levels = 0;
     __syncthreads();
     for (;;) {
@@ -261,6 +379,7 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
         unsigned long long *fsup = a.fsup + mb;
         uint8_t *alive = a.alive + mb;
         int32_t *alist = a.alist + mb;
+        int32_t *alist_next = a.alist2 + mb;
         int32_t *plist = a.plist + mb;
         int32_t *blist = a.blist + mb;
         const int32_t *mem = a.members + mb;
@@ -271,6 +390,8 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
         }
         int32_t nalive = ni;
         unsigned long long level = 0;
+        // anchors aggregated per pass of the batched update
+        const int32_t bk = ni <= DENSE_KEYS / 2 ? min(FD_BATCH, DENSE_KEYS / ni) : 1;
         __syncthreads();
         while (nalive > 0) {
             // minimum support over the remaining vertices
@@ -281,6 +402,12 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
             }
             mn = warp_min(mn);
             if ((threadIdx.x & 31) == 0) s_min[threadIdx.x >> 5] = mn;
+            if (threadIdx.x == 0) {
+                s_np = 0;
+                s_nk = 0;
+                s_nbig = 0;
+                s_nwide = 0;
+            }
             __syncthreads();
             if (threadIdx.x < 32) {
                 unsigned long long v = threadIdx.x < (blockDim.x >> 5) ? s_min[threadIdx.x] : ~0ull;
@@ -291,40 +418,38 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
             const unsigned long long mu = s_min[0] > level ? s_min[0] : level;
             level = mu;
             levels++;
-            // peel every remaining vertex with support <= mu; compact the rest
-            if (threadIdx.x == 0) {
-                s_np = 0;
-                s_nk = 0;
-            }
-            __syncthreads();
+            // peel every remaining vertex with support <= mu; the rest go to
+            // the other alive buffer (ballot compaction, order irrelevant)
             for (int base = 0; base < nalive; base += blockDim.x) {
-                int j = base + threadIdx.x;
+                const int j = base + threadIdx.x;
                 int32_t r = -1;
                 unsigned long long v = 0;
                 if (j < nalive) {
                     r = alist[j];
                     v = fsup[r];
                 }
-                bool keep = (r >= 0) && v > mu;
-                int32_t total;
-                int32_t pos = block_exclusive_scan<int32_t>(keep ? 1 : 0, s_tmp, &total);
-                if (keep) alist[s_nk + pos] = r;
-                if (r >= 0 && !keep) {
+                const bool keep = r >= 0 && v > mu;
+                const bool peel = r >= 0 && !keep;
+                if (peel) {
                     alive[r] = 0;
                     a.tip[a.new2old[mem[r]]] = mu;
-                    if (v > 0) plist[atomicAdd(&s_np, 1)] = r;
                 }
-                __syncthreads();
-                if (threadIdx.x == 0) s_nk += total;
-                __syncthreads();
+                warp_append(keep, r, &s_nk, alist_next);
+                warp_append(peel && v > 0, r, &s_np, plist);
             }
+            __syncthreads();
             nalive = s_nk;
+            {
+                int32_t *tmp = alist;
+                alist = alist_next;
+                alist_next = tmp;
+            }
             const int np = s_np;
             // updates of the peeled vertices inside G_i. Phase A: one warp per
-            // peeled vertex whose update walks at most WARP_MAX_W wedges.
-            FdEmit emit_w{fsup, alive};
-            if (threadIdx.x == 0) s_nbig = 0;
-            __syncthreads();
+            // peeled vertex whose update walks at most WARP_MAX_W wedges;
+            // bigger ones are listed for phase B (those of degree >= 65535,
+            // whose counts need 32 bits, from the end of the list).
+            FdEmit emit{fsup, alive};
             for (int pi = warp; pi < np; pi += nwarps) {
                 const int32_t r = plist[pi];
                 const int32_t x = mem[r];
@@ -333,73 +458,66 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
                 for (int64_t q = q0 + lane; q < q1; q += 32) W += a.fd_len[q];
                 W = warp_sum(W);
                 if (W > WARP_MAX_W) {
-                    if (lane == 0) blist[atomicAdd(&s_nbig, 1)] = r;
+                    if (lane == 0) {
+                        if (q1 - q0 >= 65535 || bk == 1)
+                            blist[ni - 1 - atomicAdd(&s_nwide, 1)] = r;
+                        else
+                            blist[atomicAdd(&s_nbig, 1)] = r;
+                    }
                     continue;
                 }
-                for (int64_t qb = q0; qb < q1; qb += 32) {
-                    int64_t q = qb + lane;
-                    int64_t beg = 0;
-                    int32_t len = 0;
-                    if (q < q1) {
-                        beg = a.fd_beg[q];
-                        len = a.fd_len[q];
-                    }
-                    const int cnt = (int)imin64(32, q1 - qb);
-                    for (int t2 = 0; t2 < cnt; t2++) {
-                        int64_t b = __shfl_sync(0xffffffffu, beg, t2);
-                        int32_t l = __shfl_sync(0xffffffffu, len, t2);
-                        for (int p = lane; p < l; p += 32) {
-                            int32_t k = a.fd_adj[b + p];
-                            if (k != r) WH.add(k);
-                        }
-                    }
-                }
-                __syncwarp();
-                for (int sl = lane; sl < WARP_SLOTS; sl += 32) {
-                    int32_t k = WH.key[sl];
-                    if (k != EMPTY_KEY) {
-                        uint32_t c = WH.val[sl];
-                        if (c >= 2) emit_w(k, c);
-                        WH.key[sl] = EMPTY_KEY;
-                        WH.val[sl] = 0;
-                    }
-                }
-                __syncwarp();
+                fd_update_warp(WH, M, a.fd_adj, q0, q1, r, lane, emit);
                 if (lane == 0) wedges += (unsigned long long)W;
             }
             __syncthreads();
-            const int nbig = s_nbig;
-            // Phase B: the whole CTA per peeled vertex with a bigger update,
-            // aggregating over slices of the subset's rank space with dense
-            // counters (32-bit counters for an anchor of degree >= 65535)
-            for (int pi = 0; pi < nbig; pi++) {
-                const int32_t r = blist[pi];
-                const int32_t x = mem[r];
-                const int64_t q0 = a.off_s[x], q1 = a.off_s[x + 1];
-                const bool wide = q1 - q0 >= 65535;
-                const int32_t SWk = wide ? DENSE_WORDS : DENSE_KEYS;
-                const int32_t C = (ni + SWk - 1) / SWk;
-                FdEmit emit{fsup, alive};
-                for (int32_t j = 0; j < C; j++) {
-                    const int32_t base = j * SWk;
-                    const int32_t w = (int32_t)imin64(SWk, (int64_t)ni - base);
-                    H.set_width(w, wide);
-                    FdSliceVisit v{&H, base, r};
-                    int64_t walked;
-                    if (C == 1) {
-                        walked = cta_walk(M, q0, q1, a.fd_adj, ch, v);
-                    } else {
-                        FdSliceMids MS{a.fd_beg, a.fd_len, a.fd_adj, base, base + w};
-                        walked = cta_walk(MS, q0, q1, a.fd_adj, ch, v);
+            const int nbig = s_nbig, nwide = s_nwide;
+            // Phase B: bk anchors per pass of the whole CTA over one dense key
+            // space of bk * ni keys
+            for (int p0 = 0; p0 < nbig; p0 += bk) {
+                const int nb = min(bk, nbig - p0);
+                if (warp == 0) {
+                    int32_t deg = 0;
+                    if (lane < nb) {
+                        const int32_t r = blist[p0 + lane];
+                        const int32_t x = mem[r];
+                        const int64_t q0 = a.off_s[x];
+                        deg = (int32_t)(a.off_s[x + 1] - q0);
+                        s_bq0[lane] = q0;
+                        s_bself[lane] = r;
                     }
-                    wedges += walked;
-                    if (walked == 0) continue;
-                    FdSliceEmit em{&emit, base};
+                    int32_t inc = deg;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                        if (lane >= o) inc += y;
+                    }
+                    if (lane < nb) s_bpre[lane + 1] = inc;
+                    if (lane == 0) s_bpre[0] = 0;
+                }
+                __syncthreads();
+                H.set_width(nb * ni, false);
+                FdBatchMids BM{a.fd_beg, a.fd_len, s_bq0, s_bpre, nb, s_slot};
+                FdBatchVisit v{&H, s_slot, s_bself, ni};
+                const int64_t walked = cta_walk(BM, 0, s_bpre[nb], a.fd_adj, ch, v);
+                if (threadIdx.x == 0) wedges += (unsigned long long)walked;
+                if (walked > 0) {
+                    FdBatchEmit em{&emit, ni};
                     H.sweep<true, true>(em);
                     __syncthreads();
                     H.reset_scalars();
                 }
+                __syncthreads();
             }
+            // one anchor at a time: degree >= 65535, or a subset too large
+            // to batch (rank slices)
+            for (int pi = 0; pi < nwide; pi++) {
+                const int32_t r = blist[ni - 1 - pi];
+                const int32_t x = mem[r];
+                const int64_t walked = fd_update_cta(H, ch, a.fd_beg, a.fd_len, a.fd_adj,
+                                                     a.off_s[x], a.off_s[x + 1], r, ni, emit);
+                if (threadIdx.x == 0) wedges += (unsigned long long)walked;
+            }
+            __syncthreads();
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -409,10 +527,171 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
             a.sub_levels[i] = levels - levels0;
         }
     }
-    if (threadIdx.x == 0) {
-        atomicAdd(&a.stats[0], wedges);
-        atomicAdd(&a.stats[1], levels);
+    if (lane == 0 && wedges) atomicAdd(&a.stats[0], wedges);
+    if (threadIdx.x == 0) atomicAdd(&a.stats[1], levels);
+}
+
+// ------------------------------------------------------------------------
+// Heavy subsets: one subset peeled by all CTAs, level by level. A subset
+// whose wedge count dwarfs the others' would otherwise keep one CTA busy
+// long after the rest of the queue is done. Per level: the minimum support
+// of the alive members; every alive member with support <= mu is peeled
+// (tip mu) and listed by the size of its walk; the warp kernel and the CTA
+// kernel apply the updates of the listed members, one warp or one CTA per
+// member. Same levels, same tip numbers as the one-CTA peel.
+// ------------------------------------------------------------------------
+struct FdhDev {
+    unsigned long long mn;     // minimum support of the alive members (this level)
+    unsigned long long level;  // mu of the last level
+    unsigned long long wedges, levels;
+    unsigned long long t0, t1; // globaltimer at the start and at the end
+    int32_t nalive, nkeep, nw, nb;
+};
+
+struct FdhArgs {
+    const int32_t *mem;  // subset members (local ids), rank order
+    int32_t ni;
+    const int64_t *off_s;
+    const int64_t *fd_beg;
+    const int32_t *fd_len;
+    const int32_t *fd_adj;
+    const int32_t *new2old;
+    const unsigned long long *init;
+    unsigned long long *fsup;  // by rank
+    uint8_t *alive;            // by rank
+    unsigned long long *wr;    // by rank: wedges of the member's walk inside G_i
+    int32_t *Lw, *Lb;          // peeled members with small / big walks
+    unsigned long long *tip;   // output, original ids
+    FdhDev *st;
+};
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__global__ void k_fdh_init(FdhArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = w0; r < a.ni; r += nw) {
+        const int32_t x = a.mem[r];
+        unsigned long long W = 0;
+        for (int64_t q = a.off_s[x] + lane; q < a.off_s[x + 1]; q += 32) W += a.fd_len[q];
+        W = warp_sum(W);
+        if (lane == 0) {
+            a.fsup[r] = a.init[x];
+            a.alive[r] = 1;
+            a.wr[r] = W;
+        }
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        FdhDev *st = a.st;
+        st->mn = ~0ull;
+        st->level = 0;
+        st->wedges = st->levels = 0;
+        st->t0 = globaltimer_ns();
+        st->t1 = 0;
+        st->nalive = a.ni;
+        st->nkeep = st->nw = st->nb = 0;
+    }
+}
+
+__global__ void k_fdh_min(FdhArgs a) {
+    __shared__ unsigned long long s_min[32];
+    unsigned long long mn = ~0ull;
+    for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < a.ni; r += gridDim.x * blockDim.x)
+        if (a.alive[r]) {
+            const unsigned long long v = a.fsup[r];
+            mn = v < mn ? v : mn;
+        }
+    mn = warp_min(mn);
+    if ((threadIdx.x & 31) == 0) s_min[threadIdx.x >> 5] = mn;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        unsigned long long v = threadIdx.x < (blockDim.x >> 5) ? s_min[threadIdx.x] : ~0ull;
+        v = warp_min(v);
+        if (threadIdx.x == 0 && v != ~0ull) atomicMin(&a.st->mn, v);
+    }
+}
+
+__global__ void k_fdh_select(FdhArgs a) {
+    const unsigned long long lv = a.st->level, mn = a.st->mn;
+    const unsigned long long mu = mn > lv ? mn : lv;
+    int32_t keep = 0;
+    for (int32_t base = blockIdx.x * blockDim.x; base < a.ni; base += gridDim.x * blockDim.x) {
+        const int32_t r = base + threadIdx.x;
+        const bool al = r < a.ni && a.alive[r];
+        const unsigned long long v = al ? a.fsup[r] : 0;
+        const bool peel = al && v <= mu;
+        if (peel) {
+            a.alive[r] = 0;
+            a.tip[a.new2old[a.mem[r]]] = mu;
+        }
+        const bool upd = peel && v > 0;
+        const bool small = upd && a.wr[r] <= (unsigned long long)WARP_MAX_W;
+        warp_append(small, r, &a.st->nw, a.Lw);
+        warp_append(upd && !small, r, &a.st->nb, a.Lb);
+        keep += (al && !peel) ? 1 : 0;
+    }
+    keep = warp_sum(keep);
+    if ((threadIdx.x & 31) == 0 && keep) atomicAdd(&a.st->nkeep, keep);
+}
+
+__global__ void __launch_bounds__(256) k_fdh_warp(FdhArgs a) {
+    __shared__ int32_t skey[8][WARP_SLOTS];
+    __shared__ uint32_t sval[8][WARP_SLOTS];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    WarpHash WH{skey[w], sval[w]};
+    WH.clear(lane);
+    __syncwarp();
+    FdEmit emit{a.fsup, a.alive};
+    FdMids M{a.fd_beg, a.fd_len};
+    const int32_t nw = a.st->nw;
+    unsigned long long wedges = 0;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t ngw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = gw; i < nw; i += ngw) {
+        const int32_t r = a.Lw[i];
+        const int32_t x = a.mem[r];
+        fd_update_warp(WH, M, a.fd_adj, a.off_s[x], a.off_s[x + 1], r, lane, emit);
+        wedges += a.wr[r];
+    }
+    if (lane == 0 && wedges) atomicAdd(&a.st->wedges, wedges);
+}
+
+__global__ void __launch_bounds__(FD_THREADS, 1) k_fdh_cta(FdhArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_dn;
+    DenseSlice H;
+    Chunk ch;
+    fd_bind_smem(smem, &s_dn, H, ch);
+    H.clear_all();
+    __syncthreads();
+    FdEmit emit{a.fsup, a.alive};
+    const int32_t nb = a.st->nb;
+    unsigned long long wedges = 0;
+    for (int32_t i = blockIdx.x; i < nb; i += gridDim.x) {
+        const int32_t r = a.Lb[i];
+        const int32_t x = a.mem[r];
+        wedges += (unsigned long long)fd_update_cta(H, ch, a.fd_beg, a.fd_len, a.fd_adj, a.off_s[x],
+                                                    a.off_s[x + 1], r, a.ni, emit);
+    }
+    if (threadIdx.x == 0 && wedges) atomicAdd(&a.st->wedges, wedges);
+}
+
+// Closes a level. Launched again after the subset is empty, it changes
+// nothing that is read later (the host enqueues levels ahead of its check).
+__global__ void k_fdh_next(FdhDev *st) {
+    if (st->nalive == 0) return;
+    const unsigned long long mu = st->mn > st->level ? st->mn : st->level;
+    st->level = mu;
+    st->mn = ~0ull;
+    st->nalive = st->nkeep;
+    st->nkeep = st->nw = st->nb = 0;
+    st->levels++;
+    if (st->nalive == 0) st->t1 = globaltimer_ns();
 }
 
 }  // namespace
@@ -471,48 +750,152 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
     DevBuf<int32_t> queue(P, s);
     k_lpt<<<ceil_div(P, 256), 256, 0, s>>>(wsub.get(), mstart.get(), P, queue.get());
     RC_LAUNCH();
-    // largest subset
-    std::vector<int32_t> hms(P + 1);
+    // subset sizes, wedge counts and the LPT order, for the heavy-subset choice
+    std::vector<int32_t> hms(P + 1), hq(P);
+    std::vector<unsigned long long> hw(P);
     RC_CUDA(cudaMemcpyAsync(hms.data(), mstart.get(), sizeof(int32_t) * (P + 1),
                             cudaMemcpyDeviceToHost, s));
+    RC_CUDA(cudaMemcpyAsync(hq.data(), queue.get(), sizeof(int32_t) * P, cudaMemcpyDeviceToHost, s));
+    RC_CUDA(cudaMemcpyAsync(hw.data(), wsub.get(), 8 * P, cudaMemcpyDeviceToHost, s));
     RC_CUDA(cudaStreamSynchronize(s));
-    int32_t maxn = 0;
-    for (int i = 0; i < P; i++) maxn = std::max(maxn, hms[i + 1] - hms[i]);
     const size_t warp_tables = (size_t)(FD_THREADS / 32) * WARP_SLOTS * 8 + 16;
     const size_t smem = DenseSlice::bytes() + CHUNK_BYTES + warp_tables;
     allow_max_smem((const void *)k_fd_peel);
     int occ = 0;
     RC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fd_peel, FD_THREADS, smem));
-    const int grid = std::max(1, std::min(num_sms() * std::max(occ, 1), P));
+    const int sms = num_sms();
+    const int grid_all = sms * std::max(occ, 1);
+    // Heavy subsets: a leading run of the LPT queue whose wedge counts exceed
+    // the threshold. Automatic: HEAVY_SHARE times the mean share of one CTA
+    // and at least HEAVY_MIN_W wedges.
+    int nheavy = 0;
+    if (D.fd_heavy_w >= 0) {
+        unsigned long long thr = (unsigned long long)D.fd_heavy_w;
+        if (D.fd_heavy_w == 0) {
+            unsigned long long tot = 0;
+            for (int i = 0; i < P; i++) tot += hw[i];
+            thr = std::max<unsigned long long>(HEAVY_MIN_W,
+                                               tot / (unsigned long long)std::min(grid_all, P) *
+                                                   HEAVY_SHARE);
+        }
+        while (nheavy < P && hw[hq[nheavy]] >= thr && hms[hq[nheavy] + 1] > hms[hq[nheavy]])
+            nheavy++;
+    }
     DevBuf<unsigned long long> fsup(n, s);
     DevBuf<uint8_t> alive(n, s);
-    DevBuf<int32_t> alist(n, s), plist(n, s), blist(n, s), qhead(1, s);
+    DevBuf<int32_t> alist(n, s), alist2(n, s), plist(n, s), blist(n, s), qhead(1, s);
     DevBuf<unsigned long long> stats(2, s), sub_ns(P, s), sub_lv(P, s);
     qhead.zero();
     stats.zero();
     sub_ns.zero();
     sub_lv.zero();
-    FdArgs a{queue.get(),   P,           qhead.get(),     mstart.get(), members.get(),
-             S.off,         fd_beg.get(), fd_len.get(),   fd_adj.get(), S.new2old,
-             D.init,        fsup.get(),  alive.get(),     alist.get(),  plist.get(), blist.get(),
-             (unsigned long long *)d_tip, stats.get(),    sub_ns.get(), sub_lv.get()};
-    k_fd_peel<<<grid, FD_THREADS, smem, s>>>(a);
-    RC_LAUNCH();
+    D.fd_heavy = nheavy;
+    D.fd_heavy_ms = 0;
+    D.fd_heavy_levels = 0;
+    std::vector<FdhDev> hh(nheavy);
+    if (nheavy > 0) {
+        DevBuf<unsigned long long> wr(n, s);
+        DevBuf<FdhDev> hst(1, s);
+        const size_t smem_h = DenseSlice::bytes() + CHUNK_BYTES;
+        allow_max_smem((const void *)k_fdh_cta);
+        int occ_h = 0;
+        RC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_h, k_fdh_cta, FD_THREADS, smem_h));
+        const int grid_h = sms * std::max(occ_h, 1);
+        int32_t *pin = (int32_t *)pinned_scratch(64);
+        cudaEvent_t evs[2] = {};
+        struct EvGuard {
+            cudaEvent_t *e;
+            ~EvGuard() {
+                for (int i = 0; i < 2; i++)
+                    if (e[i]) cudaEventDestroy(e[i]);
+            }
+        } eg{evs};
+        for (int i = 0; i < 2; i++) RC_CUDA(cudaEventCreateWithFlags(&evs[i], cudaEventDisableTiming));
+        for (int h = 0; h < nheavy; h++) {
+            const int32_t i = hq[h];
+            const int32_t mb = hms[i], ni = hms[i + 1] - hms[i];
+            FdhArgs ha{members.get() + mb, ni,           S.off,          fd_beg.get(),
+                       fd_len.get(),       fd_adj.get(), S.new2old,      D.init,
+                       fsup.get() + mb,    alive.get() + mb, wr.get() + mb, plist.get() + mb,
+                       blist.get() + mb,   (unsigned long long *)d_tip,  hst.get()};
+            const int gm = std::max(1, std::min(ceil_div(ni, 256), sms * 4));
+            const int gi = std::max(1, std::min(ceil_div((int64_t)ni * 32, 256), sms * 16));
+            k_fdh_init<<<gi, 256, 0, s>>>(ha);
+            RC_LAUNCH();
+            // levels are enqueued in batches; the alive count of batch k is
+            // checked while batch k + 1 runs (levels after the last change
+            // nothing)
+            for (int64_t batch = 0;; batch++) {
+                for (int l = 0; l < HEAVY_LEVELS_PER_CHECK; l++) {
+                    k_fdh_min<<<gm, 256, 0, s>>>(ha);
+                    RC_LAUNCH();
+                    k_fdh_select<<<gm, 256, 0, s>>>(ha);
+                    RC_LAUNCH();
+                    k_fdh_warp<<<sms * 8, 256, 0, s>>>(ha);
+                    RC_LAUNCH();
+                    k_fdh_cta<<<grid_h, FD_THREADS, smem_h, s>>>(ha);
+                    RC_LAUNCH();
+                    k_fdh_next<<<1, 1, 0, s>>>(hst.get());
+                    RC_LAUNCH();
+                }
+                const int slot = (int)(batch & 1);
+                RC_CUDA(cudaMemcpyAsync(pin + slot, &hst.get()->nalive, 4, cudaMemcpyDeviceToHost, s));
+                RC_CUDA(cudaEventRecord(evs[slot], s));
+                if (batch > 0) {
+                    RC_CUDA(cudaEventSynchronize(evs[slot ^ 1]));
+                    if (pin[slot ^ 1] == 0) break;
+                }
+            }
+            RC_CUDA(cudaMemcpyAsync(&hh[h], hst.get(), sizeof(FdhDev), cudaMemcpyDeviceToHost, s));
+            RC_CUDA(cudaStreamSynchronize(s));
+            D.fd_heavy_ms += (float)((hh[h].t1 - hh[h].t0) * 1e-6);
+            D.fd_heavy_levels += (int64_t)hh[h].levels;
+        }
+        RC_CUDA(cudaMemcpyAsync(qhead.get(), &nheavy, 4, cudaMemcpyHostToDevice, s));
+    }
+    if (nheavy < P) {
+        const int grid = std::max(1, std::min(grid_all, P - nheavy));
+        FdArgs a{queue.get(),   P,           qhead.get(),     mstart.get(), members.get(),
+                 S.off,         fd_beg.get(), fd_len.get(),   fd_adj.get(), S.new2old,
+                 D.init,        fsup.get(),  alive.get(),     alist.get(),  alist2.get(),
+                 plist.get(),   blist.get(),
+                 (unsigned long long *)d_tip, stats.get(),    sub_ns.get(), sub_lv.get()};
+        k_fd_peel<<<grid, FD_THREADS, smem, s>>>(a);
+        RC_LAUNCH();
+    }
     unsigned long long hs[2] = {0, 0};
     RC_CUDA(cudaMemcpyAsync(hs, stats.get(), sizeof(hs), cudaMemcpyDeviceToHost, s));
-    RC_CUDA(cudaStreamSynchronize(s));
-    D.wedges_fd = hs[0];
-    D.levels = (int64_t)hs[1];
     std::vector<unsigned long long> hns(P), hlv(P);
     RC_CUDA(cudaMemcpyAsync(hns.data(), sub_ns.get(), 8 * P, cudaMemcpyDeviceToHost, s));
     RC_CUDA(cudaMemcpyAsync(hlv.data(), sub_lv.get(), 8 * P, cudaMemcpyDeviceToHost, s));
     RC_CUDA(cudaStreamSynchronize(s));
-    int worst = 0;
-    for (int i = 1; i < P; i++)
-        if (hns[i] > hns[worst]) worst = i;
-    D.fd_max_ms = (float)(hns[worst] * 1e-6);
-    D.fd_max_n = hms[worst + 1] - hms[worst];
-    D.fd_max_levels = (int64_t)hlv[worst];
+    D.wedges_fd = hs[0];
+    D.levels = (int64_t)hs[1];
+    std::vector<bool> heavy(P, false);
+    for (int h = 0; h < nheavy; h++) {
+        const int32_t i = hq[h];
+        heavy[i] = true;
+        hns[i] = hh[h].t1 - hh[h].t0;
+        hlv[i] = hh[h].levels;
+        D.wedges_fd += hh[h].wedges;
+        D.levels += (int64_t)hh[h].levels;
+    }
+    D.subsets.resize(P);
+    int worst = -1;
+    for (int i = 0; i < P; i++) {
+        receipt_subset &r = D.subsets[i];
+        r.n = hms[i + 1] - hms[i];
+        r.heavy = heavy[i] ? 1 : 0;
+        r.levels = (int64_t)hlv[i];
+        r.wedges_est = hw[i];
+        r.ms = (float)(hns[i] * 1e-6);
+        r.pad = 0;
+        if (!heavy[i] && (worst < 0 || hns[i] > hns[worst])) worst = i;
+    }
+    // slowest subset peeled by one CTA
+    D.fd_max_ms = worst >= 0 ? (float)(hns[worst] * 1e-6) : 0.f;
+    D.fd_max_n = worst >= 0 ? hms[worst + 1] - hms[worst] : 0;
+    D.fd_max_levels = worst >= 0 ? (int64_t)hlv[worst] : 0;
 }
 
 }  // namespace receipt

@@ -60,6 +60,11 @@ struct Decomp {
     float fd_max_ms = 0;         // slowest subset of the fine-grained step
     int32_t fd_max_n = 0;        // its size
     int64_t fd_max_levels = 0;   // its peeling levels
+    int64_t fd_heavy_w = 0;      // heavy-subset threshold (0 automatic, -1 never)
+    int32_t fd_heavy = 0;        // subsets peeled by all CTAs
+    float fd_heavy_ms = 0;
+    int64_t fd_heavy_levels = 0;
+    std::vector<receipt_subset> subsets;
 };
 
 void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s);

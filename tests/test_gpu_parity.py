@@ -194,6 +194,47 @@ def test_any_P_and_injected_ranges_give_same_tips(R):
         assert np.array_equal(R.as_u64(t), want), f"bounds {b}"
 
 
+def test_heavy_subset_path_gives_same_tips(R):
+    """Subsets peeled by all CTAs level by level (forced for every subset,
+    or never) give the one-CTA result; the per-subset records add up."""
+    eu, ev = synth.chung_lu(20000, 4000, 120000, 2.4, 2.2, seed=33)
+    want, _ = oracle.bup(eu, ev, 20000, 4000, 0)
+    g = R.Graph(eu, ev, 20000, 4000)
+    for P in (1, 5, 150):
+        for hw in (1, -1, 0):
+            t = R.as_u64(g.tip_decompose(0, P=P, fd_heavy_w=hw))
+            assert np.array_equal(t, want), f"P={P} fd_heavy_w={hw}"
+            st, subs = g.stats(), g.subsets()
+            assert len(subs) == st["p_eff"]
+            assert sum(s["n"] for s in subs) == 20000
+            heavy = [s for s in subs if s["heavy"]]
+            assert len(heavy) == st["fd_heavy_subsets"]
+            if hw == 1:
+                assert len(heavy) == sum(1 for s in subs if s["n"] > 0 and s["wedges_est"] >= 1)
+            if hw == -1:
+                assert not heavy
+            assert sum(s["levels"] for s in subs) == st["levels_fd"]
+            assert sum(s["levels"] for s in heavy) == st["levels_fd_heavy"]
+    # V side of a graph with a hub of degree >= 2^16 (32-bit counters) and a
+    # side of 150k ranks in one subset (several rank slices), heavy path forced
+    rng = np.random.default_rng(22)
+    nu, nv = 80000, 50
+    eu = [np.arange(70000, dtype=np.int32)]
+    ev = [np.zeros(70000, np.int32)]
+    for v in range(1, nv):
+        us = rng.choice(nu, 1200, replace=False).astype(np.int32)
+        eu.append(us)
+        ev.append(np.full(len(us), v, np.int32))
+    eu, ev = np.concatenate(eu), np.concatenate(ev)
+    want, _ = oracle.bup(eu, ev, nu, nv, 1)
+    got, _ = _gpu_tips(R, eu, ev, nu, nv, 1, fd_heavy_w=1)
+    assert np.array_equal(got, want)
+    eu, ev = synth.chung_lu(150000, 3000, 600000, 2.3, 2.1, seed=34)
+    want, _ = oracle.bup(eu, ev, 150000, 3000, 0)
+    got, _ = _gpu_tips(R, eu, ev, 150000, 3000, 0, P=1, fd_heavy_w=1)
+    assert np.array_equal(got, want)
+
+
 def test_batch_equals_alone(R):
     specs = synth.batch_specs(24, seed=4)
     graphs, sides, wants = [], [], []
