@@ -176,8 +176,10 @@ __device__ __forceinline__ unsigned long long choose2(unsigned long long c) {
 }
 
 // Block-wide exclusive scan of one value per thread (blockDim.x <= 1024,
-// multiple of 32). `tmp` is __shared__ storage of 33 elements.
-template <typename T>
+// multiple of 32). `tmp` is __shared__ storage of 33 elements. TAIL_SYNC =
+// false leaves out the closing barrier: the caller must pass a barrier
+// before `tmp` is written again.
+template <typename T, bool TAIL_SYNC = true>
 __device__ __forceinline__ T block_exclusive_scan(T v, T *tmp, T *total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
@@ -203,7 +205,7 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T *tmp, T *total) {
     T base = warp ? tmp[warp - 1] : T(0);
     T r = base + x - v;
     if (total) *total = tmp[32];
-    __syncthreads();
+    if (TAIL_SYNC) __syncthreads();
     return r;
 }
 

@@ -484,6 +484,9 @@ struct NoChunkHook {
 template <class Mids, class Visit, class Hook = NoChunkHook>
 __device__ int64_t cta_walk(const Mids &M, int64_t q0, int64_t q1, const int32_t *__restrict__ keys,
                             Chunk &ch, Visit &visit, Hook *hook = nullptr) {
+    // one scan of (segment length | non-empty flag << 40) gives both the
+    // wedge offsets and the compacted slots (a chunk holds < 2^40 wedges)
+    __shared__ long long s_scan[33];
     int64_t walked = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const unsigned lanes_le = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
@@ -492,9 +495,13 @@ __device__ int64_t cta_walk(const Mids &M, int64_t q0, int64_t q1, const int32_t
         int64_t beg = 0;
         int32_t len = 0;
         if ((int)threadIdx.x < nm) M.seg(c0 + threadIdx.x, beg, len);
-        int32_t total, nnz;
-        const int32_t ex = block_exclusive_scan<int32_t>(len, ch.tmp, &total);
-        const int32_t slot = block_exclusive_scan<int32_t>(len > 0 ? 1 : 0, ch.tmp, &nnz);
+        long long tot2;
+        const long long packed = (long long)len | (len > 0 ? (1ll << 40) : 0ll);
+        const long long ex2 = block_exclusive_scan<long long, false>(packed, s_scan, &tot2);
+        const int32_t ex = (int32_t)(ex2 & ((1ll << 40) - 1));
+        const int32_t slot = (int32_t)(ex2 >> 40);
+        const int32_t total = (int32_t)(tot2 & ((1ll << 40) - 1));
+        const int32_t nnz = (int32_t)(tot2 >> 40);
         if (len > 0) {
             ch.beg[slot] = beg;
             ch.pre[slot] = ex;

@@ -168,6 +168,7 @@ struct FdArgs {
     unsigned long long *stats; // [0] wedges, [1] levels
     unsigned long long *sub_ns;     // per subset: nanoseconds spent
     unsigned long long *sub_levels; // per subset: peeling levels
+    unsigned long long *wr;    // by member position: walk size inside G_i (WIDE_BIT: degree >= 65535)
 };
 
 struct FdMids {
@@ -179,11 +180,20 @@ struct FdMids {
     }
 };
 
+// Support decrement of an alive member; the decremented value also lowers
+// *mn, so that after a level's updates *mn holds the minimum support of the
+// survivors (together with the minimum of the untouched ones, taken when the
+// level's peeled vertices are selected).
 struct FdEmit {
     unsigned long long *fsup;  // subset base
     const uint8_t *alive;      // subset base
+    unsigned long long *mn;    // next level's minimum (shared or global)
     __device__ __forceinline__ void operator()(int32_t k, uint32_t c) {
-        if (alive[k]) atomicAdd(&fsup[k], 0ull - choose2(c));
+        if (alive[k]) {
+            const unsigned long long d = choose2(c);
+            const unsigned long long old = atomicAdd(&fsup[k], 0ull - d);
+            atomicMin(mn, old - d);
+        }
     }
 };
 
@@ -225,6 +235,7 @@ struct FdSliceEmit {
 // edges form one virtual list of middle vertices; the thread that stages a
 // middle vertex records its anchor slot for the visits.
 constexpr int FD_BATCH = 32;
+constexpr unsigned long long WIDE_BIT = 1ull << 63;
 
 struct FdBatchMids {
     const int64_t *fd_beg;
@@ -347,7 +358,7 @@ __device__ __forceinline__ unsigned char *fd_bind_smem(unsigned char *smem, int 
 __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_t, s_dn, s_np, s_nk, s_nbig, s_nwide;
-    __shared__ unsigned long long s_min[32];
+    __shared__ unsigned long long s_mn;  // minimum support of the alive members
     __shared__ int64_t s_bq0[FD_BATCH];
     __shared__ int32_t s_bpre[FD_BATCH + 1], s_bself[FD_BATCH];
     __shared__ uint8_t s_slot[FD_THREADS];
@@ -383,41 +394,47 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
         int32_t *plist = a.plist + mb;
         int32_t *blist = a.blist + mb;
         const int32_t *mem = a.members + mb;
+        unsigned long long *wr = a.wr + mb;
+        unsigned long long mn0 = ~0ull;
         for (int r = threadIdx.x; r < ni; r += blockDim.x) {
-            fsup[r] = a.init[mem[r]];
+            const unsigned long long v = a.init[mem[r]];
+            fsup[r] = v;
             alive[r] = 1;
             alist[r] = r;
+            mn0 = v < mn0 ? v : mn0;
         }
+        // walk size of every member inside G_i (one warp per member)
+        for (int r = warp; r < ni; r += nwarps) {
+            const int32_t x = mem[r];
+            const int64_t q0 = a.off_s[x], q1 = a.off_s[x + 1];
+            unsigned long long W = 0;
+            for (int64_t q = q0 + lane; q < q1; q += 32) W += (unsigned long long)a.fd_len[q];
+            W = warp_sum(W);
+            if (lane == 0) wr[r] = W | (q1 - q0 >= 65535 ? WIDE_BIT : 0ull);
+        }
+        mn0 = warp_min(mn0);
+        if (threadIdx.x == 0) s_mn = ~0ull;
+        __syncthreads();
+        if (lane == 0) atomicMin(&s_mn, mn0);
         int32_t nalive = ni;
         unsigned long long level = 0;
         // anchors aggregated per pass of the batched update
         const int32_t bk = ni <= DENSE_KEYS / 2 ? min(FD_BATCH, DENSE_KEYS / ni) : 1;
         __syncthreads();
         while (nalive > 0) {
-            // minimum support over the remaining vertices
-            unsigned long long mn = ~0ull;
-            for (int j = threadIdx.x; j < nalive; j += blockDim.x) {
-                unsigned long long v = fsup[alist[j]];
-                mn = v < mn ? v : mn;
-            }
-            mn = warp_min(mn);
-            if ((threadIdx.x & 31) == 0) s_min[threadIdx.x >> 5] = mn;
+            // mu from the minimum left by the previous level (or the start)
+            const unsigned long long mu = s_mn > level ? s_mn : level;
+            level = mu;
+            levels++;
+            __syncthreads();
             if (threadIdx.x == 0) {
                 s_np = 0;
                 s_nk = 0;
                 s_nbig = 0;
                 s_nwide = 0;
+                s_mn = ~0ull;
             }
             __syncthreads();
-            if (threadIdx.x < 32) {
-                unsigned long long v = threadIdx.x < (blockDim.x >> 5) ? s_min[threadIdx.x] : ~0ull;
-                v = warp_min(v);
-                if (threadIdx.x == 0) s_min[0] = v;
-            }
-            __syncthreads();
-            const unsigned long long mu = s_min[0] > level ? s_min[0] : level;
-            level = mu;
-            levels++;
             // peel every remaining vertex with support <= mu; the rest go to
             // the other alive buffer (ballot compaction, order irrelevant)
             for (int base = 0; base < nalive; base += blockDim.x) {
@@ -430,12 +447,25 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
                 }
                 const bool keep = r >= 0 && v > mu;
                 const bool peel = r >= 0 && !keep;
+                unsigned long long w = 0;
                 if (peel) {
                     alive[r] = 0;
                     a.tip[a.new2old[mem[r]]] = mu;
+                    w = wr[r];
                 }
+                // updates: small walks -> one warp each; bigger ones -> the
+                // batched pass; degree >= 65535 (32-bit counts) or a subset
+                // too large to batch -> one anchor per pass (end of blist)
+                const bool upd = peel && v > 0;
+                const bool small = upd && w <= (unsigned long long)WARP_MAX_W;
+                const bool single = upd && !small && ((w & WIDE_BIT) || bk == 1);
                 warp_append(keep, r, &s_nk, alist_next);
-                warp_append(peel && v > 0, r, &s_np, plist);
+                warp_append(small, r, &s_np, plist);
+                warp_append(upd && !small && !single, r, &s_nbig, blist);
+                if (single) blist[ni - 1 - atomicAdd(&s_nwide, 1)] = r;
+                // minimum of the survivors before this level's updates
+                const unsigned long long kv = warp_min(keep ? v : ~0ull);
+                if (lane == 0 && kv != ~0ull) atomicMin(&s_mn, kv);
             }
             __syncthreads();
             nalive = s_nk;
@@ -446,28 +476,13 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
             }
             const int np = s_np;
             // updates of the peeled vertices inside G_i. Phase A: one warp per
-            // peeled vertex whose update walks at most WARP_MAX_W wedges;
-            // bigger ones are listed for phase B (those of degree >= 65535,
-            // whose counts need 32 bits, from the end of the list).
-            FdEmit emit{fsup, alive};
+            // peeled vertex whose update walks at most WARP_MAX_W wedges.
+            FdEmit emit{fsup, alive, &s_mn};
             for (int pi = warp; pi < np; pi += nwarps) {
                 const int32_t r = plist[pi];
                 const int32_t x = mem[r];
-                const int64_t q0 = a.off_s[x], q1 = a.off_s[x + 1];
-                int64_t W = 0;
-                for (int64_t q = q0 + lane; q < q1; q += 32) W += a.fd_len[q];
-                W = warp_sum(W);
-                if (W > WARP_MAX_W) {
-                    if (lane == 0) {
-                        if (q1 - q0 >= 65535 || bk == 1)
-                            blist[ni - 1 - atomicAdd(&s_nwide, 1)] = r;
-                        else
-                            blist[atomicAdd(&s_nbig, 1)] = r;
-                    }
-                    continue;
-                }
-                fd_update_warp(WH, M, a.fd_adj, q0, q1, r, lane, emit);
-                if (lane == 0) wedges += (unsigned long long)W;
+                fd_update_warp(WH, M, a.fd_adj, a.off_s[x], a.off_s[x + 1], r, lane, emit);
+                if (lane == 0) wedges += wr[r];
             }
             __syncthreads();
             const int nbig = s_nbig, nwide = s_nwide;
@@ -534,17 +549,19 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
 // ------------------------------------------------------------------------
 // Heavy subsets: one subset peeled by all CTAs, level by level. A subset
 // whose wedge count dwarfs the others' would otherwise keep one CTA busy
-// long after the rest of the queue is done. Per level: the minimum support
-// of the alive members; every alive member with support <= mu is peeled
-// (tip mu) and listed by the size of its walk; the warp kernel and the CTA
-// kernel apply the updates of the listed members, one warp or one CTA per
-// member. Same levels, same tip numbers as the one-CTA peel.
+// long after the rest of the queue is done. Per level: mu from the minimum
+// support of the alive members; every alive member with support <= mu is
+// peeled (tip mu) and listed by the size of its walk; the warp kernel and the
+// CTA kernel apply the updates of the listed members, one warp or one CTA per
+// member, and the survivors' minimum for the next level is gathered on the
+// way. Same levels, same tip numbers as the one-CTA peel.
 // ------------------------------------------------------------------------
 struct FdhDev {
-    unsigned long long mn;     // minimum support of the alive members (this level)
-    unsigned long long level;  // mu of the last level
+    unsigned long long mn;       // minimum support of the alive members
+    unsigned long long mn_next;  // the same after this level (survivors, updates)
+    unsigned long long level;    // mu of the last level
     unsigned long long wedges, levels;
-    unsigned long long t0, t1; // globaltimer at the start and at the end
+    unsigned long long t0, t1;   // globaltimer at the start and at the end
     int32_t nalive, nkeep, nw, nb;
 };
 
@@ -571,55 +588,42 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     return t;
 }
 
+__global__ void k_fdh_reset(FdhDev *st, int32_t ni) {
+    st->mn = st->mn_next = ~0ull;
+    st->level = 0;
+    st->wedges = st->levels = 0;
+    st->t0 = globaltimer_ns();
+    st->t1 = 0;
+    st->nalive = ni;
+    st->nkeep = st->nw = st->nb = 0;
+}
+
 __global__ void k_fdh_init(FdhArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long mn = ~0ull;
     for (int64_t r = w0; r < a.ni; r += nw) {
         const int32_t x = a.mem[r];
         unsigned long long W = 0;
         for (int64_t q = a.off_s[x] + lane; q < a.off_s[x + 1]; q += 32) W += a.fd_len[q];
         W = warp_sum(W);
         if (lane == 0) {
-            a.fsup[r] = a.init[x];
+            const unsigned long long v = a.init[x];
+            a.fsup[r] = v;
             a.alive[r] = 1;
             a.wr[r] = W;
-        }
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        FdhDev *st = a.st;
-        st->mn = ~0ull;
-        st->level = 0;
-        st->wedges = st->levels = 0;
-        st->t0 = globaltimer_ns();
-        st->t1 = 0;
-        st->nalive = a.ni;
-        st->nkeep = st->nw = st->nb = 0;
-    }
-}
-
-__global__ void k_fdh_min(FdhArgs a) {
-    __shared__ unsigned long long s_min[32];
-    unsigned long long mn = ~0ull;
-    for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < a.ni; r += gridDim.x * blockDim.x)
-        if (a.alive[r]) {
-            const unsigned long long v = a.fsup[r];
             mn = v < mn ? v : mn;
         }
-    mn = warp_min(mn);
-    if ((threadIdx.x & 31) == 0) s_min[threadIdx.x >> 5] = mn;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        unsigned long long v = threadIdx.x < (blockDim.x >> 5) ? s_min[threadIdx.x] : ~0ull;
-        v = warp_min(v);
-        if (threadIdx.x == 0 && v != ~0ull) atomicMin(&a.st->mn, v);
     }
+    if (lane == 0 && mn != ~0ull) atomicMin(&a.st->mn, mn);
 }
 
 __global__ void k_fdh_select(FdhArgs a) {
     const unsigned long long lv = a.st->level, mn = a.st->mn;
     const unsigned long long mu = mn > lv ? mn : lv;
     int32_t keep = 0;
+    unsigned long long kmin = ~0ull;
     for (int32_t base = blockIdx.x * blockDim.x; base < a.ni; base += gridDim.x * blockDim.x) {
         const int32_t r = base + threadIdx.x;
         const bool al = r < a.ni && a.alive[r];
@@ -633,10 +637,17 @@ __global__ void k_fdh_select(FdhArgs a) {
         const bool small = upd && a.wr[r] <= (unsigned long long)WARP_MAX_W;
         warp_append(small, r, &a.st->nw, a.Lw);
         warp_append(upd && !small, r, &a.st->nb, a.Lb);
-        keep += (al && !peel) ? 1 : 0;
+        if (al && !peel) {
+            keep++;
+            kmin = v < kmin ? v : kmin;
+        }
     }
     keep = warp_sum(keep);
-    if ((threadIdx.x & 31) == 0 && keep) atomicAdd(&a.st->nkeep, keep);
+    kmin = warp_min(kmin);
+    if ((threadIdx.x & 31) == 0) {
+        if (keep) atomicAdd(&a.st->nkeep, keep);
+        if (kmin != ~0ull) atomicMin(&a.st->mn_next, kmin);
+    }
 }
 
 __global__ void __launch_bounds__(256) k_fdh_warp(FdhArgs a) {
@@ -646,7 +657,7 @@ __global__ void __launch_bounds__(256) k_fdh_warp(FdhArgs a) {
     WarpHash WH{skey[w], sval[w]};
     WH.clear(lane);
     __syncwarp();
-    FdEmit emit{a.fsup, a.alive};
+    FdEmit emit{a.fsup, a.alive, &a.st->mn_next};
     FdMids M{a.fd_beg, a.fd_len};
     const int32_t nw = a.st->nw;
     unsigned long long wedges = 0;
@@ -669,7 +680,7 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fdh_cta(FdhArgs a) {
     fd_bind_smem(smem, &s_dn, H, ch);
     H.clear_all();
     __syncthreads();
-    FdEmit emit{a.fsup, a.alive};
+    FdEmit emit{a.fsup, a.alive, &a.st->mn_next};
     const int32_t nb = a.st->nb;
     unsigned long long wedges = 0;
     for (int32_t i = blockIdx.x; i < nb; i += gridDim.x) {
@@ -687,7 +698,8 @@ __global__ void k_fdh_next(FdhDev *st) {
     if (st->nalive == 0) return;
     const unsigned long long mu = st->mn > st->level ? st->mn : st->level;
     st->level = mu;
-    st->mn = ~0ull;
+    st->mn = st->mn_next;
+    st->mn_next = ~0ull;
     st->nalive = st->nkeep;
     st->nkeep = st->nw = st->nb = 0;
     st->levels++;
@@ -781,7 +793,7 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
         while (nheavy < P && hw[hq[nheavy]] >= thr && hms[hq[nheavy] + 1] > hms[hq[nheavy]])
             nheavy++;
     }
-    DevBuf<unsigned long long> fsup(n, s);
+    DevBuf<unsigned long long> fsup(n, s), wr(n, s);
     DevBuf<uint8_t> alive(n, s);
     DevBuf<int32_t> alist(n, s), alist2(n, s), plist(n, s), blist(n, s), qhead(1, s);
     DevBuf<unsigned long long> stats(2, s), sub_ns(P, s), sub_lv(P, s);
@@ -794,7 +806,6 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
     D.fd_heavy_levels = 0;
     std::vector<FdhDev> hh(nheavy);
     if (nheavy > 0) {
-        DevBuf<unsigned long long> wr(n, s);
         DevBuf<FdhDev> hst(1, s);
         const size_t smem_h = DenseSlice::bytes() + CHUNK_BYTES;
         allow_max_smem((const void *)k_fdh_cta);
@@ -820,6 +831,8 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
                        blist.get() + mb,   (unsigned long long *)d_tip,  hst.get()};
             const int gm = std::max(1, std::min(ceil_div(ni, 256), sms * 4));
             const int gi = std::max(1, std::min(ceil_div((int64_t)ni * 32, 256), sms * 16));
+            k_fdh_reset<<<1, 1, 0, s>>>(hst.get(), ni);
+            RC_LAUNCH();
             k_fdh_init<<<gi, 256, 0, s>>>(ha);
             RC_LAUNCH();
             // levels are enqueued in batches; the alive count of batch k is
@@ -827,8 +840,6 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
             // nothing)
             for (int64_t batch = 0;; batch++) {
                 for (int l = 0; l < HEAVY_LEVELS_PER_CHECK; l++) {
-                    k_fdh_min<<<gm, 256, 0, s>>>(ha);
-                    RC_LAUNCH();
                     k_fdh_select<<<gm, 256, 0, s>>>(ha);
                     RC_LAUNCH();
                     k_fdh_warp<<<sms * 8, 256, 0, s>>>(ha);
@@ -859,7 +870,8 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
                  S.off,         fd_beg.get(), fd_len.get(),   fd_adj.get(), S.new2old,
                  D.init,        fsup.get(),  alive.get(),     alist.get(),  alist2.get(),
                  plist.get(),   blist.get(),
-                 (unsigned long long *)d_tip, stats.get(),    sub_ns.get(), sub_lv.get()};
+                 (unsigned long long *)d_tip, stats.get(),    sub_ns.get(), sub_lv.get(),
+                 wr.get()};
         k_fd_peel<<<grid, FD_THREADS, smem, s>>>(a);
         RC_LAUNCH();
     }
