@@ -407,10 +407,12 @@ __global__ void __launch_bounds__(256) k_cd_update_warp(PeelArgs a) {
     __shared__ int32_t skey[8][WARP_SLOTS];
     __shared__ uint32_t sval[8][WARP_SLOTS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // blocks past the round's anchors leave at once (rounds are often empty)
+    const int32_t n = a.st->nLw;
+    if ((int64_t)blockIdx.x * (blockDim.x >> 5) >= n) return;
     WarpHash H{skey[w], sval[w]};
     H.clear(lane);
     __syncwarp();
-    const int32_t n = a.st->nLw;
     CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext};
     unsigned long long cw = 0, cm = 0, ca = 0;
     for (;;) {
@@ -474,6 +476,8 @@ __global__ void __maxnreg__(64) k_cd_update_cta(PeelArgs a, int32_t head_cap,
                                                             int32_t bm_cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_idx, s_used, s_over;
+    const int32_t n = a.st->nLc;
+    if ((int32_t)blockIdx.x >= n) return;
     CtaHybrid H;
     unsigned char *p = H.bind(smem, head_cap, bm_cap, &s_used, &s_over);
     Chunk ch;
@@ -483,7 +487,6 @@ __global__ void __maxnreg__(64) k_cd_update_cta(PeelArgs a, int32_t head_cap,
     ch.len = chunk_len_ptr(ch.tmp);
     H.clear_all();
     __syncthreads();
-    const int32_t n = a.st->nLc;
     CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext};
     PeelMids M{a.adj_s, a.off_o, a.len_o};
     unsigned long long cw = 0, cm = 0, ca = 0;
@@ -497,7 +500,7 @@ __global__ void __maxnreg__(64) k_cd_update_cta(PeelArgs a, int32_t head_cap,
         const int32_t kw = a.Lc_w[idx];
         H.set_range((int32_t)imin64(H.head_cap, kw), kw);
         SliceVisit<CtaHybrid> v{&H, x - kb, kb};
-        cw += cta_walk(M, a.off_s[x], a.off_s[x + 1], a.adj_o, ch, v);
+        cw += cta_walk<false>(M, a.off_s[x], a.off_s[x + 1], a.adj_o, ch, v);
         cm += (unsigned long long)(a.off_s[x + 1] - a.off_s[x]);
         ca++;
         SliceEmit em{&emit, kb};
@@ -534,6 +537,7 @@ __global__ void __maxnreg__(64) k_cd_update_global(PeelArgs a, uint32_t *gcnt,
     ch.len = chunk_len_ptr(ch.tmp);
     GlobalDense G{gcnt + (size_t)blockIdx.x * keyspace, gtouch + (size_t)blockIdx.x * keyspace, &s_nt};
     const int32_t n1 = a.st->nLg, n2 = 0;
+    if ((int32_t)blockIdx.x >= n1 + n2) return;
     CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext};
     PeelMids M{a.adj_s, a.off_o, a.len_o};
     unsigned long long cw = 0, cm = 0, ca = 0;
@@ -566,11 +570,14 @@ __global__ void __maxnreg__(64) k_cd_update_global(PeelArgs a, uint32_t *gcnt,
 // every (anchor, slice) pair is one work item, so the slices of a heavy
 // anchor run on different CTAs. Each item aggregates its slice with dense
 // 16-bit counters in shared memory.
-__global__ void __launch_bounds__(SLICE_THREADS, 2) k_cd_update_slice(PeelArgs a, int32_t n) {
+using SliceEngine = DenseSliceT<SLICE_WORDS>;
+
+__global__ void __launch_bounds__(SLICE_THREADS, 1) k_cd_update_slice(PeelArgs a, int32_t n) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_idx;
     __shared__ int s_nt;
-    DenseSlice H;
+    if (a.st->nLs == 0) return;
+    SliceEngine H;
     unsigned char *p = H.bind(smem, &s_nt);
     Chunk ch;
     ch.beg = (int64_t *)p;
@@ -611,7 +618,7 @@ __global__ void __launch_bounds__(SLICE_THREADS, 2) k_cd_update_slice(PeelArgs a
         H.set_width(w);
         SlicedMids M{a.adj_s, a.off_o, a.soff, a.len_o, a.adj_o, a.C + 1, j, a.SW};
         const int32_t self = (x >= base && x < base + w) ? x - base : -1;
-        SliceVisit<DenseSlice> v{&H, self, base};
+        SliceVisit<SliceEngine> v{&H, self, base};
         int64_t walked = cta_walk(M, q0, q1, a.adj_o, ch, v);
         cw += walked;
         if (walked == 0) continue;
@@ -635,6 +642,8 @@ __global__ void __launch_bounds__(SLICE_THREADS, 2) k_cd_update_slice(PeelArgs a
 __global__ void __maxnreg__(64) k_cd_update_dense(PeelArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_idx, s_nt;
+    const int32_t n = a.st->nLd;
+    if ((int32_t)blockIdx.x >= n) return;
     DenseSlice H;
     unsigned char *p = H.bind(smem, &s_nt);
     Chunk ch;
@@ -647,7 +656,6 @@ __global__ void __maxnreg__(64) k_cd_update_dense(PeelArgs a) {
     CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext};
     PeelMids M{a.adj_s, a.off_o, a.len_o};
     unsigned long long cw = 0, cm = 0, ca = 0;
-    const int32_t n = a.st->nLd;
     for (;;) {
         if (threadIdx.x == 0) s_idx = atomicAdd(&a.st->work[4], 1);
         __syncthreads();
@@ -813,7 +821,7 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
             RC_LAUNCH();
         }
     }
-    const size_t smem_slice = DenseSlice::bytes() + CHUNK_BYTES;
+    const size_t smem_slice = SliceEngine::bytes() + CHUNK_BYTES;
     allow_max_smem((const void *)k_cd_update_slice);
     int occ_s = 1;
     RC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, k_cd_update_slice, SLICE_THREADS,
@@ -829,7 +837,7 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
     if (cta_ok) allow_max_smem((const void *)k_cd_update_cta);
     allow_max_smem((const void *)k_cd_update_dense);
     int occ_d = 1;
-    RC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_d, k_cd_update_dense, SLICE_THREADS,
+    RC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_d, k_cd_update_dense, DENSE_THREADS,
                                                           DenseSlice::bytes() + CHUNK_BYTES));
     const int dblocks = sms * std::max(1, occ_d);
     // global-counter slots only exist if the side has a hub whose counts can
@@ -900,7 +908,7 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
             k_cd_update_warp<<<sms * 8, 256, 0, s>>>(a);
             RC_LAUNCH();
             if (D.timing) RC_CUDA(cudaEventRecord(ev[1], s));
-            k_cd_update_dense<<<dblocks, SLICE_THREADS, DenseSlice::bytes() + CHUNK_BYTES, s>>>(a);
+            k_cd_update_dense<<<dblocks, DENSE_THREADS, DenseSlice::bytes() + CHUNK_BYTES, s>>>(a);
             RC_LAUNCH();
             if (D.timing) RC_CUDA(cudaEventRecord(ev[2], s));
             if (cta_ok) {

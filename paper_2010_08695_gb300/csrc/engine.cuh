@@ -30,13 +30,15 @@ constexpr int32_t EMPTY_KEY = -1;
 constexpr int WARP_MAX_W = 256;     // wedges of a warp-tier anchor
 constexpr int WARP_SLOTS = 512;     // per-warp table (load factor <= 1/2)
 constexpr int CTA_THREADS = 1024;
-constexpr int SLICE_THREADS = 512;  // CTAs of the key-sliced tier (two per SM)
+constexpr int SLICE_THREADS = 1024; // CTAs of the key-sliced tier (one per SM)
+constexpr int DENSE_THREADS = 512;  // CTAs of the dense-window tier (two per SM)
 constexpr int MID_CHUNK = CTA_THREADS;
 constexpr int REPEAT_SLOTS = 4096;  // CtaHybrid repeat table
 constexpr int REPEAT_LIMIT = REPEAT_SLOTS / 2;
 constexpr int HEAD_MAX = 16384;     // dense 16-bit counters for keys < head
 constexpr int HEAD_SLICE = 2048;    // head of the key slices after the first
-constexpr int SLICE_KEYS = 36864;   // keys per slice of the sliced tier (= dense slice)
+constexpr int SLICE_WORDS = 45056;  // 16-bit counter words of a slice of the sliced tier
+constexpr int SLICE_KEYS = 2 * SLICE_WORDS;  // keys per slice of the sliced tier
 constexpr int SLICE_MIN_W = 49152;  // anchors with more wedges use the sliced tier
 constexpr int MAX_PROBE = 64;
 constexpr int WALK_UNROLL = 8;     // independent loads in flight per warp in cta_walk
@@ -100,8 +102,8 @@ struct WarpHash {
 // Keys from headn on set a bit in a bitmap; a bit found already set sends the
 // key to a small open-addressing table of extra occurrences; every repeat slot
 // taken is listed, so the table is flushed and cleared in time proportional
-// to its use. Head counters and the bitmap are swept with 16-byte accesses
-// over the key range in use.
+// to its use. The head is swept one word per thread and step; the bitmap is
+// cleared with 16-byte stores over the key range in use.
 struct CtaHybrid {
     uint32_t *head;   // head_cap/2 words
     uint32_t *hsum;   // reserved (keeps the layout 16-byte aligned)
@@ -231,21 +233,17 @@ struct CtaHybrid {
     __device__ void sweep(Emit &emit) {
         const int used = *(volatile int *)s_used;
         const int over = *(volatile int *)s_over;
-        // head: words [0, hw), four at a time
-        const int hw4 = (hw + 3) >> 2;
-        for (int i = threadIdx.x; i < hw4; i += blockDim.x) {
-            uint4 v = ((uint4 *)head)[i];
-            if ((v.x | v.y | v.z | v.w) == 0) continue;
-            if (CLEAR) ((uint4 *)head)[i] = make_uint4(0, 0, 0, 0);
+        // head: words [0, hw), one per thread and step, so that the hot low
+        // keys (the window's highest-degree vertices) and their emits are
+        // spread over all threads
+        for (int w = threadIdx.x; w < hw; w += blockDim.x) {
+            const uint32_t v = head[w];
+            if (v == 0) continue;
+            if (CLEAR) head[w] = 0;
             if (EMIT) {
-                const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                for (int e = 0; e < 4; e++) {
-                    const int w = 4 * i + e;
-                    const uint32_t c0 = vv[e] & 0xffffu, c1 = vv[e] >> 16;
-                    if (c0 >= 2) emit(w, c0);
-                    if (c1 >= 2) emit(w + hw, c1);
-                }
+                const uint32_t c0 = v & 0xffffu, c1 = v >> 16;
+                if (c0 >= 2) emit(w, c0);
+                if (c1 >= 2) emit(w + hw, c1);
             }
         }
         // tail bitmap: the words the current key range can use
@@ -316,34 +314,37 @@ inline size_t hybrid_bytes(int64_t keyspace, int32_t *head_cap_out = nullptr,
 // list (one shared atomic per warp and step), so flushing and clearing cost
 // what the slice touched; past the list's capacity the sweep scans the slice.
 // Counts must stay below 2^16 (the caller routes anchors of degree >= 65535
-// elsewhere).
+// elsewhere) unless the slice is set up with 32-bit counters. WORDS counter
+// words (at most 65,536: touched-list entries are 16-bit word indices).
 constexpr int DENSE_KEYS = 36864;               // keys per dense slice
 constexpr int DENSE_WORDS = DENSE_KEYS / 2;     // 18432 words (72 KB)
 constexpr int TOUCH_CAP = 8192;                 // touched-word list capacity
 
-struct DenseSlice {
-    uint32_t *cnt;     // DENSE_WORDS
+template <int WORDS>
+struct DenseSliceT {
+    static_assert(WORDS % 4 == 0 && WORDS <= 65536, "counter words");
+    uint32_t *cnt;     // WORDS
     uint16_t *tl;      // TOUCH_CAP
     int *s_nt;         // shared scalar: touched words
-    int32_t hw;        // half of the current slice width (<= DENSE_WORDS)
-    bool wide;         // 32-bit counters, one key per word (slices of DENSE_WORDS keys)
+    int32_t hw;        // half of the current slice width (<= WORDS)
+    bool wide;         // 32-bit counters, one key per word (slices of WORDS keys)
 
-    static constexpr size_t bytes() { return (size_t)DENSE_WORDS * 4 + (size_t)TOUCH_CAP * 2; }
+    static constexpr size_t bytes() { return (size_t)WORDS * 4 + (size_t)TOUCH_CAP * 2; }
     __device__ unsigned char *bind(unsigned char *base, int *nt) {
         cnt = (uint32_t *)base;
-        tl = (uint16_t *)(cnt + DENSE_WORDS);
+        tl = (uint16_t *)(cnt + WORDS);
         s_nt = nt;
-        hw = DENSE_WORDS;
+        hw = WORDS;
         wide = false;
         return (unsigned char *)(tl + TOUCH_CAP);
     }
     __device__ void clear_all() {
-        for (int i = threadIdx.x; i < DENSE_WORDS / 4; i += blockDim.x)
+        for (int i = threadIdx.x; i < WORDS / 4; i += blockDim.x)
             ((uint4 *)cnt)[i] = make_uint4(0, 0, 0, 0);
         if (threadIdx.x == 0) *s_nt = 0;
     }
-    // Slice of w keys: 16-bit counters (w <= DENSE_KEYS), or 32-bit counters
-    // when counts may reach 2^16 (w <= DENSE_WORDS).
+    // Slice of w keys: 16-bit counters (w <= 2 * WORDS), or 32-bit counters
+    // when counts may reach 2^16 (w <= WORDS).
     __device__ void set_width(int32_t w, bool wide_counts = false) {
         wide = wide_counts;
         hw = wide ? w : (w + 1) >> 1;
@@ -392,24 +393,18 @@ struct DenseSlice {
                 }
             }
         } else {
-            const int hw4 = (hw + 3) >> 2;
-            for (int i = threadIdx.x; i < hw4; i += blockDim.x) {
-                uint4 v = ((uint4 *)cnt)[i];
-                if ((v.x | v.y | v.z | v.w) == 0) continue;
-                if (CLEAR) ((uint4 *)cnt)[i] = make_uint4(0, 0, 0, 0);
+            for (int w = threadIdx.x; w < hw; w += blockDim.x) {
+                const uint32_t v = cnt[w];
+                if (v == 0) continue;
+                if (CLEAR) cnt[w] = 0;
                 if (EMIT) {
-                    const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                    for (int e = 0; e < 4; e++) {
-                        const int w = 4 * i + e;
-                        if (wide) {
-                            if (vv[e] >= 2) emit(w, vv[e]);
-                            continue;
-                        }
-                        const uint32_t c0 = vv[e] & 0xffffu, c1 = vv[e] >> 16;
-                        if (c0 >= 2) emit(w, c0);
-                        if (c1 >= 2) emit(w + hw, c1);
+                    if (wide) {
+                        if (v >= 2) emit(w, v);
+                        continue;
                     }
+                    const uint32_t c0 = v & 0xffffu, c1 = v >> 16;
+                    if (c0 >= 2) emit(w, c0);
+                    if (c1 >= 2) emit(w + hw, c1);
                 }
             }
         }
@@ -418,6 +413,8 @@ struct DenseSlice {
         if (threadIdx.x == 0) *s_nt = 0;
     }
 };
+
+using DenseSlice = DenseSliceT<DENSE_WORDS>;
 
 // ------------------------------------------------------------------
 // Global dense counters + touched list (one slot per CTA)
@@ -471,8 +468,10 @@ struct NoChunkHook {
 // Walks every wedge of one anchor: for q in [q0, q1) (middle vertices), the
 // segment M.seg(q) of `keys`. The non-empty segments of up to blockDim.x
 // middle vertices are staged at a time; the flat list of their wedges is cut
-// into 32-wedge groups and each warp takes WALK_UNROLL consecutive groups per
-// step. In a group, lane i fetches the start of the i-th segment after the
+// into 32-wedge groups. BALANCED: every warp takes an equal contiguous share
+// of the groups, WALK_UNROLL per step; otherwise warps take WALK_UNROLL
+// consecutive groups in turn (fewer warps busy on small chunks, which suits
+// the hybrid engine's shared-memory traffic). In a group, lane i fetches the start of the i-th segment after the
 // group's first one; one OR-reduction of those starts gives every lane the
 // segment its wedge falls in (a population count), so every lane loads a key
 // even when segments are short, and all loads of a step are issued before any
@@ -481,7 +480,7 @@ struct NoChunkHook {
 //   __device__ void seg(int64_t q, int64_t &beg, int32_t &len) const;
 // visit(k, key): k = mid index within the chunk, key = end point.
 // Returns the number of wedges walked. All threads of the CTA must call it.
-template <class Mids, class Visit, class Hook = NoChunkHook>
+template <bool BALANCED = true, class Mids, class Visit, class Hook = NoChunkHook>
 __device__ int64_t cta_walk(const Mids &M, int64_t q0, int64_t q1, const int32_t *__restrict__ keys,
                             Chunk &ch, Visit &visit, Hook *hook = nullptr) {
     // one scan of (segment length | non-empty flag << 40) gives both the
@@ -510,7 +509,10 @@ __device__ int64_t cta_walk(const Mids &M, int64_t q0, int64_t q1, const int32_t
         if (threadIdx.x == 0) ch.pre[nnz] = total;
         __syncthreads();
         const int32_t groups = (total + 31) >> 5;
-        for (int32_t gb = warp * WALK_UNROLL; gb < groups; gb += nwarps * WALK_UNROLL) {
+        const int32_t g_lo = BALANCED ? (int32_t)(((int64_t)groups * warp) / nwarps) : warp * WALK_UNROLL;
+        const int32_t g_hi = BALANCED ? (int32_t)(((int64_t)groups * (warp + 1)) / nwarps) : groups;
+        const int32_t g_step = BALANCED ? WALK_UNROLL : nwarps * WALK_UNROLL;
+        for (int32_t gb = g_lo; gb < g_hi; gb += g_step) {
             // segment of the first wedge of group gb (warp-uniform search)
             int lo = 0, hi = nnz - 1;
             const int32_t b0 = gb << 5;
@@ -528,7 +530,7 @@ __device__ int64_t cta_walk(const Mids &M, int64_t q0, int64_t q1, const int32_t
             for (int u = 0; u < WALK_UNROLL; u++) {
                 const int32_t base = (gb + u) << 5;
                 kk[u] = -1;
-                if (base < total) {
+                if (BALANCED ? gb + u < g_hi : base < total) {
                     while (ch.pre[k0 + 1] <= base) k0++;
                     const int kn = k0 + 1 + lane;
                     const int32_t bnd = kn < nnz ? ch.pre[kn] - base : 32;
