@@ -524,6 +524,10 @@ __device__ int64_t cta_walk(const Mids &M, int64_t q0, int64_t q1, const int32_t
                     hi = mid - 1;
             }
             int k0 = lo;
+            // segment k0 in registers: wedges [p0, p1), first key, mid index
+            int32_t p0 = ch.pre[k0], p1 = ch.pre[k0 + 1];
+            int64_t bg0 = ch.beg[k0];
+            int kl0 = ch.len[k0];
             int kk[WALK_UNROLL];
             int32_t key[WALK_UNROLL];
 #pragma unroll
@@ -531,15 +535,29 @@ __device__ int64_t cta_walk(const Mids &M, int64_t q0, int64_t q1, const int32_t
                 const int32_t base = (gb + u) << 5;
                 kk[u] = -1;
                 if (BALANCED ? gb + u < g_hi : base < total) {
-                    while (ch.pre[k0 + 1] <= base) k0++;
-                    const int kn = k0 + 1 + lane;
-                    const int32_t bnd = kn < nnz ? ch.pre[kn] - base : 32;
-                    const unsigned m = __reduce_or_sync(0xffffffffu, bnd < 32 ? (1u << bnd) : 0u);
-                    const int k = k0 + __popc(m & lanes_le);
                     const int32_t j = base + lane;
-                    if (j < total) {
-                        kk[u] = ch.len[k];
-                        key[u] = __ldg(keys + ch.beg[k] + (j - ch.pre[k]));
+                    if (base >= p0 && base + 32 <= p1) {
+                        // the whole group lies in segment k0 (long lists: the
+                        // common case), no shared-memory lookups
+                        kk[u] = kl0;
+                        key[u] = __ldg(keys + bg0 + (j - p0));
+                    } else {
+                        while (ch.pre[k0 + 1] <= base) k0++;
+                        const int kn = k0 + 1 + lane;
+                        const int32_t bnd = kn < nnz ? ch.pre[kn] - base : 32;
+                        const unsigned m =
+                            __reduce_or_sync(0xffffffffu, bnd < 32 ? (1u << bnd) : 0u);
+                        const int k = k0 + __popc(m & lanes_le);
+                        if (j < total) {
+                            kk[u] = ch.len[k];
+                            key[u] = __ldg(keys + ch.beg[k] + (j - ch.pre[k]));
+                        }
+                        // continue from the segment of the group's last wedge
+                        k0 = min(k0 + __popc(m), nnz - 1);
+                        p0 = ch.pre[k0];
+                        p1 = ch.pre[k0 + 1];
+                        bg0 = ch.beg[k0];
+                        kl0 = ch.len[k0];
                     }
                 }
             }
