@@ -266,13 +266,27 @@ __global__ void k_cd_route(CdDev *st, const int32_t *__restrict__ Lb,
         const int32_t x = Lb[i];
         const int64_t q0 = off_s[x], q1 = off_s[x + 1];
         int32_t kmin = INT32_MAX, kmax = -1;
-        for (int64_t q = q0 + lane; q < q1; q += 32) {
-            const int32_t y = adj_s[q];
-            const int64_t b = off_o[y], e = b + len_o[y];
-            if (e > b) {
-                kmin = min(kmin, adj_o[b]);
-                kmax = max(kmax, adj_o[e - 1]);
+        // four middle vertices per lane and step, loads independent
+        for (int64_t qb = q0; qb < q1; qb += 128) {
+            int32_t y[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int64_t q = qb + 32 * u + lane;
+                y[u] = q < q1 ? adj_s[q] : -1;
             }
+            int64_t b[4];
+            int32_t l[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                b[u] = y[u] >= 0 ? off_o[y[u]] : 0;
+                l[u] = y[u] >= 0 ? len_o[y[u]] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if (l[u] > 0) {
+                    kmin = min(kmin, adj_o[b[u]]);
+                    kmax = max(kmax, adj_o[b[u] + l[u] - 1]);
+                }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -695,18 +709,24 @@ __global__ void k_dgm_compact(const int64_t *__restrict__ off_o, int32_t *__rest
         const int64_t b = off_o[y];
         const int32_t l = len_o[y];
         int32_t w = 0;
-        for (int32_t r0 = 0; r0 < l; r0 += 32) {
-            const int32_t r = r0 + lane;
-            int32_t x = -1;
-            bool keep = false;
-            if (r < l) {
-                x = adj_w[b + r];
-                keep = sub[x] < 0;
+        // 128 entries per step: all loads first, then the ordered writes
+        for (int32_t r0 = 0; r0 < l; r0 += 128) {
+            int32_t x[4];
+            bool keep[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int32_t r = r0 + 32 * u + lane;
+                x[u] = r < l ? adj_w[b + r] : -1;
             }
-            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+#pragma unroll
+            for (int u = 0; u < 4; u++) keep[u] = x[u] >= 0 && sub[x[u]] < 0;
             __syncwarp();
-            if (keep) adj_w[b + w + __popc(bal & lanemask_lt())] = x;
-            w += __popc(bal);
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const unsigned bal = __ballot_sync(0xffffffffu, keep[u]);
+                if (keep[u]) adj_w[b + w + __popc(bal & lanemask_lt())] = x[u];
+                w += __popc(bal);
+            }
             __syncwarp();
         }
         if (lane == 0) len_o[y] = w;
@@ -740,11 +760,13 @@ __global__ void k_cd_advance(CdDev *st) {
 }
 
 __global__ void k_cd_new_range(CdDev *st) {
-    st->nF = st->nNext = 0;
-    st->nLw = st->nLc = st->nLg = st->nLo = st->nLs = st->nLb = st->nLd = 0;
-    for (int i = 0; i < 6; i++) st->work[i] = 0;
-    st->work64 = 0;
-    for (int b = 0; b < NBUCKET; b++) {
+    if (threadIdx.x == 0) {
+        st->nF = st->nNext = 0;
+        st->nLw = st->nLc = st->nLg = st->nLo = st->nLs = st->nLb = st->nLd = 0;
+        for (int i = 0; i < 6; i++) st->work[i] = 0;
+        st->work64 = 0;
+    }
+    for (int b = threadIdx.x; b < NBUCKET; b += blockDim.x) {
         st->hist_w[b] = 0;
         st->hist_c[b] = 0;
     }
@@ -872,7 +894,7 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
     const int nranges = opt.n_bounds > 0 ? std::min(opt.n_bounds, P) : P;
     int32_t *cur = F.get(), *nxt = Nx.get();
     for (range = 0; range < nranges; range++) {
-        k_cd_new_range<<<1, 1, 0, s>>>(st.get());
+        k_cd_new_range<<<1, 256, 0, s>>>(st.get());
         RC_LAUNCH();
         k_cd_hist<<<nb, 512, 0, s>>>(n, D.sub, D.sup, D.wfull, S.off, D.init, st.get());
         RC_LAUNCH();

@@ -30,6 +30,12 @@ namespace receipt {
 namespace {
 
 constexpr int FD_THREADS = 512;
+// dense counters of the fine-grained step: 30,720 words (61,440 16-bit keys)
+constexpr int FD_WORDS = 30720;
+constexpr int FD_KEYS = 2 * FD_WORDS;
+using FdEngine = DenseSliceT<FD_WORDS>;
+// walk-size flag: the vertex's degree is >= 65535 (counts may need 32 bits)
+constexpr unsigned long long WIDE_BIT = 1ull << 63;
 // heavy subsets: automatic threshold and levels enqueued per alive check
 constexpr unsigned long long HEAVY_MIN_W = 1ull << 23;
 constexpr unsigned long long HEAVY_SHARE = 8;
@@ -132,6 +138,25 @@ __global__ void k_fd_edges(const uint32_t *__restrict__ perm, int64_t m,
     }
 }
 
+__global__ void k_i32_to_i64(const int32_t *__restrict__ v, int64_t m, int64_t *__restrict__ out) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < m) out[q] = v[q];
+}
+
+// Walk size inside G_i of every vertex (sum of its edges' run lengths, from
+// the prefix sums `pre`), stored at its member position; WIDE_BIT marks a
+// degree >= 65535 (counts may need 32 bits).
+__global__ void k_fd_walk_sizes(const int64_t *__restrict__ off_s, int32_t n,
+                                const int64_t *__restrict__ pre, const int32_t *__restrict__ sub,
+                                const int32_t *__restrict__ mstart, const int32_t *__restrict__ rank,
+                                unsigned long long *__restrict__ wr) {
+    int32_t x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= n) return;
+    const int64_t q0 = off_s[x], q1 = off_s[x + 1];
+    const unsigned long long W = (unsigned long long)(pre[q1] - pre[q0]);
+    wr[mstart[sub[x]] + rank[x]] = W | (q1 - q0 >= 65535 ? WIDE_BIT : 0ull);
+}
+
 // LPT order: rank of subset i = number of subsets with larger work (ties by id).
 __global__ void k_lpt(const unsigned long long *__restrict__ wsub, const int32_t *__restrict__ mstart,
                       int32_t P, int32_t *__restrict__ queue) {
@@ -216,7 +241,7 @@ struct FdSliceMids {
 };
 
 struct FdSliceVisit {
-    DenseSlice *eng;
+    FdEngine *eng;
     int32_t base;  // first rank of the slice
     int32_t self;  // the anchor's own rank
     __device__ __forceinline__ void operator()(int, int32_t key) {
@@ -235,7 +260,6 @@ struct FdSliceEmit {
 // edges form one virtual list of middle vertices; the thread that stages a
 // middle vertex records its anchor slot for the visits.
 constexpr int FD_BATCH = 32;
-constexpr unsigned long long WIDE_BIT = 1ull << 63;
 
 struct FdBatchMids {
     const int64_t *fd_beg;
@@ -261,7 +285,7 @@ struct FdBatchMids {
 };
 
 struct FdBatchVisit {
-    DenseSlice *eng;
+    FdEngine *eng;
     const uint8_t *slot;
     const int32_t *bself;  // rank of each anchor
     int32_t ni;
@@ -314,12 +338,12 @@ __device__ __forceinline__ void fd_update_warp(WarpHash &WH, const FdMids &M,
 // slice by slice of the subset's rank space (ni ranks) with dense counters,
 // 32-bit ones when the anchor's degree lets a count reach 2^16. Returns the
 // wedges walked (the same value in every thread). All threads must call it.
-__device__ int64_t fd_update_cta(DenseSlice &H, Chunk &ch, const int64_t *__restrict__ fd_beg,
+__device__ int64_t fd_update_cta(FdEngine &H, Chunk &ch, const int64_t *__restrict__ fd_beg,
                                  const int32_t *__restrict__ fd_len,
                                  const int32_t *__restrict__ fd_adj, int64_t q0, int64_t q1,
                                  int32_t r, int32_t ni, FdEmit &emit) {
     const bool wide = q1 - q0 >= 65535;
-    const int32_t SWk = wide ? DENSE_WORDS : DENSE_KEYS;
+    const int32_t SWk = wide ? FD_WORDS : FD_KEYS;
     const int32_t C = (ni + SWk - 1) / SWk;
     int64_t wedges = 0;
     for (int32_t j = 0; j < C; j++) {
@@ -345,7 +369,7 @@ __device__ int64_t fd_update_cta(DenseSlice &H, Chunk &ch, const int64_t *__rest
     return wedges;
 }
 
-__device__ __forceinline__ unsigned char *fd_bind_smem(unsigned char *smem, int *s_dn, DenseSlice &H,
+__device__ __forceinline__ unsigned char *fd_bind_smem(unsigned char *smem, int *s_dn, FdEngine &H,
                                                        Chunk &ch) {
     unsigned char *p = H.bind(smem, s_dn);
     ch.beg = (int64_t *)p;
@@ -362,7 +386,7 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
     __shared__ int64_t s_bq0[FD_BATCH];
     __shared__ int32_t s_bpre[FD_BATCH + 1], s_bself[FD_BATCH];
     __shared__ uint8_t s_slot[FD_THREADS];
-    DenseSlice H;
+    FdEngine H;
     Chunk ch;
     // warp-private tables after the chunk staging
     int32_t *wkey = (int32_t *)fd_bind_smem(smem, &s_dn, H, ch);
@@ -403,15 +427,6 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
             alist[r] = r;
             mn0 = v < mn0 ? v : mn0;
         }
-        // walk size of every member inside G_i (one warp per member)
-        for (int r = warp; r < ni; r += nwarps) {
-            const int32_t x = mem[r];
-            const int64_t q0 = a.off_s[x], q1 = a.off_s[x + 1];
-            unsigned long long W = 0;
-            for (int64_t q = q0 + lane; q < q1; q += 32) W += (unsigned long long)a.fd_len[q];
-            W = warp_sum(W);
-            if (lane == 0) wr[r] = W | (q1 - q0 >= 65535 ? WIDE_BIT : 0ull);
-        }
         mn0 = warp_min(mn0);
         if (threadIdx.x == 0) s_mn = ~0ull;
         __syncthreads();
@@ -419,7 +434,7 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
         int32_t nalive = ni;
         unsigned long long level = 0;
         // anchors aggregated per pass of the batched update
-        const int32_t bk = ni <= DENSE_KEYS / 2 ? min(FD_BATCH, DENSE_KEYS / ni) : 1;
+        const int32_t bk = ni <= FD_KEYS / 2 ? min(FD_BATCH, FD_KEYS / ni) : 1;
         __syncthreads();
         while (nalive > 0) {
             // mu from the minimum left by the previous level (or the start)
@@ -604,15 +619,10 @@ __global__ void k_fdh_init(FdhArgs a) {
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long mn = ~0ull;
     for (int64_t r = w0; r < a.ni; r += nw) {
-        const int32_t x = a.mem[r];
-        unsigned long long W = 0;
-        for (int64_t q = a.off_s[x] + lane; q < a.off_s[x + 1]; q += 32) W += a.fd_len[q];
-        W = warp_sum(W);
         if (lane == 0) {
-            const unsigned long long v = a.init[x];
+            const unsigned long long v = a.init[a.mem[r]];
             a.fsup[r] = v;
             a.alive[r] = 1;
-            a.wr[r] = W;
             mn = v < mn ? v : mn;
         }
     }
@@ -675,7 +685,7 @@ __global__ void __launch_bounds__(256) k_fdh_warp(FdhArgs a) {
 __global__ void __launch_bounds__(FD_THREADS, 1) k_fdh_cta(FdhArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_dn;
-    DenseSlice H;
+    FdEngine H;
     Chunk ch;
     fd_bind_smem(smem, &s_dn, H, ch);
     H.clear_all();
@@ -732,6 +742,7 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
     // induced subgraphs
     DevBuf<int32_t> fd_adj(m, s), fd_len(m, s);
     DevBuf<int64_t> fd_beg(m, s);
+    DevBuf<unsigned long long> wr(n, s);
     DevBuf<unsigned long long> wsub(P, s);
     wsub.zero();
     if (m > 0) {
@@ -758,6 +769,17 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
                                                     hpos.get(), run_start.get(), nruns, S.off, S.adj,
                                                     D.sub, fd_beg.get(), fd_len.get(), wsub.get());
         RC_LAUNCH();
+        // walk sizes of all vertices: prefix sums of the run lengths
+        DevBuf<int64_t> l64(m + 1, s), pre(m + 1, s);
+        k_i32_to_i64<<<ceil_div(m, 256), 256, 0, s>>>(fd_len.get(), m, l64.get());
+        RC_LAUNCH();
+        RC_CUDA(cudaMemsetAsync(l64.get() + m, 0, sizeof(int64_t), s));
+        scan_exclusive<int64_t>(l64.get(), pre.get(), m + 1, s);
+        k_fd_walk_sizes<<<ceil_div(n, 256), 256, 0, s>>>(S.off, n, pre.get(), D.sub, mstart.get(),
+                                                         rank.get(), wr.get());
+        RC_LAUNCH();
+    } else {
+        wr.zero();
     }
     DevBuf<int32_t> queue(P, s);
     k_lpt<<<ceil_div(P, 256), 256, 0, s>>>(wsub.get(), mstart.get(), P, queue.get());
@@ -771,7 +793,7 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
     RC_CUDA(cudaMemcpyAsync(hw.data(), wsub.get(), 8 * P, cudaMemcpyDeviceToHost, s));
     RC_CUDA(cudaStreamSynchronize(s));
     const size_t warp_tables = (size_t)(FD_THREADS / 32) * WARP_SLOTS * 8 + 16;
-    const size_t smem = DenseSlice::bytes() + CHUNK_BYTES + warp_tables;
+    const size_t smem = FdEngine::bytes() + CHUNK_BYTES + warp_tables;
     allow_max_smem((const void *)k_fd_peel);
     int occ = 0;
     RC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fd_peel, FD_THREADS, smem));
@@ -793,7 +815,7 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
         while (nheavy < P && hw[hq[nheavy]] >= thr && hms[hq[nheavy] + 1] > hms[hq[nheavy]])
             nheavy++;
     }
-    DevBuf<unsigned long long> fsup(n, s), wr(n, s);
+    DevBuf<unsigned long long> fsup(n, s);
     DevBuf<uint8_t> alive(n, s);
     DevBuf<int32_t> alist(n, s), alist2(n, s), plist(n, s), blist(n, s), qhead(1, s);
     DevBuf<unsigned long long> stats(2, s), sub_ns(P, s), sub_lv(P, s);
@@ -807,7 +829,7 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
     std::vector<FdhDev> hh(nheavy);
     if (nheavy > 0) {
         DevBuf<FdhDev> hst(1, s);
-        const size_t smem_h = DenseSlice::bytes() + CHUNK_BYTES;
+        const size_t smem_h = FdEngine::bytes() + CHUNK_BYTES;
         allow_max_smem((const void *)k_fdh_cta);
         int occ_h = 0;
         RC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_h, k_fdh_cta, FD_THREADS, smem_h));
