@@ -188,6 +188,31 @@ struct CountOppVisit {
         uint32_t c = eng->count(key);
         if (c > 1) atomicAdd(&sacc[k], (unsigned long long)(c - 1));
     }
+    // One walk step: where all the warp's wedges of a group share one middle
+    // vertex (long lists), the warp sums its contributions first and makes
+    // one shared-memory atomic instead of 32 to the same word.
+    template <int N>
+    __device__ __forceinline__ void many(const int (&kk)[N], const int32_t (&key)[N]) {
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int u = 0; u < N; u++) {
+            uint32_t v = 0;
+            if (key[u] >= 0) {
+                const uint32_t c = eng->count(key[u]);
+                v = c > 1 ? c - 1 : 0;
+            }
+            const int k = key[u] >= 0 ? kk[u] : -1;
+            const unsigned valid = __ballot_sync(0xffffffffu, k >= 0);
+            if (!valid) continue;
+            const int kl = __shfl_sync(0xffffffffu, k, __ffs(valid) - 1);
+            if (__all_sync(0xffffffffu, k < 0 || k == kl)) {
+                const uint32_t sum = __reduce_add_sync(0xffffffffu, v);
+                if (lane == 0 && sum) atomicAdd(&sacc[kl], (unsigned long long)sum);
+            } else if (v) {
+                atomicAdd(&sacc[k], (unsigned long long)v);
+            }
+        }
+    }
 };
 
 struct CountOppHook {

@@ -47,6 +47,26 @@ __device__ __forceinline__ uint32_t hash_key(int32_t k) {
     return (uint32_t)k * 2654435761u;
 }
 
+// Visits of one walk step (key < 0: no wedge). A visitor with a many<N>()
+// member gets the whole step with all 32 lanes (for warp-level aggregation);
+// others get one call per key.
+template <int N, class V>
+__device__ __forceinline__ auto visit_many_impl(V &v, const int (&kk)[N], const int32_t (&key)[N],
+                                                int) -> decltype(v.template many<N>(kk, key), void()) {
+    v.template many<N>(kk, key);
+}
+template <int N, class V>
+__device__ __forceinline__ void visit_many_impl(V &v, const int (&kk)[N], const int32_t (&key)[N],
+                                                long) {
+#pragma unroll
+    for (int u = 0; u < N; u++)
+        if (key[u] >= 0) v(kk[u], key[u]);
+}
+template <int N, class V>
+__device__ __forceinline__ void visit_many(V &v, const int (&kk)[N], const int32_t (&key)[N]) {
+    visit_many_impl<N>(v, kk, key, 0);
+}
+
 // ------------------------------------------------------------------
 // Warp-private table
 // ------------------------------------------------------------------
@@ -533,7 +553,8 @@ __device__ int64_t cta_walk(const Mids &M, int64_t q0, int64_t q1, const int32_t
 #pragma unroll
             for (int u = 0; u < WALK_UNROLL; u++) {
                 const int32_t base = (gb + u) << 5;
-                kk[u] = -1;
+                kk[u] = 0;
+                key[u] = -1;
                 if (BALANCED ? gb + u < g_hi : base < total) {
                     const int32_t j = base + lane;
                     if (base >= p0 && base + 32 <= p1) {
@@ -561,9 +582,7 @@ __device__ int64_t cta_walk(const Mids &M, int64_t q0, int64_t q1, const int32_t
                     }
                 }
             }
-#pragma unroll
-            for (int u = 0; u < WALK_UNROLL; u++)
-                if (kk[u] >= 0) visit(kk[u], key[u]);
+            visit_many<WALK_UNROLL>(visit, kk, key);
         }
         walked += total;
         __syncthreads();
