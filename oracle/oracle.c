@@ -334,71 +334,88 @@ done:
 }
 
 /* ------------------------------------------------------------------ */
-/* Monotone radix heap on 64-bit keys with lazy deletion               */
-/* A key may be pushed only if it is >= the last key popped; bucket b   */
-/* holds keys whose highest bit differing from `last` is bit b-1.       */
+/* Monotone radix heap over vertices keyed by their current support    */
+/* Keys never drop below the last key popped (the clamp of Algorithm   */
+/* 2 guarantees it). Bucket b holds vertices whose key's highest bit    */
+/* differing from `last` is bit b-1 (bucket 0: key == last). A vertex   */
+/* is filed again only when its bucket changes, and where[v] names the  */
+/* bucket of its live entry, so older entries are recognised as stale  */
+/* and a vertex has at most 66 entries over the whole peel.             */
 /* ------------------------------------------------------------------ */
 
 typedef struct {
-    uint64_t key;
-    int32_t v;
-} rh_item;
-
-typedef struct {
-    rh_item *b[65];
+    int32_t *b[65];
     size_t n[65], cap[65];
     uint64_t last;
-    size_t size;
+    const uint64_t *key; /* current key of every vertex (its support) */
+    int8_t *where;       /* bucket of the vertex's live entry, -1: none */
 } radix_heap;
 
 static int rh_bucket(uint64_t key, uint64_t last) {
     return key == last ? 0 : 64 - __builtin_clzll(key ^ last);
 }
 
-static int rh_append(radix_heap *h, int b, uint64_t key, int32_t v) {
+static int rh_append(radix_heap *h, int b, int32_t v) {
     if (h->n[b] == h->cap[b]) {
         size_t nc = h->cap[b] ? 2 * h->cap[b] : 16;
-        rh_item *p = (rh_item *)realloc(h->b[b], nc * sizeof(rh_item));
+        int32_t *p = (int32_t *)realloc(h->b[b], nc * sizeof(int32_t));
         if (!p) return ORC_ENOMEM;
         h->b[b] = p;
         h->cap[b] = nc;
     }
-    h->b[b][h->n[b]].key = key;
-    h->b[b][h->n[b]].v = v;
-    h->n[b]++;
+    h->b[b][h->n[b]++] = v;
     return ORC_OK;
 }
 
-static int rh_push(radix_heap *h, uint64_t key, int32_t v) {
-    if (key < h->last) return ORC_EINVAL; /* monotonicity violated */
-    h->size++;
-    return rh_append(h, rh_bucket(key, h->last), key, v);
+/* Files v under its current key (after it was set or lowered). */
+static int rh_put(radix_heap *h, int32_t v) {
+    if (h->key[v] < h->last) return ORC_EINVAL; /* monotonicity violated */
+    int b = rh_bucket(h->key[v], h->last);
+    if (h->where[v] == b) return ORC_OK; /* its live entry is in the right bucket */
+    h->where[v] = (int8_t)b;
+    return rh_append(h, b, v);
 }
 
-/* Pops one item with the minimum key; returns 0 if the heap is empty. */
-static int rh_pop(radix_heap *h, uint64_t *key, int32_t *v) {
-    if (h->size == 0) return 0;
-    if (h->n[0] == 0) {
+/* Pops a vertex with the minimum key into *v; returns 1, 0 if no vertex is
+ * filed, or minus an ORC_ code on failure. */
+static int rh_pop(radix_heap *h, int32_t *v) {
+    for (;;) {
+        while (h->n[0] > 0) {
+            int32_t u = h->b[0][--h->n[0]];
+            if (h->where[u] == 0) {
+                h->where[u] = -1;
+                *v = u;
+                return 1;
+            }
+        }
         int b = 1;
-        while (h->n[b] == 0) b++;
-        uint64_t mn = UINT64_MAX;
-        for (size_t i = 0; i < h->n[b]; i++)
-            if (h->b[b][i].key < mn) mn = h->b[b][i].key;
-        h->last = mn;
+        while (b < 65 && h->n[b] == 0) b++;
+        if (b == 65) return 0;
+        /* the smallest key among the live entries of bucket b is the new
+         * `last`; they all move to lower buckets */
+        int32_t *items = h->b[b];
         size_t cnt = h->n[b];
-        rh_item *items = h->b[b];
         h->b[b] = NULL;
         h->n[b] = 0;
         h->cap[b] = 0;
+        uint64_t mn = UINT64_MAX;
         for (size_t i = 0; i < cnt; i++)
-            rh_append(h, rh_bucket(items[i].key, mn), items[i].key, items[i].v);
+            if (h->where[items[i]] == b && h->key[items[i]] < mn) mn = h->key[items[i]];
+        if (mn != UINT64_MAX) {
+            h->last = mn;
+            for (size_t i = 0; i < cnt; i++) {
+                int32_t u = items[i];
+                if (h->where[u] != b) continue; /* stale entry */
+                h->where[u] = -1;
+                int rc = rh_put(h, u);
+                if (rc) {
+                    free(items);
+                    return -rc;
+                }
+            }
+        }
         free(items);
     }
-    h->n[0]--;
-    *key = h->b[0][h->n[0]].key;
-    *v = h->b[0][h->n[0]].v;
-    h->size--;
-    return 1;
 }
 
 static void rh_free(radix_heap *h) {
@@ -459,11 +476,14 @@ static int bup_impl(int32_t nu, int32_t nv, int64_t m, const int32_t *eu, const 
     uint8_t *peeled = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
     uint32_t *c = (uint32_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(uint32_t));
     int32_t *touched = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int8_t *where = (int8_t *)malloc((size_t)(n > 0 ? n : 1));
     radix_heap h;
     memset(&h, 0, sizeof(h));
+    h.key = sup;
+    h.where = where;
     oracle_bup_stats s;
     memset(&s, 0, sizeof(s));
-    if (!sup || !peeled || !c || !touched) {
+    if (!sup || !peeled || !c || !touched || !where) {
         rc = ORC_ENOMEM;
         goto done;
     }
@@ -475,12 +495,16 @@ static int bup_impl(int32_t nu, int32_t nv, int64_t m, const int32_t *eu, const 
     if (rc) goto done;
     double t1 = now_s();
     s.seconds_count = t1 - t0;
+    memset(where, -1, (size_t)n);
     for (int64_t x = 0; x < n; x++)
-        if ((rc = rh_push(&h, sup[x], (int32_t)x))) goto done;
-    uint64_t key;
+        if ((rc = rh_put(&h, (int32_t)x))) goto done;
     int32_t x;
-    while (rh_pop(&h, &key, &x)) {
-        if (peeled[x] || key != sup[x]) continue; /* stale heap entry */
+    int got;
+    while ((got = rh_pop(&h, &x)) != 0) {
+        if (got < 0) {
+            rc = -got;
+            goto done;
+        }
         if (max_wedges && s.wedges >= max_wedges) break;
         uint64_t theta = sup[x]; /* minimum support: x's tip number */
         tip[x] = theta;
@@ -506,7 +530,7 @@ static int bup_impl(int32_t nu, int32_t nv, int64_t m, const int32_t *eu, const 
             uint64_t nv2 = (sup[xp] >= b && sup[xp] - b >= theta) ? sup[xp] - b : theta;
             if (nv2 != sup[xp]) {
                 sup[xp] = nv2;
-                if ((rc = rh_push(&h, nv2, xp))) goto done;
+                if ((rc = rh_put(&h, xp))) goto done;
             }
         }
     }
@@ -515,6 +539,7 @@ static int bup_impl(int32_t nu, int32_t nv, int64_t m, const int32_t *eu, const 
 done:
     if (st) *st = s;
     rh_free(&h);
+    free(where);
     free(sup);
     free(peeled);
     free(c);
