@@ -39,6 +39,7 @@ constexpr unsigned long long WIDE_BIT = 1ull << 63;
 // heavy subsets: automatic threshold and levels enqueued per alive check
 constexpr unsigned long long HEAVY_MIN_W = 1ull << 23;
 constexpr unsigned long long HEAVY_SHARE = 8;
+constexpr int32_t HEAVY_MIN_N = 32768;
 constexpr int HEAVY_LEVELS_PER_CHECK = 4;
 
 __global__ void k_sub_keys(const int32_t *__restrict__ sub, int32_t n, uint64_t *__restrict__ key,
@@ -812,8 +813,24 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
                                                tot / (unsigned long long)std::min(grid_all, P) *
                                                    HEAVY_SHARE);
         }
-        while (nheavy < P && hw[hq[nheavy]] >= thr && hms[hq[nheavy] + 1] > hms[hq[nheavy]])
-            nheavy++;
+        // heavy: many wedges, or (automatic choice) so many vertices that
+        // one CTA would rescan a long alive list at every level
+        std::vector<int32_t> front, back;
+        for (int k = 0; k < P; k++) {
+            const int32_t i = hq[k];
+            const int32_t ni = hms[i + 1] - hms[i];
+            const bool big = hw[i] >= thr || (D.fd_heavy_w == 0 && ni >= HEAVY_MIN_N);
+            (big && ni > 0 ? front : back).push_back(i);
+        }
+        nheavy = (int)front.size();
+        if (nheavy > 0) {
+            // heavy subsets first, then the rest in LPT order
+            int pos = 0;
+            for (int32_t i : front) hq[pos++] = i;
+            for (int32_t i : back) hq[pos++] = i;
+            RC_CUDA(cudaMemcpyAsync(queue.get(), hq.data(), sizeof(int32_t) * P,
+                                    cudaMemcpyHostToDevice, s));
+        }
     }
     DevBuf<unsigned long long> fsup(n, s);
     DevBuf<uint8_t> alive(n, s);
