@@ -98,7 +98,7 @@ typedef struct {
      * of Sec. 3.2.1, sum of L(L-1) over the runs L of G_i) is at least this
      * are peeled by all CTAs level by level instead of by one CTA of the
      * persistent queue. 0 = automatic (8 times the mean share of one CTA and
-     * at least 2^23, or at least 32,768 vertices), -1 = never. Speed only. */
+     * at least 2^23), -1 = never. Speed only. */
     int64_t fd_heavy_w;
 } receipt_options;
 

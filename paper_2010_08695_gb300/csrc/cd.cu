@@ -32,23 +32,12 @@ namespace receipt {
 
 namespace {
 
-constexpr int NBUCKET = 1920;
+constexpr int NBUCKET = LOG_BUCKETS;
 constexpr int NTIER = 5;  // warp, hybrid, global, sliced, dense window
-constexpr double DGM_FRAC = 0.125;  // stale share of live entries that triggers a compaction  // 32 exact buckets + 58 octaves x 32 mantissa steps
+constexpr double DGM_FRAC = 0.125;  // stale share of live entries that triggers a compaction
 
-__device__ __forceinline__ int bucket_of(unsigned long long k) {
-    if (k < 32) return (int)k;
-    int e = 63 - __clzll((long long)k);
-    int mant = (int)((k >> (e - 5)) & 31);
-    return 32 + (e - 5) * 32 + mant;
-}
-
-__device__ __forceinline__ unsigned long long bucket_top(int b) {
-    if (b < 32) return (unsigned long long)b;
-    int e = (b - 32) / 32 + 5, mant = (b - 32) % 32;
-    if (e == 63 && mant == 31) return ~0ull;
-    return ((unsigned long long)(33 + mant) << (e - 5)) - 1ull;
-}
+__device__ __forceinline__ int bucket_of(unsigned long long k) { return log_bucket_of(k); }
+__device__ __forceinline__ unsigned long long bucket_top(int b) { return log_bucket_top(b); }
 
 struct CdDev {
     unsigned long long hi;

@@ -47,6 +47,23 @@ __device__ __forceinline__ uint32_t hash_key(int32_t k) {
     return (uint32_t)k * 2654435761u;
 }
 
+// Log-spaced buckets of 64-bit values: 32 exact values, then 32 mantissa
+// steps per power of two (58 octaves); a bucket's top is within 3% of its
+// bottom.
+constexpr int LOG_BUCKETS = 1920;
+__device__ __forceinline__ int log_bucket_of(unsigned long long k) {
+    if (k < 32) return (int)k;
+    const int e = 63 - __clzll((long long)k);
+    const int mant = (int)((k >> (e - 5)) & 31);
+    return 32 + (e - 5) * 32 + mant;
+}
+__device__ __forceinline__ unsigned long long log_bucket_top(int b) {
+    if (b < 32) return (unsigned long long)b;
+    const int e = (b - 32) / 32 + 5, mant = (b - 32) % 32;
+    if (e == 63 && mant == 31) return ~0ull;
+    return ((unsigned long long)(33 + mant) << (e - 5)) - 1ull;
+}
+
 // Visits of one walk step (key < 0: no wedge). A visitor with a many<N>()
 // member gets the whole step with all 32 lanes (for warp-level aggregation);
 // others get one call per key.

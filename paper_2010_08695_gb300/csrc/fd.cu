@@ -39,7 +39,6 @@ constexpr unsigned long long WIDE_BIT = 1ull << 63;
 // heavy subsets: automatic threshold and levels enqueued per alive check
 constexpr unsigned long long HEAVY_MIN_W = 1ull << 23;
 constexpr unsigned long long HEAVY_SHARE = 8;
-constexpr int32_t HEAVY_MIN_N = 32768;
 constexpr int HEAVY_LEVELS_PER_CHECK = 4;
 
 __global__ void k_sub_keys(const int32_t *__restrict__ sub, int32_t n, uint64_t *__restrict__ key,
@@ -186,8 +185,10 @@ struct FdArgs {
     const unsigned long long *init;
     unsigned long long *fsup;  // by member position
     uint8_t *alive;            // by member position
-    int32_t *alist;            // by member position: alive members (two buffers)
+    int32_t *alist;            // by member position: alive members outside the window (two buffers)
     int32_t *alist2;
+    int32_t *clist;            // by member position: members inside the window (two buffers)
+    int32_t *clist2;
     int32_t *plist;            // by member position
     int32_t *blist;            // by member position: peeled vertices with big updates
     unsigned long long *tip;   // output, original ids
@@ -206,19 +207,27 @@ struct FdMids {
     }
 };
 
-// Support decrement of an alive member; the decremented value also lowers
-// *mn, so that after a level's updates *mn holds the minimum support of the
-// survivors (together with the minimum of the untouched ones, taken when the
-// level's peeled vertices are selected).
+// Support decrement of an alive member. Values below the window bound T
+// also lower *mn, so that after a level's updates *mn holds the minimum
+// support of the window's survivors (together with the minimum of the
+// untouched ones, taken when the level's peeled vertices are selected); a
+// member whose support falls below T here joins the window's list.
 struct FdEmit {
     unsigned long long *fsup;  // subset base
     const uint8_t *alive;      // subset base
     unsigned long long *mn;    // next level's minimum (shared or global)
+    unsigned long long T;      // window bound (~0: everything is inside)
+    int32_t *cand;             // window list (null without a window)
+    int *n_cand;
     __device__ __forceinline__ void operator()(int32_t k, uint32_t c) {
         if (alive[k]) {
             const unsigned long long d = choose2(c);
             const unsigned long long old = atomicAdd(&fsup[k], 0ull - d);
-            atomicMin(mn, old - d);
+            const unsigned long long nv = old - d;
+            if (nv < T) {
+                atomicMin(mn, nv);
+                if (old >= T) cand[atomicAdd(n_cand, 1)] = k;
+            }
         }
     }
 };
@@ -261,6 +270,9 @@ struct FdSliceEmit {
 // edges form one virtual list of middle vertices; the thread that stages a
 // middle vertex records its anchor slot for the visits.
 constexpr int FD_BATCH = 32;
+// window of the level loop: about max(MIN, min(MAX, alive / 32)) members
+constexpr int FD_WINDOW_MIN = 512;
+constexpr int FD_WINDOW_MAX = 4096;
 
 struct FdBatchMids {
     const int64_t *fd_beg;
@@ -382,8 +394,10 @@ __device__ __forceinline__ unsigned char *fd_bind_smem(unsigned char *smem, int 
 
 __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_t, s_dn, s_np, s_nk, s_nbig, s_nwide;
-    __shared__ unsigned long long s_mn;  // minimum support of the alive members
+    __shared__ int s_t, s_dn, s_np, s_nk, s_nbig, s_nwide, s_nf, s_pick, s_peel;
+    __shared__ unsigned long long s_mn;  // minimum support of the window's members
+    __shared__ unsigned long long s_T;   // window bound
+    __shared__ int32_t s_scan[33];
     __shared__ int64_t s_bq0[FD_BATCH];
     __shared__ int32_t s_bpre[FD_BATCH + 1], s_bself[FD_BATCH];
     __shared__ uint8_t s_slot[FD_THREADS];
@@ -414,32 +428,100 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
         const unsigned long long levels0 = levels;
         unsigned long long *fsup = a.fsup + mb;
         uint8_t *alive = a.alive + mb;
-        int32_t *alist = a.alist + mb;
-        int32_t *alist_next = a.alist2 + mb;
+        // members outside the window (far) and inside it (cand), each
+        // double-buffered for compaction
+        int32_t *flist = a.alist + mb;
+        int32_t *flist_next = a.alist2 + mb;
+        int32_t *clist = a.clist + mb;
+        int32_t *clist_next = a.clist2 + mb;
         int32_t *plist = a.plist + mb;
         int32_t *blist = a.blist + mb;
         const int32_t *mem = a.members + mb;
         unsigned long long *wr = a.wr + mb;
-        unsigned long long mn0 = ~0ull;
         for (int r = threadIdx.x; r < ni; r += blockDim.x) {
-            const unsigned long long v = a.init[mem[r]];
-            fsup[r] = v;
+            fsup[r] = a.init[mem[r]];
             alive[r] = 1;
-            alist[r] = r;
-            mn0 = v < mn0 ? v : mn0;
+            flist[r] = r;
         }
-        mn0 = warp_min(mn0);
-        if (threadIdx.x == 0) s_mn = ~0ull;
-        __syncthreads();
-        if (lane == 0) atomicMin(&s_mn, mn0);
-        int32_t nalive = ni;
+        int32_t nalive = ni, nfar = ni, ncand = 0;
         unsigned long long level = 0;
         // anchors aggregated per pass of the batched update
         const int32_t bk = ni <= FD_KEYS / 2 ? min(FD_BATCH, FD_KEYS / ni) : 1;
         __syncthreads();
         while (nalive > 0) {
-            // mu from the minimum left by the previous level (or the start)
+            if (ncand == 0) {
+                // Window refill: the smallest supports among the far members,
+                // about `target` of them, become the window [.., T); a level
+                // then scans the window only, and members whose support
+                // falls below T during updates join it.
+                uint32_t *hist = (uint32_t *)H.tl;  // idle between passes
+                for (int b = threadIdx.x; b < LOG_BUCKETS; b += blockDim.x) hist[b] = 0;
+                if (threadIdx.x == 0) {
+                    s_pick = LOG_BUCKETS - 1;
+                    s_nf = 0;
+                    s_nk = 0;
+                    s_mn = ~0ull;
+                }
+                __syncthreads();
+                for (int j = threadIdx.x; j < nfar; j += blockDim.x) {
+                    const int32_t r = flist[j];
+                    if (alive[r]) atomicAdd(&hist[log_bucket_of(fsup[r])], 1u);
+                }
+                __syncthreads();
+                {
+                    constexpr int PER = (LOG_BUCKETS + FD_THREADS - 1) / FD_THREADS;
+                    const int target = max(FD_WINDOW_MIN, min(FD_WINDOW_MAX, nalive / 32));
+                    int32_t c[PER], sum = 0;
+#pragma unroll
+                    for (int e = 0; e < PER; e++) {
+                        const int b = threadIdx.x * PER + e;
+                        c[e] = b < LOG_BUCKETS ? (int32_t)hist[b] : 0;
+                        sum += c[e];
+                    }
+                    int32_t run = block_exclusive_scan<int32_t>(sum, s_scan, nullptr);
+#pragma unroll
+                    for (int e = 0; e < PER; e++) {
+                        run += c[e];
+                        if (run >= target && c[e] > 0) atomicMin(&s_pick, threadIdx.x * PER + e);
+                    }
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    const unsigned long long top = log_bucket_top(s_pick);
+                    s_T = top == ~0ull ? ~0ull : top + 1ull;
+                }
+                __syncthreads();
+                const unsigned long long T = s_T;
+                for (int base = 0; base < nfar; base += blockDim.x) {
+                    const int j = base + threadIdx.x;
+                    int32_t r = -1;
+                    unsigned long long v = ~0ull;
+                    if (j < nfar) {
+                        r = flist[j];
+                        if (alive[r])
+                            v = fsup[r];
+                        else
+                            r = -1;
+                    }
+                    const bool in = r >= 0 && v < T;
+                    warp_append(in, r, &s_nk, clist);
+                    warp_append(r >= 0 && !in, r, &s_nf, flist_next);
+                    const unsigned long long kv = warp_min(in ? v : ~0ull);
+                    if (lane == 0 && kv != ~0ull) atomicMin(&s_mn, kv);
+                }
+                __syncthreads();
+                ncand = s_nk;
+                nfar = s_nf;
+                {
+                    int32_t *tmp = flist;
+                    flist = flist_next;
+                    flist_next = tmp;
+                }
+                if (ncand == 0) break;  // cannot happen while members are alive
+            }
+            // mu from the minimum left by the previous level (or the refill)
             const unsigned long long mu = s_mn > level ? s_mn : level;
+            const unsigned long long T = s_T;
             level = mu;
             levels++;
             __syncthreads();
@@ -448,17 +530,19 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
                 s_nk = 0;
                 s_nbig = 0;
                 s_nwide = 0;
+                s_peel = 0;
                 s_mn = ~0ull;
             }
             __syncthreads();
-            // peel every remaining vertex with support <= mu; the rest go to
-            // the other alive buffer (ballot compaction, order irrelevant)
-            for (int base = 0; base < nalive; base += blockDim.x) {
+            // peel every window member with support <= mu; the rest go to
+            // the other window buffer (ballot compaction, order irrelevant)
+            int peeled = 0;
+            for (int base = 0; base < ncand; base += blockDim.x) {
                 const int j = base + threadIdx.x;
                 int32_t r = -1;
                 unsigned long long v = 0;
-                if (j < nalive) {
-                    r = alist[j];
+                if (j < ncand) {
+                    r = clist[j];
                     v = fsup[r];
                 }
                 const bool keep = r >= 0 && v > mu;
@@ -468,6 +552,7 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
                     alive[r] = 0;
                     a.tip[a.new2old[mem[r]]] = mu;
                     w = wr[r];
+                    peeled++;
                 }
                 // updates: small walks -> one warp each; bigger ones -> the
                 // batched pass; degree >= 65535 (32-bit counts) or a subset
@@ -475,7 +560,7 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
                 const bool upd = peel && v > 0;
                 const bool small = upd && w <= (unsigned long long)WARP_MAX_W;
                 const bool single = upd && !small && ((w & WIDE_BIT) || bk == 1);
-                warp_append(keep, r, &s_nk, alist_next);
+                warp_append(keep, r, &s_nk, clist_next);
                 warp_append(small, r, &s_np, plist);
                 warp_append(upd && !small && !single, r, &s_nbig, blist);
                 if (single) blist[ni - 1 - atomicAdd(&s_nwide, 1)] = r;
@@ -483,17 +568,19 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
                 const unsigned long long kv = warp_min(keep ? v : ~0ull);
                 if (lane == 0 && kv != ~0ull) atomicMin(&s_mn, kv);
             }
+            peeled = warp_sum(peeled);
+            if (lane == 0 && peeled) atomicAdd(&s_peel, peeled);
             __syncthreads();
-            nalive = s_nk;
+            nalive -= s_peel;
             {
-                int32_t *tmp = alist;
-                alist = alist_next;
-                alist_next = tmp;
+                int32_t *tmp = clist;
+                clist = clist_next;
+                clist_next = tmp;
             }
             const int np = s_np;
             // updates of the peeled vertices inside G_i. Phase A: one warp per
             // peeled vertex whose update walks at most WARP_MAX_W wedges.
-            FdEmit emit{fsup, alive, &s_mn};
+            FdEmit emit{fsup, alive, &s_mn, T, clist, &s_nk};
             for (int pi = warp; pi < np; pi += nwarps) {
                 const int32_t r = plist[pi];
                 const int32_t x = mem[r];
@@ -549,6 +636,8 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
                 if (threadIdx.x == 0) wedges += (unsigned long long)walked;
             }
             __syncthreads();
+            // window survivors plus the members that fell below T
+            ncand = s_nk;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -668,7 +757,7 @@ __global__ void __launch_bounds__(256) k_fdh_warp(FdhArgs a) {
     WarpHash WH{skey[w], sval[w]};
     WH.clear(lane);
     __syncwarp();
-    FdEmit emit{a.fsup, a.alive, &a.st->mn_next};
+    FdEmit emit{a.fsup, a.alive, &a.st->mn_next, ~0ull, nullptr, nullptr};
     FdMids M{a.fd_beg, a.fd_len};
     const int32_t nw = a.st->nw;
     unsigned long long wedges = 0;
@@ -691,7 +780,7 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fdh_cta(FdhArgs a) {
     fd_bind_smem(smem, &s_dn, H, ch);
     H.clear_all();
     __syncthreads();
-    FdEmit emit{a.fsup, a.alive, &a.st->mn_next};
+    FdEmit emit{a.fsup, a.alive, &a.st->mn_next, ~0ull, nullptr, nullptr};
     const int32_t nb = a.st->nb;
     unsigned long long wedges = 0;
     for (int32_t i = blockIdx.x; i < nb; i += gridDim.x) {
@@ -813,14 +902,11 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
                                                tot / (unsigned long long)std::min(grid_all, P) *
                                                    HEAVY_SHARE);
         }
-        // heavy: many wedges, or (automatic choice) so many vertices that
-        // one CTA would rescan a long alive list at every level
         std::vector<int32_t> front, back;
         for (int k = 0; k < P; k++) {
             const int32_t i = hq[k];
             const int32_t ni = hms[i + 1] - hms[i];
-            const bool big = hw[i] >= thr || (D.fd_heavy_w == 0 && ni >= HEAVY_MIN_N);
-            (big && ni > 0 ? front : back).push_back(i);
+            (hw[i] >= thr && ni > 0 ? front : back).push_back(i);
         }
         nheavy = (int)front.size();
         if (nheavy > 0) {
@@ -834,7 +920,8 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
     }
     DevBuf<unsigned long long> fsup(n, s);
     DevBuf<uint8_t> alive(n, s);
-    DevBuf<int32_t> alist(n, s), alist2(n, s), plist(n, s), blist(n, s), qhead(1, s);
+    DevBuf<int32_t> alist(n, s), alist2(n, s), clist(n, s), clist2(n, s), plist(n, s), blist(n, s),
+        qhead(1, s);
     DevBuf<unsigned long long> stats(2, s), sub_ns(P, s), sub_lv(P, s);
     qhead.zero();
     stats.zero();
@@ -908,6 +995,7 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
         FdArgs a{queue.get(),   P,           qhead.get(),     mstart.get(), members.get(),
                  S.off,         fd_beg.get(), fd_len.get(),   fd_adj.get(), S.new2old,
                  D.init,        fsup.get(),  alive.get(),     alist.get(),  alist2.get(),
+                 clist.get(),   clist2.get(),
                  plist.get(),   blist.get(),
                  (unsigned long long *)d_tip, stats.get(),    sub_ns.get(), sub_lv.get(),
                  wr.get()};
