@@ -214,7 +214,8 @@ def run_ours(args):
 
     def step(timing):
         g = R.Graph(eu_d, ev_d, nu, nv, stream=stream)
-        g.tip_decompose(side, timing=timing, out=tip, stream=stream)
+        g.tip_decompose(side, timing=timing, out=tip, stream=stream,
+                        round_graphs=args.round_graphs)
         st = g.stats()
         if args.trace:
             last_trace[:] = g.trace()
@@ -304,6 +305,7 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "nu": nu, "nv": nv, "m": int(len(eu)), "side": "U",
+                       "round_graphs": bool(args.round_graphs),
                        "P": tuned.get("P", 150), "tuning": tuned or "defaults",
                        "wedges_bup": wedges, "parallelism": "replicas" if world > 1
                        else "single", "l2": "flushed between steps (256 MiB write)"},
@@ -370,12 +372,13 @@ def run_batch(args):
     for (eu, ev), s in zip(graphs, specs):
         dv = np.bincount(ev, minlength=s.nv).astype(np.int64)
         wedges += int((dv * (dv - 1)).sum())
-    outs = R.receipt_decompose_batch(built, sides)  # warm-up
+    outs = R.receipt_decompose_batch(built, sides, round_graphs=args.round_graphs)  # warm-up
     torch.cuda.synchronize()
     tb = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        outs = R.receipt_decompose_batch(built, sides, outs=outs, timing=True)
+        outs = R.receipt_decompose_batch(built, sides, outs=outs, timing=True,
+                                         round_graphs=args.round_graphs)
         torch.cuda.synchronize()
         tb.append(time.perf_counter() - t0)
     batch_stats = built[0].stats()
@@ -495,6 +498,8 @@ def main():
                     help="single: the 10M-edge graph (default); batch: 4,096 graphs packed "
                          "vs one per launch; serve: the serving stream prefix")
     ap.add_argument("--batch-graphs", type=int, default=4096)
+    ap.add_argument("--round-graphs", action="store_true",
+                    help="run each coarse-grained round as one CUDA graph launch")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-calib", type=int, default=40)
     ap.add_argument("--serve-slots", type=int, default=4)

@@ -100,6 +100,11 @@ typedef struct {
      * persistent queue. 0 = automatic (8 times the mean share of one CTA and
      * at least 2^23), -1 = never. Speed only. */
     int64_t fd_heavy_w;
+    /* Non-zero: every synchronisation round of Algorithm 3 runs as one
+     * launch of a CUDA graph captured once per call (the round's kernels,
+     * the copy of its counters to the host and the advance to the next
+     * activeSet) instead of separate launches. Speed only. */
+    int32_t round_graphs;
 } receipt_options;
 
 /* Counters of the last call on a graph (Sec. 5: wedges and rounds). */

@@ -47,7 +47,7 @@ class Options(ctypes.Structure):
                 ("h_p_eff", ctypes.POINTER(ctypes.c_int32)), ("timing", ctypes.c_int32),
                 ("warp_max_w", ctypes.c_int32), ("slice_min_w", ctypes.c_int32),
                 ("no_dgm", ctypes.c_int32), ("dgm_frac_1024", ctypes.c_int32),
-                ("fd_heavy_w", ctypes.c_int64)]
+                ("fd_heavy_w", ctypes.c_int64), ("round_graphs", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -172,11 +172,13 @@ def _dptr(t):
 
 
 def _options(P=150, bounds=None, subset=None, bounds_out=None, p_eff=None, timing=False,
-             warp_max_w=0, slice_min_w=0, dgm=True, dgm_frac_1024=0, fd_heavy_w=0):
+             warp_max_w=0, slice_min_w=0, dgm=True, dgm_frac_1024=0, fd_heavy_w=0,
+             round_graphs=False):
     o = Options()
     load().receipt_options_default(ctypes.byref(o))
     o.P = int(P)
     o.fd_heavy_w = int(fd_heavy_w)
+    o.round_graphs = 1 if round_graphs else 0
     o.dgm_frac_1024 = int(dgm_frac_1024)
     o.no_dgm = 0 if dgm else 1
     o.warp_max_w = int(warp_max_w)
@@ -317,7 +319,7 @@ class Graph:
 
     def tip_decompose(self, side: int = SIDE_U, P: int = 0, bounds=None, subsets=False,
                       timing=False, out=None, stream=None, warp_max_w=0, slice_min_w=0, dgm=True,
-                      dgm_frac_1024=0, fd_heavy_w=0):
+                      dgm_frac_1024=0, fd_heavy_w=0, round_graphs=False):
         """Tip numbers of ``side`` (Algorithms 3 and 4). P = 0 takes the tuned
         value for this graph's shape class, else 150. With ``subsets=True``
         returns ``(tips, subset_of_vertex, range_bounds)``."""
@@ -339,7 +341,7 @@ class Graph:
             if subsets else None
         peff = ctypes.c_int32(0)
         o, keep = _options(P, bounds, sub, bout, peff, timing, warp_max_w, slice_min_w, dgm,
-                           dgm_frac_1024, fd_heavy_w)
+                           dgm_frac_1024, fd_heavy_w, round_graphs)
         receipt_tip_decompose(self._h, side, tip, o, stream)
         if subsets:
             return tip, sub, bout[: peff.value + 1]
@@ -355,7 +357,8 @@ class Graph:
         return receipt_get_subsets(self._h)
 
 
-def receipt_decompose_batch(graphs, sides, outs=None, P: int = 150, stream=None, timing=False):
+def receipt_decompose_batch(graphs, sides, outs=None, P: int = 150, stream=None, timing=False,
+                            round_graphs=False):
     """Tip numbers of many graphs in one pass (disjoint-union packing)."""
     import torch
     n = len(graphs)
@@ -365,7 +368,7 @@ def receipt_decompose_batch(graphs, sides, outs=None, P: int = 150, stream=None,
         outs = [torch.empty(g.nu if s == 0 else g.nv, dtype=torch.int64, device=g.device)
                 for g, s in zip(graphs, sides)]
     ps = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
-    o, keep = _options(P, timing=timing)
+    o, keep = _options(P, timing=timing, round_graphs=round_graphs)
     _check(load().receipt_decompose_batch(hs, ss, n, ps, ctypes.byref(o), _stream_handle(stream)))
     return outs
 

@@ -17,6 +17,8 @@ static thread_local std::string g_last_error;
 static std::atomic<uint64_t> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void uncount_launches(uint64_t n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
 
 void set_last_error(const std::string &msg) { g_last_error = msg; }
 
@@ -83,6 +85,25 @@ void *pinned_scratch(size_t bytes) {
         g_pinned.n = want;
     }
     return g_pinned.p;
+}
+
+namespace {
+struct CaptureTLS {
+    cudaStream_t s[64] = {};
+    ~CaptureTLS() {
+        for (auto &x : s)
+            if (x) cudaStreamDestroy(x);
+    }
+};
+thread_local CaptureTLS g_capture;
+}  // namespace
+
+cudaStream_t capture_stream() {
+    int d = 0;
+    RC_CUDA(cudaGetDevice(&d));
+    if (d < 0 || d >= 64) fail(RECEIPT_ERR_INTERNAL, "device index out of range");
+    if (!g_capture.s[d]) RC_CUDA(cudaStreamCreateWithFlags(&g_capture.s[d], cudaStreamNonBlocking));
+    return g_capture.s[d];
 }
 
 int num_sms() { return dev_info().sms; }

@@ -24,6 +24,7 @@
 // remaining vertex, so its update is skipped.
 #include <algorithm>
 #include <cstddef>
+#include <vector>
 
 #include "engine.cuh"
 #include "internal.cuh"
@@ -46,7 +47,7 @@ struct CdDev {
     unsigned long long work64;  // item counter of the sliced tier
     unsigned long long peeled_edges;  // adjacency entries of assigned vertices (for DGM)
     int32_t n_remaining;
-    int32_t pad;
+    int32_t range;  // 0-based index of the range being peeled
     unsigned long long wrem_prev;
     double tgt_prev;
     unsigned long long wedges;
@@ -197,12 +198,13 @@ __global__ void k_cd_frontier(int32_t n, const int32_t *__restrict__ sub,
 
 // Assigns the activeSet to subset `range` and splits the vertices that have
 // updates to make into the three engine tiers.
-__global__ void k_cd_prepare(const int32_t *__restrict__ F, CdDev *st, int32_t range,
+__global__ void k_cd_prepare(const int32_t *__restrict__ F, CdDev *st,
                              int32_t *__restrict__ sub, const unsigned long long *__restrict__ sup,
                              const unsigned long long *__restrict__ wfull,
                              const int64_t *__restrict__ off_s, int32_t *__restrict__ Lw,
                              int32_t *__restrict__ Lb, int32_t warp_max_w) {
     const int32_t nF = st->nF;
+    const int32_t range = st->range;
     unsigned long long wsum = 0, esum = 0;
     for (int32_t base = blockIdx.x * blockDim.x; base < nF; base += gridDim.x * blockDim.x) {
         int32_t i = base + threadIdx.x;
@@ -748,8 +750,9 @@ __global__ void k_cd_advance(CdDev *st) {
     st->work64 = 0;
 }
 
-__global__ void k_cd_new_range(CdDev *st) {
+__global__ void k_cd_new_range(CdDev *st, int32_t range) {
     if (threadIdx.x == 0) {
+        st->range = range;
         st->nF = st->nNext = 0;
         st->nLw = st->nLc = st->nLg = st->nLo = st->nLs = st->nLb = st->nLd = 0;
         for (int i = 0; i < 6; i++) st->work[i] = 0;
@@ -881,9 +884,100 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
     const int nb = std::min(ceil_div(n, 512), sms * 4);
     int range = 0;
     const int nranges = opt.n_bounds > 0 ? std::min(opt.n_bounds, P) : P;
-    int32_t *cur = F.get(), *nxt = Nx.get();
+    // activeSet buffers of the two round parities; the range index comes
+    // from device memory, so a round's launches do not depend on the range
+    int32_t *abuf[2] = {F.get(), Nx.get()};
+    cudaGraph_t round_graph[2] = {};
+    cudaGraphExec_t round_exec[2] = {};
+    struct GraphGuard {
+        cudaGraph_t *g;
+        cudaGraphExec_t *e;
+        ~GraphGuard() {
+            for (int k = 0; k < 2; k++) {
+                if (e[k]) cudaGraphExecDestroy(e[k]);
+                if (g[k]) cudaGraphDestroy(g[k]);
+            }
+        }
+    } gg{round_graph, round_exec};
+    uint64_t round_kernels = 0;
+    // The round body on stream `q`: split the activeSet `cur` into tiers,
+    // route, apply the updates of every tier (their crossings form the next
+    // activeSet in `nxt`), copy the round's header to the host, advance.
+    auto round_body = [&](cudaStream_t q, int32_t *cur, int32_t *nxt, bool external_events) {
+        auto mark = [&](int i) {
+            if (!D.timing) return;
+            if (external_events)
+                RC_CUDA(cudaEventRecordWithFlags(ev[i], q, cudaEventRecordExternal));
+            else
+                RC_CUDA(cudaEventRecord(ev[i], q));
+        };
+        k_cd_prepare<<<nb, 512, 0, q>>>(cur, st.get(), D.sub, D.sup, D.wfull, S.off, Lw.get(),
+                                        Lb.get(), warp_max_w);
+        RC_LAUNCH();
+        k_cd_route<<<sms * 8, 256, 0, q>>>(st.get(), Lb.get(), S.off, S.adj, O.off, len_w.get(),
+                                           adj_w.get(), D.wfull, cta_ok ? cta_keys : 0, slice_min_w,
+                                           SW, Lc.get(), Lc_k.get(), Lc_w.get(), Ld.get(),
+                                           Ld_k.get(), Lg.get(), Ls.get(), Ls_lo.get(),
+                                           Ls_hi.get());
+        RC_LAUNCH();
+        PeelArgs a{S.off,     S.adj,      O.off,       len_w.get(), adj_w.get(), D.sup, D.sub,
+                   st.get(),  Lw.get(),   Lc.get(),    Lg.get(),    Ls.get(), nxt,
+                   Lc_k.get(), Lc_w.get(), Ls_lo.get(), Ls_hi.get(), Ld.get(), Ld_k.get(),
+                   table ? soff.get() : nullptr, C, SW, n};
+        mark(0);
+        k_cd_update_warp<<<sms * 8, 256, 0, q>>>(a);
+        RC_LAUNCH();
+        mark(1);
+        k_cd_update_dense<<<dblocks, DENSE_THREADS, DenseSlice::bytes() + CHUNK_BYTES, q>>>(a);
+        RC_LAUNCH();
+        mark(2);
+        if (cta_ok) {
+            k_cd_update_cta<<<sms, CTA_THREADS, smem_cta, q>>>(a, head_cap, bm_cap);
+            RC_LAUNCH();
+        }
+        mark(3);
+        if (hubs) {
+            k_cd_update_global<<<gblocks, CTA_THREADS, smem_glob, q>>>(a, gcnt.get(), gtouch.get(),
+                                                                      n);
+            RC_LAUNCH();
+        }
+        mark(4);
+        k_cd_update_slice<<<sblocks, SLICE_THREADS, smem_slice, q>>>(a, n);
+        RC_LAUNCH();
+        mark(5);
+        RC_CUDA(cudaMemcpyAsync(hst, st.get(), hdr, cudaMemcpyDeviceToHost, q));
+        k_cd_advance<<<1, 1, 0, q>>>(st.get());
+        RC_LAUNCH();
+    };
+    // With round_graphs the body is captured once per activeSet parity (on a
+    // private stream: the caller's may be the legacy default stream, which
+    // cannot capture) and each round is one graph launch.
+    const bool graphs = opt.round_graphs != 0;
+    if (graphs) {
+        cudaStream_t cs = capture_stream();
+        for (int par = 0; par < 2; par++) {
+            RC_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            round_body(cs, abuf[par], abuf[par ^ 1], true);
+            RC_CUDA(cudaStreamEndCapture(cs, &round_graph[par]));
+            RC_CUDA(cudaGraphInstantiate(&round_exec[par], round_graph[par], 0));
+            // the captured launches are counted per graph launch instead
+            size_t nn = 0;
+            RC_CUDA(cudaGraphGetNodes(round_graph[par], nullptr, &nn));
+            std::vector<cudaGraphNode_t> nodes(nn);
+            RC_CUDA(cudaGraphGetNodes(round_graph[par], nodes.data(), &nn));
+            round_kernels = 0;
+            for (size_t k = 0; k < nn; k++) {
+                cudaGraphNodeType t;
+                RC_CUDA(cudaGraphNodeGetType(nodes[k], &t));
+                if (t == cudaGraphNodeTypeKernel) round_kernels++;
+            }
+            uncount_launches(round_kernels);
+        }
+    }
+    int parity = 0;
+    int32_t *cur = abuf[0];
     for (range = 0; range < nranges; range++) {
-        k_cd_new_range<<<1, 256, 0, s>>>(st.get());
+        k_cd_new_range<<<1, 256, 0, s>>>(st.get(), range);
         RC_LAUNCH();
         k_cd_hist<<<nb, 512, 0, s>>>(n, D.sub, D.sup, D.wfull, S.off, D.init, st.get());
         RC_LAUNCH();
@@ -899,51 +993,19 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
         RC_CUDA(cudaStreamSynchronize(s));
         const uint64_t hi = hpin[0];
         if (hi32[2] == 0) break;  // nothing remains
+        cur = abuf[parity];
         k_cd_frontier<<<nb, 512, 0, s>>>(n, D.sub, D.sup, st.get(), cur);
         RC_LAUNCH();
         for (;;) {
-            k_cd_prepare<<<nb, 512, 0, s>>>(cur, st.get(), range, D.sub, D.sup, D.wfull, S.off,
-                                            Lw.get(), Lb.get(), warp_max_w);
-            RC_LAUNCH();
-            k_cd_route<<<sms * 8, 256, 0, s>>>(st.get(), Lb.get(), S.off, S.adj, O.off, len_w.get(),
-                                               adj_w.get(), D.wfull, cta_ok ? cta_keys : 0, slice_min_w, SW,
-                                               Lc.get(), Lc_k.get(), Lc_w.get(), Ld.get(),
-                                               Ld_k.get(), Lg.get(), Ls.get(), Ls_lo.get(),
-                                               Ls_hi.get());
-            RC_LAUNCH();
-            PeelArgs a{S.off,     S.adj,      O.off,       len_w.get(), adj_w.get(), D.sup, D.sub,
-                       st.get(),  Lw.get(),   Lc.get(),    Lg.get(),    Ls.get(), nxt,
-                       Lc_k.get(), Lc_w.get(), Ls_lo.get(), Ls_hi.get(), Ld.get(), Ld_k.get(),
-                       table ? soff.get() : nullptr, C, SW, n};
-            if (D.timing) RC_CUDA(cudaEventRecord(ev[0], s));
-            k_cd_update_warp<<<sms * 8, 256, 0, s>>>(a);
-            RC_LAUNCH();
-            if (D.timing) RC_CUDA(cudaEventRecord(ev[1], s));
-            k_cd_update_dense<<<dblocks, DENSE_THREADS, DenseSlice::bytes() + CHUNK_BYTES, s>>>(a);
-            RC_LAUNCH();
-            if (D.timing) RC_CUDA(cudaEventRecord(ev[2], s));
-            if (cta_ok) {
-                k_cd_update_cta<<<sms, CTA_THREADS, smem_cta, s>>>(a, head_cap, bm_cap);
-                RC_LAUNCH();
-                D.tier_launches[1]++;
+            if (graphs) {
+                RC_CUDA(cudaGraphLaunch(round_exec[parity], s));
+                count_launches(round_kernels);
+            } else {
+                round_body(s, abuf[parity], abuf[parity ^ 1], false);
             }
-            if (D.timing) RC_CUDA(cudaEventRecord(ev[3], s));
-            if (hubs) {
-                k_cd_update_global<<<gblocks, CTA_THREADS, smem_glob, s>>>(a, gcnt.get(),
-                                                                          gtouch.get(), n);
-                RC_LAUNCH();
-            }
-            if (D.timing) RC_CUDA(cudaEventRecord(ev[4], s));
-            k_cd_update_slice<<<sblocks, SLICE_THREADS, smem_slice, s>>>(a, n);
-            RC_LAUNCH();
-            if (D.timing) RC_CUDA(cudaEventRecord(ev[5], s));
-            D.tier_launches[4]++;
-            D.tier_launches[0]++;
-            D.tier_launches[2]++;
-            D.tier_launches[3]++;
-            D.rounds++;
-            RC_CUDA(cudaMemcpyAsync(hst, st.get(), hdr, cudaMemcpyDeviceToHost, s));
             RC_CUDA(cudaStreamSynchronize(s));
+            for (int t = 0; t < NTIER; t++) D.tier_launches[t]++;
+            D.rounds++;
             receipt_round rr{};
             rr.range = range;
             rr.frontier = hst->nF;
@@ -966,9 +1028,7 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
             }
             D.trace.push_back(rr);
             if (hst->nNext == 0) break;
-            k_cd_advance<<<1, 1, 0, s>>>(st.get());
-            RC_LAUNCH();
-            std::swap(cur, nxt);
+            parity ^= 1;  // the next round reads the activeSet this one wrote
         }
         D.bounds.push_back(hi);
         // dynamic graph maintenance: once the vertices assigned since the last

@@ -32,6 +32,9 @@ void count_launch();
     } while (0)
 
 int num_sms();
+// Kernel launch counter of the library (graph launches add their kernels).
+void count_launches(uint64_t n);
+void uncount_launches(uint64_t n);
 int max_smem_optin();
 // Sets a kernel's MaxDynamicSharedMemorySize to all the shared memory the
 // device allows it (opt-in limit minus its static shared memory), once per

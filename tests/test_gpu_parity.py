@@ -185,6 +185,9 @@ def test_any_P_and_injected_ranges_give_same_tips(R):
         assert (lo <= t).all() and (t < hi).all(), f"P={P}"
     t = R.as_u64(g.tip_decompose(0, dgm=False))  # without dynamic graph maintenance
     assert np.array_equal(t, want)
+    t = R.as_u64(g.tip_decompose(0, round_graphs=True))  # rounds as CUDA graph launches
+    assert np.array_equal(t, want)
+    assert g.stats()["rounds_cd"] >= 1
     rng = np.random.default_rng(3)
     top = int(want.max()) + 2
     for trial in range(4):
@@ -247,6 +250,9 @@ def test_batch_equals_alone(R):
     outs = R.receipt_decompose_batch(graphs, sides)
     for i, (o, w) in enumerate(zip(outs, wants)):
         assert np.array_equal(R.as_u64(o), w), f"graph {i}"
+    outs = R.receipt_decompose_batch(graphs, sides, round_graphs=True)
+    for i, (o, w) in enumerate(zip(outs, wants)):
+        assert np.array_equal(R.as_u64(o), w), f"graph {i} (graph rounds)"
         alone = R.as_u64(graphs[i].tip_decompose(sides[i]))
         assert np.array_equal(alone, w)
 
