@@ -358,14 +358,46 @@ __device__ int64_t fd_update_cta(FdEngine &H, Chunk &ch, const int64_t *__restri
     const bool wide = q1 - q0 >= 65535;
     const int32_t SWk = wide ? FD_WORDS : FD_KEYS;
     const int32_t C = (ni + SWk - 1) / SWk;
+    // only the slices that meet the anchor's rank window (first and last
+    // entries of its runs, which are sorted by rank)
+    int32_t j0 = 0, j1 = C - 1;
+    if (C > 1) {
+        int32_t *win = ch.tmp;  // scan scratch, idle here
+        if (threadIdx.x == 0) {
+            win[0] = INT32_MAX;
+            win[1] = -1;
+        }
+        __syncthreads();
+        int32_t lo = INT32_MAX, hi = -1;
+        for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+            const int32_t l = fd_len[q];
+            if (l > 0) {
+                const int64_t b = fd_beg[q];
+                lo = min(lo, fd_adj[b]);
+                hi = max(hi, fd_adj[b + l - 1]);
+            }
+        }
+        lo = warp_min(lo);
+        hi = -warp_min(-hi);
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&win[0], lo);
+            atomicMax(&win[1], hi);
+        }
+        __syncthreads();
+        const int32_t wlo = win[0], whi = win[1];
+        __syncthreads();  // win is rewritten by the next call
+        if (whi < 0) return 0;  // no runs
+        j0 = wlo / SWk;
+        j1 = whi / SWk;
+    }
     int64_t wedges = 0;
-    for (int32_t j = 0; j < C; j++) {
+    for (int32_t j = j0; j <= j1; j++) {
         const int32_t base = j * SWk;
         const int32_t w = (int32_t)imin64(SWk, (int64_t)ni - base);
         H.set_width(w, wide);
         FdSliceVisit v{&H, base, r};
         int64_t walked;
-        if (C == 1) {
+        if (j0 == j1) {
             FdMids M{fd_beg, fd_len};
             walked = cta_walk(M, q0, q1, fd_adj, ch, v);
         } else {
