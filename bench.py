@@ -316,8 +316,8 @@ def run_ours(args):
             "phase_ms": {"count": st["ms_count"], "cd": st["ms_cd"], "fd": st["ms_fd"],
                          "peel_tiers": st["ms_peel"]},
             "rounds_cd": st["rounds_cd"], "levels_fd": st["levels_fd"], "subsets": st["p_eff"],
-            "fd_slowest_subset": {"ms": st["ms_fd_max_subset"], "n": st["fd_max_subset_n"],
-                                  "levels": st["fd_max_subset_levels"]},
+            "fd_slowest_task": {"ms": st["ms_fd_max_subset"], "n": st["fd_max_subset_n"],
+                                "levels": st["fd_max_subset_levels"]},
             "fd_heavy": {"subsets": st["fd_heavy_subsets"], "ms": st["ms_fd_heavy"],
                          "levels": st["levels_fd_heavy"]},
             "peel_tier_wedges": st["peel_wedges"], "peel_tier_anchors": st["peel_anchors"],
@@ -412,9 +412,10 @@ def run_batch(args):
             "rounds_cd": batch_stats["rounds_cd"], "subsets": batch_stats["p_eff"],
             "phase_ms": {"count": batch_stats["ms_count"], "cd": batch_stats["ms_cd"],
                          "fd": batch_stats["ms_fd"], "peel_tiers": batch_stats["ms_peel"]},
-            "fd_slowest_subset": {"ms": batch_stats["ms_fd_max_subset"],
-                                  "n": batch_stats["fd_max_subset_n"],
-                                  "levels": batch_stats["fd_max_subset_levels"]},
+            "fd_slowest_task": {"ms": batch_stats["ms_fd_max_subset"],
+                                "n": batch_stats["fd_max_subset_n"],
+                                "levels": batch_stats["fd_max_subset_levels"]},
+            "fd_tasks": batch_stats["fd_tasks"],
             "walked_wedges": {"count": batch_stats["wedges_count"], "cd": batch_stats["wedges_cd"],
                               "fd": batch_stats["wedges_fd"]},
             "batch_equals_alone": same, "oracle_sample_ok": oracle_ok,

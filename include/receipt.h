@@ -130,15 +130,20 @@ typedef struct {
     uint64_t peel_anchors[5];
     int64_t peel_launches[5];
     float ms_peel[5];
-    /* Slowest subset of the fine-grained step: device time, size, levels. */
+    /* Slowest task of the fine-grained step peeled by one CTA: device time,
+     * size, levels. */
     float ms_fd_max_subset;
     int32_t fd_max_subset_n;
     int64_t fd_max_subset_levels;
-    /* Subsets peeled by all CTAs level by level (see fd_heavy_w), their
+    /* Tasks peeled by all CTAs level by level (see fd_heavy_w), their
      * summed device time (globaltimer) and levels. */
     int32_t fd_heavy_subsets;
     float ms_fd_heavy;
     int64_t levels_fd_heavy;
+    /* Tasks of the fine-grained step: one per subset, or, for a batch, one
+     * per packed graph's part of a subset (small parts merged). */
+    int32_t fd_tasks;
+    int32_t reserved2;
 } receipt_stats;
 
 /* One synchronisation round of the coarse-grained step (Algorithm 3). */

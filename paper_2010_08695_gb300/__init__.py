@@ -62,7 +62,8 @@ class Stats(ctypes.Structure):
                 ("ms_peel", ctypes.c_float * 5), ("ms_fd_max_subset", ctypes.c_float),
                 ("fd_max_subset_n", ctypes.c_int32), ("fd_max_subset_levels", ctypes.c_int64),
                 ("fd_heavy_subsets", ctypes.c_int32), ("ms_fd_heavy", ctypes.c_float),
-                ("levels_fd_heavy", ctypes.c_int64)]
+                ("levels_fd_heavy", ctypes.c_int64), ("fd_tasks", ctypes.c_int32),
+                ("reserved2", ctypes.c_int32)]
 
 
 class Round(ctypes.Structure):

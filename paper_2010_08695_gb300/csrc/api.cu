@@ -200,6 +200,7 @@ void tip_decompose_impl(receipt_graph *g, int side, uint64_t *d_tip, const recei
     D.timing = opt.timing != 0;
     D.max_deg_s = g->max_deg[side];
     D.fd_heavy_w = opt.fd_heavy_w;
+    D.parts = (side == 0 && !g->parts.empty()) ? &g->parts : nullptr;
     DevBuf<unsigned long long> cu(g->nu, s), cv(g->nv, s), init(n, s), wfull(n, s);
     DevBuf<int32_t> sub(n, s);
     DevBuf<unsigned long long> wbup(1, s);
@@ -247,6 +248,7 @@ void tip_decompose_impl(receipt_graph *g, int side, uint64_t *d_tip, const recei
     st.fd_heavy_subsets = D.fd_heavy;
     st.ms_fd_heavy = D.fd_heavy_ms;
     st.levels_fd_heavy = D.fd_heavy_levels;
+    st.fd_tasks = D.fd_tasks;
     g->subsets = std::move(D.subsets);
     for (int t = 0; t < 5; t++) {
         st.peel_wedges[t] = D.tier_wedges[t];
@@ -370,6 +372,7 @@ void decompose_batch_impl(receipt_graph *const *gs, const receipt_side *sides, i
     U.device = dev;
     U.max_deg[0] = maxdeg[0];
     U.max_deg[1] = maxdeg[1];
+    U.parts = abase;
     DevBuf<int64_t> offA(NA + 1, s), offB(NB + 1, s);
     DevBuf<int32_t> adjA(M, s), adjB(M, s), n2oA(NA, s), n2oB(NB, s), belA(NA, s), belB(NB, s);
     DevBuf<PackSrc> dsrc(n, s);

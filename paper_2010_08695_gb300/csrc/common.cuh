@@ -115,6 +115,7 @@ struct receipt_graph {
     receipt_stats stats{};
     std::vector<receipt_round> trace;  // rounds of the last decomposition
     std::vector<receipt_subset> subsets;  // fine-grained subsets of the last decomposition
+    std::vector<int64_t> parts;  // batch union: first side-0 vertex of every packed graph
     void *owned = nullptr;  // device allocation holding every array above
 };
 

@@ -40,6 +40,8 @@ constexpr unsigned long long WIDE_BIT = 1ull << 63;
 constexpr unsigned long long HEAVY_MIN_W = 1ull << 23;
 constexpr unsigned long long HEAVY_SHARE = 8;
 constexpr int HEAVY_LEVELS_PER_CHECK = 4;
+// parts of one subset are merged into tasks of at least this many members
+constexpr int32_t TASK_MIN = 2048;
 
 __global__ void k_sub_keys(const int32_t *__restrict__ sub, int32_t n, uint64_t *__restrict__ key,
                            uint32_t *__restrict__ val, int32_t *__restrict__ cnt) {
@@ -157,25 +159,60 @@ __global__ void k_fd_walk_sizes(const int64_t *__restrict__ off_s, int32_t n,
     wr[mstart[sub[x]] + rank[x]] = W | (q1 - q0 >= 65535 ? WIDE_BIT : 0ull);
 }
 
-// LPT order: rank of subset i = number of subsets with larger work (ties by id).
-__global__ void k_lpt(const unsigned long long *__restrict__ wsub, const int32_t *__restrict__ mstart,
-                      int32_t P, int32_t *__restrict__ queue) {
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P) return;
-    unsigned long long ki = wsub[i] + (unsigned long long)(mstart[i + 1] - mstart[i]);
-    int32_t r = 0;
-    for (int32_t j = 0; j < P; j++) {
-        unsigned long long kj = wsub[j] + (unsigned long long)(mstart[j + 1] - mstart[j]);
-        if (kj > ki || (kj == ki && j < i)) r++;
+// Task boundaries: the first member of every subset and, when the side is a
+// union of packed graphs (parts = first vertex of each graph), every member
+// whose graph differs from the previous member's.
+__global__ void k_task_flags(const int32_t *__restrict__ members, int32_t n,
+                             const int32_t *__restrict__ sub, const int32_t *__restrict__ mstart,
+                             const int64_t *__restrict__ parts, int ng,
+                             uint32_t *__restrict__ flag) {
+    const int32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int32_t x = members[p];
+    uint32_t f = p == mstart[sub[x]] ? 1u : 0u;
+    if (!f && ng > 0) {
+        auto graph_of = [&](int64_t v) {
+            int lo = 0, hi = ng - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (parts[mid] <= v)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            return lo;
+        };
+        f = graph_of(x) != graph_of(members[p - 1]) ? 1u : 0u;
     }
-    queue[r] = i;
+    flag[p] = f;
+}
+
+__global__ void k_flag_positions(const uint32_t *__restrict__ flag, const uint32_t *__restrict__ pos,
+                                 int32_t n, int32_t *__restrict__ out) {
+    const int32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n && flag[p]) out[pos[p]] = p;
+}
+
+__global__ void k_walk_plain(const unsigned long long *__restrict__ wr, int32_t n,
+                             int64_t *__restrict__ out) {
+    const int32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) out[p] = (int64_t)(wr[p] & ~WIDE_BIT);
+}
+
+__global__ void k_task_weights(const int32_t *__restrict__ tstart, const int32_t *__restrict__ tlen,
+                               const int64_t *__restrict__ cw, int32_t T,
+                               unsigned long long *__restrict__ w) {
+    const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < T) w[t] = (unsigned long long)(cw[tstart[t] + tlen[t]] - cw[tstart[t]]);
 }
 
 struct FdArgs {
-    const int32_t *queue;
-    int32_t P;
+    const int32_t *queue;      // task ids, LPT order
+    int32_t P;                 // tasks
     int32_t *qhead;
-    const int32_t *mstart;
+    const int32_t *tstart;     // per task: first member position
+    const int32_t *tlen;       // per task: members
+    const int32_t *tkb;        // per task: rank of its first member inside its subset
     const int32_t *members;
     const int64_t *off_s;
     const int64_t *fd_beg;
@@ -193,8 +230,8 @@ struct FdArgs {
     int32_t *blist;            // by member position: peeled vertices with big updates
     unsigned long long *tip;   // output, original ids
     unsigned long long *stats; // [0] wedges, [1] levels
-    unsigned long long *sub_ns;     // per subset: nanoseconds spent
-    unsigned long long *sub_levels; // per subset: peeling levels
+    unsigned long long *sub_ns;     // per task: nanoseconds spent
+    unsigned long long *sub_levels; // per task: peeling levels
     unsigned long long *wr;    // by member position: walk size inside G_i (WIDE_BIT: degree >= 65535)
 };
 
@@ -250,10 +287,12 @@ struct FdSliceMids {
     }
 };
 
+// Keys of a run are ranks inside the subset; a task covering the subset's
+// ranks [kb, kb + ni) sees them shifted by kb.
 struct FdSliceVisit {
     FdEngine *eng;
-    int32_t base;  // first rank of the slice
-    int32_t self;  // the anchor's own rank
+    int32_t base;  // first rank of the slice (subset ranks)
+    int32_t self;  // the anchor's own rank (subset ranks)
     __device__ __forceinline__ void operator()(int, int32_t key) {
         if (key != self) eng->add(key - base);
     }
@@ -300,10 +339,12 @@ struct FdBatchMids {
 struct FdBatchVisit {
     FdEngine *eng;
     const uint8_t *slot;
-    const int32_t *bself;  // rank of each anchor
+    const int32_t *bself;  // rank of each anchor (task ranks)
     int32_t ni;
+    int32_t kb;            // first subset rank of the task
     __device__ __forceinline__ void operator()(int k, int32_t key) {
         const int a = slot[k];
+        key -= kb;
         if (key != bself[a]) eng->add(a * ni + key);
     }
 };
@@ -318,7 +359,8 @@ struct FdBatchEmit {
 // walk has at most WARP_MAX_W wedges: one warp with its private table.
 __device__ __forceinline__ void fd_update_warp(WarpHash &WH, const FdMids &M,
                                                const int32_t *__restrict__ fd_adj, int64_t q0,
-                                               int64_t q1, int32_t r, int lane, FdEmit &emit) {
+                                               int64_t q1, int32_t r, int32_t kb, int lane,
+                                               FdEmit &emit) {
     for (int64_t qb = q0; qb < q1; qb += 32) {
         const int64_t q = qb + lane;
         int64_t beg = 0;
@@ -329,7 +371,7 @@ __device__ __forceinline__ void fd_update_warp(WarpHash &WH, const FdMids &M,
             const int64_t b = __shfl_sync(0xffffffffu, beg, t2);
             const int32_t l = __shfl_sync(0xffffffffu, len, t2);
             for (int p = lane; p < l; p += 32) {
-                const int32_t k = fd_adj[b + p];
+                const int32_t k = fd_adj[b + p] - kb;
                 if (k != r) WH.add(k);
             }
         }
@@ -354,7 +396,7 @@ __device__ __forceinline__ void fd_update_warp(WarpHash &WH, const FdMids &M,
 __device__ int64_t fd_update_cta(FdEngine &H, Chunk &ch, const int64_t *__restrict__ fd_beg,
                                  const int32_t *__restrict__ fd_len,
                                  const int32_t *__restrict__ fd_adj, int64_t q0, int64_t q1,
-                                 int32_t r, int32_t ni, FdEmit &emit) {
+                                 int32_t r, int32_t ni, int32_t kb, FdEmit &emit) {
     const bool wide = q1 - q0 >= 65535;
     const int32_t SWk = wide ? FD_WORDS : FD_KEYS;
     const int32_t C = (ni + SWk - 1) / SWk;
@@ -387,21 +429,21 @@ __device__ int64_t fd_update_cta(FdEngine &H, Chunk &ch, const int64_t *__restri
         const int32_t wlo = win[0], whi = win[1];
         __syncthreads();  // win is rewritten by the next call
         if (whi < 0) return 0;  // no runs
-        j0 = wlo / SWk;
-        j1 = whi / SWk;
+        j0 = (wlo - kb) / SWk;
+        j1 = (whi - kb) / SWk;
     }
     int64_t wedges = 0;
     for (int32_t j = j0; j <= j1; j++) {
         const int32_t base = j * SWk;
         const int32_t w = (int32_t)imin64(SWk, (int64_t)ni - base);
         H.set_width(w, wide);
-        FdSliceVisit v{&H, base, r};
+        FdSliceVisit v{&H, base + kb, r + kb};
         int64_t walked;
         if (j0 == j1) {
             FdMids M{fd_beg, fd_len};
             walked = cta_walk(M, q0, q1, fd_adj, ch, v);
         } else {
-            FdSliceMids MS{fd_beg, fd_len, fd_adj, base, base + w};
+            FdSliceMids MS{fd_beg, fd_len, fd_adj, base + kb, base + kb + w};
             walked = cta_walk(MS, q0, q1, fd_adj, ch, v);
         }
         wedges += walked;
@@ -452,8 +494,9 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
         const int t = s_t;
         if (t >= a.P) break;
         const int32_t i = a.queue[t];
-        const int32_t mb = a.mstart[i];
-        const int32_t ni = a.mstart[i + 1] - mb;
+        const int32_t mb = a.tstart[i];
+        const int32_t ni = a.tlen[i];
+        const int32_t kb = a.tkb[i];
         if (ni == 0) continue;
         unsigned long long t_start = 0;
         if (threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
@@ -616,7 +659,7 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
             for (int pi = warp; pi < np; pi += nwarps) {
                 const int32_t r = plist[pi];
                 const int32_t x = mem[r];
-                fd_update_warp(WH, M, a.fd_adj, a.off_s[x], a.off_s[x + 1], r, lane, emit);
+                fd_update_warp(WH, M, a.fd_adj, a.off_s[x], a.off_s[x + 1], r, kb, lane, emit);
                 if (lane == 0) wedges += wr[r];
             }
             __syncthreads();
@@ -647,7 +690,7 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
                 __syncthreads();
                 H.set_width(nb * ni, false);
                 FdBatchMids BM{a.fd_beg, a.fd_len, s_bq0, s_bpre, nb, s_slot};
-                FdBatchVisit v{&H, s_slot, s_bself, ni};
+                FdBatchVisit v{&H, s_slot, s_bself, ni, kb};
                 const int64_t walked = cta_walk(BM, 0, s_bpre[nb], a.fd_adj, ch, v);
                 if (threadIdx.x == 0) wedges += (unsigned long long)walked;
                 if (walked > 0) {
@@ -664,7 +707,7 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
                 const int32_t r = blist[ni - 1 - pi];
                 const int32_t x = mem[r];
                 const int64_t walked = fd_update_cta(H, ch, a.fd_beg, a.fd_len, a.fd_adj,
-                                                     a.off_s[x], a.off_s[x + 1], r, ni, emit);
+                                                     a.off_s[x], a.off_s[x + 1], r, ni, kb, emit);
                 if (threadIdx.x == 0) wedges += (unsigned long long)walked;
             }
             __syncthreads();
@@ -703,8 +746,9 @@ struct FdhDev {
 };
 
 struct FdhArgs {
-    const int32_t *mem;  // subset members (local ids), rank order
+    const int32_t *mem;  // task members (local ids), rank order
     int32_t ni;
+    int32_t kb;          // rank of the task's first member inside its subset
     const int64_t *off_s;
     const int64_t *fd_beg;
     const int32_t *fd_len;
@@ -798,7 +842,7 @@ __global__ void __launch_bounds__(256) k_fdh_warp(FdhArgs a) {
     for (int64_t i = gw; i < nw; i += ngw) {
         const int32_t r = a.Lw[i];
         const int32_t x = a.mem[r];
-        fd_update_warp(WH, M, a.fd_adj, a.off_s[x], a.off_s[x + 1], r, lane, emit);
+        fd_update_warp(WH, M, a.fd_adj, a.off_s[x], a.off_s[x + 1], r, a.kb, lane, emit);
         wedges += a.wr[r];
     }
     if (lane == 0 && wedges) atomicAdd(&a.st->wedges, wedges);
@@ -819,7 +863,7 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fdh_cta(FdhArgs a) {
         const int32_t r = a.Lb[i];
         const int32_t x = a.mem[r];
         wedges += (unsigned long long)fd_update_cta(H, ch, a.fd_beg, a.fd_len, a.fd_adj, a.off_s[x],
-                                                    a.off_s[x + 1], r, a.ni, emit);
+                                                    a.off_s[x + 1], r, a.ni, a.kb, emit);
     }
     if (threadIdx.x == 0 && wedges) atomicAdd(&a.st->wedges, wedges);
 }
@@ -903,17 +947,84 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
     } else {
         wr.zero();
     }
-    DevBuf<int32_t> queue(P, s);
-    k_lpt<<<ceil_div(P, 256), 256, 0, s>>>(wsub.get(), mstart.get(), P, queue.get());
-    RC_LAUNCH();
-    // subset sizes, wedge counts and the LPT order, for the heavy-subset choice
-    std::vector<int32_t> hms(P + 1), hq(P);
+    // subset sizes and wedge counts
+    std::vector<int32_t> hms(P + 1);
     std::vector<unsigned long long> hw(P);
     RC_CUDA(cudaMemcpyAsync(hms.data(), mstart.get(), sizeof(int32_t) * (P + 1),
                             cudaMemcpyDeviceToHost, s));
-    RC_CUDA(cudaMemcpyAsync(hq.data(), queue.get(), sizeof(int32_t) * P, cudaMemcpyDeviceToHost, s));
     RC_CUDA(cudaMemcpyAsync(hw.data(), wsub.get(), 8 * P, cudaMemcpyDeviceToHost, s));
-    RC_CUDA(cudaStreamSynchronize(s));
+    // Tasks: a subset, or, in a batch's disjoint union, each packed graph's
+    // part of a subset (parts share no butterfly, so each is peeled on its
+    // own; consecutive small parts of one subset are merged up to TASK_MIN
+    // members). A task covers consecutive member positions, which are
+    // consecutive ranks of its subset.
+    std::vector<int32_t> tstart, tlen, tkb, tsub;
+    {
+        const int ng = D.parts ? (int)D.parts->size() - 1 : 0;
+        DevBuf<int64_t> dparts(ng > 0 ? ng + 1 : 1, s);
+        if (ng > 0)
+            RC_CUDA(cudaMemcpyAsync(dparts.get(), D.parts->data(), 8 * (ng + 1),
+                                    cudaMemcpyHostToDevice, s));
+        DevBuf<uint32_t> flag(n + 1, s), fpos(n + 1, s);
+        k_task_flags<<<ceil_div(n, 256), 256, 0, s>>>(members.get(), n, D.sub, mstart.get(),
+                                                      dparts.get(), ng, flag.get());
+        RC_LAUNCH();
+        RC_CUDA(cudaMemsetAsync(flag.get() + n, 0, 4, s));
+        scan_exclusive<uint32_t>(flag.get(), fpos.get(), n + 1, s);
+        uint32_t nseg = 0;
+        RC_CUDA(cudaMemcpyAsync(&nseg, fpos.get() + n, 4, cudaMemcpyDeviceToHost, s));
+        RC_CUDA(cudaStreamSynchronize(s));
+        DevBuf<int32_t> segs(nseg > 0 ? nseg : 1, s);
+        k_flag_positions<<<ceil_div(n, 256), 256, 0, s>>>(flag.get(), fpos.get(), n, segs.get());
+        RC_LAUNCH();
+        std::vector<int32_t> hseg(nseg);
+        if (nseg > 0)
+            RC_CUDA(cudaMemcpyAsync(hseg.data(), segs.get(), 4 * (size_t)nseg,
+                                    cudaMemcpyDeviceToHost, s));
+        RC_CUDA(cudaStreamSynchronize(s));
+        int sub_i = 0;
+        for (uint32_t k = 0; k < nseg; k++) {
+            const int32_t b = hseg[k];
+            while (sub_i + 1 <= P && hms[sub_i + 1] <= b) sub_i++;  // subset holding b
+            const bool new_sub = tsub.empty() || tsub.back() != sub_i;
+            if (new_sub || tlen.back() >= TASK_MIN) {
+                tstart.push_back(b);
+                tlen.push_back(0);
+                tkb.push_back(b - hms[sub_i]);
+                tsub.push_back(sub_i);
+            }
+            const int32_t e = k + 1 < nseg ? hseg[k + 1] : n;
+            tlen.back() += e - b;
+        }
+    }
+    const int T = (int)tstart.size();
+    // task weights: walk sizes summed over the task's members (LPT key)
+    std::vector<unsigned long long> tw(T);
+    DevBuf<int32_t> d_tstart(T > 0 ? T : 1, s), d_tlen(T > 0 ? T : 1, s), d_tkb(T > 0 ? T : 1, s);
+    if (T > 0) {
+        RC_CUDA(cudaMemcpyAsync(d_tstart.get(), tstart.data(), 4 * (size_t)T, cudaMemcpyHostToDevice, s));
+        RC_CUDA(cudaMemcpyAsync(d_tlen.get(), tlen.data(), 4 * (size_t)T, cudaMemcpyHostToDevice, s));
+        RC_CUDA(cudaMemcpyAsync(d_tkb.get(), tkb.data(), 4 * (size_t)T, cudaMemcpyHostToDevice, s));
+        DevBuf<int64_t> w64(n + 1, s), cw(n + 1, s);
+        DevBuf<unsigned long long> dtw(T, s);
+        k_walk_plain<<<ceil_div(n, 256), 256, 0, s>>>(wr.get(), n, w64.get());
+        RC_LAUNCH();
+        RC_CUDA(cudaMemsetAsync(w64.get() + n, 0, 8, s));
+        scan_exclusive<int64_t>(w64.get(), cw.get(), n + 1, s);
+        k_task_weights<<<ceil_div(T, 256), 256, 0, s>>>(d_tstart.get(), d_tlen.get(), cw.get(), T,
+                                                        dtw.get());
+        RC_LAUNCH();
+        RC_CUDA(cudaMemcpyAsync(tw.data(), dtw.get(), 8 * (size_t)T, cudaMemcpyDeviceToHost, s));
+        RC_CUDA(cudaStreamSynchronize(s));
+    }
+    // LPT order (ties by task id)
+    std::vector<int32_t> hq(T);
+    for (int k = 0; k < T; k++) hq[k] = k;
+    std::stable_sort(hq.begin(), hq.end(), [&](int32_t x, int32_t y) {
+        const unsigned long long kx = tw[x] + (unsigned long long)tlen[x];
+        const unsigned long long ky = tw[y] + (unsigned long long)tlen[y];
+        return kx > ky;
+    });
     const size_t warp_tables = (size_t)(FD_THREADS / 32) * WARP_SLOTS * 8 + 16;
     const size_t smem = FdEngine::bytes() + CHUNK_BYTES + warp_tables;
     allow_max_smem((const void *)k_fd_peel);
@@ -921,40 +1032,37 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
     RC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fd_peel, FD_THREADS, smem));
     const int sms = num_sms();
     const int grid_all = sms * std::max(occ, 1);
-    // Heavy subsets: a leading run of the LPT queue whose wedge counts exceed
-    // the threshold. Automatic: HEAVY_SHARE times the mean share of one CTA
-    // and at least HEAVY_MIN_W wedges.
+    // Heavy tasks (peeled first by all CTAs): task weight at least the
+    // threshold. Automatic: HEAVY_SHARE times the mean share of one CTA and
+    // at least HEAVY_MIN_W.
     int nheavy = 0;
-    if (D.fd_heavy_w >= 0) {
+    if (D.fd_heavy_w >= 0 && T > 0) {
         unsigned long long thr = (unsigned long long)D.fd_heavy_w;
         if (D.fd_heavy_w == 0) {
             unsigned long long tot = 0;
-            for (int i = 0; i < P; i++) tot += hw[i];
+            for (int k = 0; k < T; k++) tot += tw[k];
             thr = std::max<unsigned long long>(HEAVY_MIN_W,
-                                               tot / (unsigned long long)std::min(grid_all, P) *
+                                               tot / (unsigned long long)std::min(grid_all, T) *
                                                    HEAVY_SHARE);
         }
         std::vector<int32_t> front, back;
-        for (int k = 0; k < P; k++) {
-            const int32_t i = hq[k];
-            const int32_t ni = hms[i + 1] - hms[i];
-            (hw[i] >= thr && ni > 0 ? front : back).push_back(i);
+        for (int k = 0; k < T; k++) {
+            const int32_t t = hq[k];
+            (tw[t] >= thr && tlen[t] > 0 ? front : back).push_back(t);
         }
         nheavy = (int)front.size();
-        if (nheavy > 0) {
-            // heavy subsets first, then the rest in LPT order
-            int pos = 0;
-            for (int32_t i : front) hq[pos++] = i;
-            for (int32_t i : back) hq[pos++] = i;
-            RC_CUDA(cudaMemcpyAsync(queue.get(), hq.data(), sizeof(int32_t) * P,
-                                    cudaMemcpyHostToDevice, s));
-        }
+        int pos = 0;
+        for (int32_t t : front) hq[pos++] = t;
+        for (int32_t t : back) hq[pos++] = t;
     }
+    DevBuf<int32_t> queue(T > 0 ? T : 1, s);
+    if (T > 0)
+        RC_CUDA(cudaMemcpyAsync(queue.get(), hq.data(), 4 * (size_t)T, cudaMemcpyHostToDevice, s));
     DevBuf<unsigned long long> fsup(n, s);
     DevBuf<uint8_t> alive(n, s);
     DevBuf<int32_t> alist(n, s), alist2(n, s), clist(n, s), clist2(n, s), plist(n, s), blist(n, s),
         qhead(1, s);
-    DevBuf<unsigned long long> stats(2, s), sub_ns(P, s), sub_lv(P, s);
+    DevBuf<unsigned long long> stats(2, s), sub_ns(T > 0 ? T : 1, s), sub_lv(T > 0 ? T : 1, s);
     qhead.zero();
     stats.zero();
     sub_ns.zero();
@@ -982,11 +1090,12 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
         for (int i = 0; i < 2; i++) RC_CUDA(cudaEventCreateWithFlags(&evs[i], cudaEventDisableTiming));
         for (int h = 0; h < nheavy; h++) {
             const int32_t i = hq[h];
-            const int32_t mb = hms[i], ni = hms[i + 1] - hms[i];
-            FdhArgs ha{members.get() + mb, ni,           S.off,          fd_beg.get(),
-                       fd_len.get(),       fd_adj.get(), S.new2old,      D.init,
-                       fsup.get() + mb,    alive.get() + mb, wr.get() + mb, plist.get() + mb,
-                       blist.get() + mb,   (unsigned long long *)d_tip,  hst.get()};
+            const int32_t mb = tstart[i], ni = tlen[i];
+            FdhArgs ha{members.get() + mb, ni,           tkb[i],         S.off,
+                       fd_beg.get(),       fd_len.get(), fd_adj.get(),   S.new2old,
+                       D.init,             fsup.get() + mb, alive.get() + mb, wr.get() + mb,
+                       plist.get() + mb,   blist.get() + mb, (unsigned long long *)d_tip,
+                       hst.get()};
             const int gm = std::max(1, std::min(ceil_div(ni, 256), sms * 4));
             const int gi = std::max(1, std::min(ceil_div((int64_t)ni * 32, 256), sms * 16));
             k_fdh_reset<<<1, 1, 0, s>>>(hst.get(), ni);
@@ -1022,9 +1131,10 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
         }
         RC_CUDA(cudaMemcpyAsync(qhead.get(), &nheavy, 4, cudaMemcpyHostToDevice, s));
     }
-    if (nheavy < P) {
-        const int grid = std::max(1, std::min(grid_all, P - nheavy));
-        FdArgs a{queue.get(),   P,           qhead.get(),     mstart.get(), members.get(),
+    if (nheavy < T) {
+        const int grid = std::max(1, std::min(grid_all, T - nheavy));
+        FdArgs a{queue.get(),   T,           qhead.get(),     d_tstart.get(), d_tlen.get(),
+                 d_tkb.get(),   members.get(),
                  S.off,         fd_beg.get(), fd_len.get(),   fd_adj.get(), S.new2old,
                  D.init,        fsup.get(),  alive.get(),     alist.get(),  alist2.get(),
                  clist.get(),   clist2.get(),
@@ -1036,37 +1146,42 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
     }
     unsigned long long hs[2] = {0, 0};
     RC_CUDA(cudaMemcpyAsync(hs, stats.get(), sizeof(hs), cudaMemcpyDeviceToHost, s));
-    std::vector<unsigned long long> hns(P), hlv(P);
-    RC_CUDA(cudaMemcpyAsync(hns.data(), sub_ns.get(), 8 * P, cudaMemcpyDeviceToHost, s));
-    RC_CUDA(cudaMemcpyAsync(hlv.data(), sub_lv.get(), 8 * P, cudaMemcpyDeviceToHost, s));
+    std::vector<unsigned long long> hns(T), hlv(T);
+    if (T > 0) {
+        RC_CUDA(cudaMemcpyAsync(hns.data(), sub_ns.get(), 8 * (size_t)T, cudaMemcpyDeviceToHost, s));
+        RC_CUDA(cudaMemcpyAsync(hlv.data(), sub_lv.get(), 8 * (size_t)T, cudaMemcpyDeviceToHost, s));
+    }
     RC_CUDA(cudaStreamSynchronize(s));
     D.wedges_fd = hs[0];
     D.levels = (int64_t)hs[1];
-    std::vector<bool> heavy(P, false);
+    std::vector<bool> heavy(T, false);
     for (int h = 0; h < nheavy; h++) {
-        const int32_t i = hq[h];
-        heavy[i] = true;
-        hns[i] = hh[h].t1 - hh[h].t0;
-        hlv[i] = hh[h].levels;
+        const int32_t t = hq[h];
+        heavy[t] = true;
+        hns[t] = hh[h].t1 - hh[h].t0;
+        hlv[t] = hh[h].levels;
         D.wedges_fd += hh[h].wedges;
         D.levels += (int64_t)hh[h].levels;
     }
-    D.subsets.resize(P);
-    int worst = -1;
+    // per subset: its tasks' levels and device time summed
+    D.subsets.assign(P, receipt_subset{});
     for (int i = 0; i < P; i++) {
-        receipt_subset &r = D.subsets[i];
-        r.n = hms[i + 1] - hms[i];
-        r.heavy = heavy[i] ? 1 : 0;
-        r.levels = (int64_t)hlv[i];
-        r.wedges_est = hw[i];
-        r.ms = (float)(hns[i] * 1e-6);
-        r.pad = 0;
-        if (!heavy[i] && (worst < 0 || hns[i] > hns[worst])) worst = i;
+        D.subsets[i].n = hms[i + 1] - hms[i];
+        D.subsets[i].wedges_est = hw[i];
     }
-    // slowest subset peeled by one CTA
+    int worst = -1;
+    for (int t = 0; t < T; t++) {
+        receipt_subset &r = D.subsets[tsub[t]];
+        r.levels += (int64_t)hlv[t];
+        r.ms += (float)(hns[t] * 1e-6);
+        if (heavy[t]) r.heavy = 1;
+        if (!heavy[t] && (worst < 0 || hns[t] > hns[worst])) worst = t;
+    }
+    // slowest task peeled by one CTA
     D.fd_max_ms = worst >= 0 ? (float)(hns[worst] * 1e-6) : 0.f;
-    D.fd_max_n = worst >= 0 ? hms[worst + 1] - hms[worst] : 0;
+    D.fd_max_n = worst >= 0 ? tlen[worst] : 0;
     D.fd_max_levels = worst >= 0 ? (int64_t)hlv[worst] : 0;
+    D.fd_tasks = T;
 }
 
 }  // namespace receipt

@@ -68,6 +68,10 @@ struct Decomp {
     int32_t fd_heavy = 0;        // subsets peeled by all CTAs
     float fd_heavy_ms = 0;
     int64_t fd_heavy_levels = 0;
+    int32_t fd_tasks = 0;        // tasks of the fine-grained step
+    // first vertex of every packed graph when the side is a batch's
+    // disjoint union (null otherwise)
+    const std::vector<int64_t> *parts = nullptr;
     std::vector<receipt_subset> subsets;
 };
 
