@@ -41,7 +41,7 @@ constexpr unsigned long long HEAVY_MIN_W = 1ull << 23;
 constexpr unsigned long long HEAVY_SHARE = 8;
 constexpr int HEAVY_LEVELS_PER_CHECK = 4;
 // parts of one subset are merged into tasks of at least this many members
-constexpr int32_t TASK_MIN = 2048;
+constexpr int32_t TASK_MIN = 8192;
 
 __global__ void k_sub_keys(const int32_t *__restrict__ sub, int32_t n, uint64_t *__restrict__ key,
                            uint32_t *__restrict__ val, int32_t *__restrict__ cnt) {
