@@ -246,7 +246,8 @@ __global__ void k_cd_route(CdDev *st, const int32_t *__restrict__ Lb,
                            int32_t slice_min_w, int32_t SW, int32_t *__restrict__ Lc,
                            int32_t *__restrict__ Lc_k, int32_t *__restrict__ Lc_w,
                            int32_t *__restrict__ Ld,
-                           int32_t *__restrict__ Ld_k, int32_t *__restrict__ Lg,
+                           int32_t *__restrict__ Ld_k, int32_t *__restrict__ Ld_w,
+                           int32_t *__restrict__ Lg,
                            int32_t *__restrict__ Ls, int32_t *__restrict__ Ls_lo,
                            int32_t *__restrict__ Ls_hi) {
     const int lane = threadIdx.x & 31;
@@ -293,6 +294,7 @@ __global__ void k_cd_route(CdDev *st, const int32_t *__restrict__ Lb,
                 p = atomicAdd(&st->nLd, 1);
                 Ld[p] = x;
                 Ld_k[p] = kmin;
+                Ld_w[p] = (int32_t)ww;
             } else if (ww <= cta_keys && wfull[x] <= (unsigned long long)slice_min_w) {
                 p = atomicAdd(&st->nLc, 1);
                 Lc[p] = x;
@@ -400,8 +402,9 @@ struct PeelArgs {
     int32_t *Lc_w;
     int32_t *Ls_lo;        // sliced anchors: first and last key slice of their window
     int32_t *Ls_hi;
-    const int32_t *Ld;     // dense-window anchors and their first key
+    const int32_t *Ld;     // dense-window anchors, their first key and window width
     const int32_t *Ld_k;
+    const int32_t *Ld_w;
     const int32_t *soff;   // per other-side vertex: C + 1 slice starts within its list
     int32_t C;             // key slices
     int32_t SW;            // keys per slice
@@ -641,14 +644,74 @@ __global__ void __launch_bounds__(SLICE_THREADS, 1) k_cd_update_slice(PeelArgs a
     }
 }
 
-// Anchors whose keys fit one window of at most DENSE_KEYS keys: one CTA per
-// anchor aggregates the window with dense 16-bit counters (exact, no
-// overflow path).
+// Anchors whose keys fit one window of at most DENSE_KEYS keys: dense 16-bit
+// counters over the window, exact (no overflow path). A CTA takes DENSE_GROUP
+// anchors at a time and aggregates as many of them per pass as their windows
+// fit side by side in the counters (anchor a's window at offset off[a]); the
+// pass's edges form one virtual list of middle vertices, and the thread that
+// stages a middle vertex records its anchor for the visits.
+constexpr int DENSE_GROUP = 8;
+
+struct DenseBatchMids {
+    const int32_t *adj_s;
+    const int64_t *off_o;
+    const int32_t *len_o;
+    const int64_t *q0;    // first edge of each anchor (shared)
+    const int32_t *pre;   // prefix of the anchors' degrees (shared)
+    int nb;
+    uint8_t *slot;
+    __device__ __forceinline__ void seg(int64_t q, int64_t &beg, int32_t &len) const {
+        int lo = 0, hi = nb - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (pre[mid] <= q)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const int32_t y = adj_s[q0[lo] + (q - pre[lo])];
+        beg = off_o[y];
+        len = len_o[y];
+        slot[threadIdx.x] = (uint8_t)lo;
+    }
+};
+
+struct DenseBatchVisit {
+    DenseSlice *eng;
+    const uint8_t *slot;
+    const int32_t *x;    // anchors (shared)
+    const int32_t *kb;   // first key of each window (shared)
+    const int32_t *off;  // offset of each window in the counters (shared)
+    __device__ __forceinline__ void operator()(int k, int32_t key) {
+        const int a = slot[k];
+        if (key != x[a]) eng->add(off[a] + key - kb[a]);
+    }
+};
+
+struct DenseBatchEmit {
+    CdEmit *e;
+    const int32_t *kb;
+    const int32_t *off;
+    int nb;
+    __device__ __forceinline__ void operator()(int32_t w, uint32_t c) {
+        int a = 0;
+        while (a + 1 < nb && off[a + 1] <= w) a++;
+        (*e)(kb[a] + w - off[a], c);
+    }
+};
+
 __global__ void __maxnreg__(64) k_cd_update_dense(PeelArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_idx, s_nt;
+    __shared__ int s_idx, s_nt, s_nb;
+    __shared__ int64_t s_q0[DENSE_GROUP];
+    __shared__ int32_t s_x[DENSE_GROUP], s_kb[DENSE_GROUP], s_off[DENSE_GROUP + 1],
+        s_pre[DENSE_GROUP + 1];
+    __shared__ uint8_t s_slot[DENSE_THREADS];
     const int32_t n = a.st->nLd;
-    if ((int32_t)blockIdx.x >= n) return;
+    // anchors per fetch: more than one only when the round has more anchors
+    // than CTAs
+    const int G = max(1, min(DENSE_GROUP, n / (int)gridDim.x));
+    if ((int32_t)blockIdx.x * G >= n) return;
     DenseSlice H;
     unsigned char *p = H.bind(smem, &s_nt);
     Chunk ch;
@@ -659,25 +722,67 @@ __global__ void __maxnreg__(64) k_cd_update_dense(PeelArgs a) {
     H.clear_all();
     __syncthreads();
     CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext};
-    PeelMids M{a.adj_s, a.off_o, a.len_o};
+    const int lane = threadIdx.x & 31;
     unsigned long long cw = 0, cm = 0, ca = 0;
     for (;;) {
-        if (threadIdx.x == 0) s_idx = atomicAdd(&a.st->work[4], 1);
+        if (threadIdx.x == 0) s_idx = atomicAdd(&a.st->work[4], G);
         __syncthreads();
-        const int idx = s_idx;
-        if (idx >= n) break;
-        const int32_t x = a.Ld[idx];
-        const int32_t kb = a.Ld_k[idx];
-        const int64_t q0 = a.off_s[x], q1 = a.off_s[x + 1];
-        H.set_width(DENSE_KEYS);
-        SliceVisit<DenseSlice> v{&H, x - kb, kb};
-        cw += cta_walk(M, q0, q1, a.adj_o, ch, v);
-        cm += (unsigned long long)(q1 - q0);
-        ca++;
-        SliceEmit em{&emit, kb};
-        H.sweep<true, true>(em);
-        __syncthreads();
-        H.reset_scalars();
+        const int base = s_idx;
+        if (base >= n) break;
+        const int gcount = min(G, n - base);
+        for (int i0 = 0; i0 < gcount;) {
+            if (threadIdx.x < 32) {
+                // the leading anchors whose windows fit side by side
+                const int i = i0 + lane;
+                int32_t w = 0, deg = 0, x = 0, kb = 0;
+                int64_t q0 = 0;
+                if (i < gcount) {
+                    x = a.Ld[base + i];
+                    kb = a.Ld_k[base + i];
+                    w = a.Ld_w[base + i];
+                    q0 = a.off_s[x];
+                    deg = (int32_t)(a.off_s[x + 1] - q0);
+                }
+                int32_t wi = w, di = deg;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int32_t yw = __shfl_up_sync(0xffffffffu, wi, o);
+                    const int32_t yd = __shfl_up_sync(0xffffffffu, di, o);
+                    if (lane >= o) {
+                        wi += yw;
+                        di += yd;
+                    }
+                }
+                const bool fits = i < gcount && (lane == 0 || wi <= DENSE_KEYS);
+                const int nb = __popc(__ballot_sync(0xffffffffu, fits));
+                if (lane < nb) {
+                    s_x[lane] = x;
+                    s_kb[lane] = kb;
+                    s_q0[lane] = q0;
+                    s_off[lane + 1] = wi;
+                    s_pre[lane + 1] = di;
+                }
+                if (lane == 0) {
+                    s_off[0] = 0;
+                    s_pre[0] = 0;
+                    s_nb = nb;
+                }
+            }
+            __syncthreads();
+            const int nb = s_nb;
+            H.set_width(s_off[nb]);
+            DenseBatchMids M{a.adj_s, a.off_o, a.len_o, s_q0, s_pre, nb, s_slot};
+            DenseBatchVisit v{&H, s_slot, s_x, s_kb, s_off};
+            cw += cta_walk(M, 0, s_pre[nb], a.adj_o, ch, v);
+            cm += (unsigned long long)s_pre[nb];
+            ca += nb;
+            DenseBatchEmit em{&emit, s_kb, s_off, nb};
+            H.sweep<true, true>(em);
+            __syncthreads();
+            H.reset_scalars();
+            i0 += nb;
+            __syncthreads();
+        }
     }
     if (threadIdx.x == 0 && ca) {
         atomicAdd(&a.st->tier_w[4], cw);
@@ -809,7 +914,7 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
     DevBuf<CdDev> st(1, s);
     st.zero();
     DevBuf<int32_t> F(n, s), Nx(n, s), Lw(n, s), Lc(n, s), Lg(n, s), Ls(n, s), Lb(n, s), Ld(n, s);
-    DevBuf<int32_t> Lc_k(n, s), Lc_w(n, s), Ld_k(n, s), Ls_lo(n, s), Ls_hi(n, s);
+    DevBuf<int32_t> Lc_k(n, s), Lc_w(n, s), Ld_k(n, s), Ld_w(n, s), Ls_lo(n, s), Ls_hi(n, s);
     const int32_t warp_max_w =
         opt.warp_max_w > 0 ? std::min(opt.warp_max_w, WARP_MAX_W) : WARP_MAX_W;
     const int32_t slice_min_w = opt.slice_min_w > 0 ? opt.slice_min_w : SLICE_MIN_W;
@@ -917,13 +1022,13 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
         k_cd_route<<<sms * 8, 256, 0, q>>>(st.get(), Lb.get(), S.off, S.adj, O.off, len_w.get(),
                                            adj_w.get(), D.wfull, cta_ok ? cta_keys : 0, slice_min_w,
                                            SW, Lc.get(), Lc_k.get(), Lc_w.get(), Ld.get(),
-                                           Ld_k.get(), Lg.get(), Ls.get(), Ls_lo.get(),
+                                           Ld_k.get(), Ld_w.get(), Lg.get(), Ls.get(), Ls_lo.get(),
                                            Ls_hi.get());
         RC_LAUNCH();
         PeelArgs a{S.off,     S.adj,      O.off,       len_w.get(), adj_w.get(), D.sup, D.sub,
                    st.get(),  Lw.get(),   Lc.get(),    Lg.get(),    Ls.get(), nxt,
                    Lc_k.get(), Lc_w.get(), Ls_lo.get(), Ls_hi.get(), Ld.get(), Ld_k.get(),
-                   table ? soff.get() : nullptr, C, SW, n};
+                   Ld_w.get(), table ? soff.get() : nullptr, C, SW, n};
         mark(0);
         k_cd_update_warp<<<sms * 8, 256, 0, q>>>(a);
         RC_LAUNCH();
