@@ -27,7 +27,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 SHIPPED = os.path.join(_HERE, "tuned.json")
 WARP_MAX_W = (64, 128, 256)
 SLICE_MIN_W = (49152, 98304, 196608, 1 << 30)
-P_CANDIDATES = (100, 150, 300, 600)
+P_CANDIDATES = (75, 100, 150, 200, 300)
 DGM_FRAC_1024 = (32, 64, 128, 256)
 _lock = threading.Lock()
 _table = None
