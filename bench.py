@@ -128,7 +128,7 @@ class ClockSampler:
 
 def load_workload():
     import synth
-    eu, ev, nu, nv, side = synth.config_graph(2)
+    eu, ev, nu, nv, side = synth.workload_graph(synth.CHUNG_LU_10M)
     dv = np.bincount(ev, minlength=nv).astype(np.int64)
     du = np.bincount(eu, minlength=nu).astype(np.int64)
     d_other = dv if side == 0 else du
@@ -291,7 +291,8 @@ def run_ours(args):
     if tr and tr.get("src") == _src_digest():
         traffic = int(tr["dram_per_alg_byte"] * alg_bytes)
     gold_ok = None
-    gpath = os.path.join(ROOT, "tests", "golden", "cfg2.json")
+    import synth
+    gpath = os.path.join(ROOT, "tests", "golden", synth.CHUNG_LU_10M + ".json")
     if os.path.exists(gpath):
         gold = json.load(open(gpath))
         gold_ok = hashlib.sha256(tips.astype("<u8").tobytes()).hexdigest() == gold["tips_sha256"]

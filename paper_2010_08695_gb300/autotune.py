@@ -123,13 +123,13 @@ def main():
     sys.path.insert(0, os.path.dirname(_HERE))
     import synth
     import paper_2010_08695_gb300 as R
-    for cfg in (2,):
-        eu, ev, nu, nv, side = synth.config_graph(cfg)
+    for name in (synth.CHUNG_LU_10M,):
+        eu, ev, nu, nv, side = synth.workload_graph(name)
         d_other = np.bincount(ev if side == 0 else eu, minlength=nv if side == 0 else nu)
         key = shape_class(nu, nv, len(eu), side, int(d_other.max()))
         g = R.Graph(eu, ev, nu, nv)
         rec, times = tune(g, side, key)
-        print(json.dumps({"config": cfg, "key": key, "best": rec, "times_ms": times}))
+        print(json.dumps({"workload": name, "key": key, "best": rec, "times_ms": times}))
 
 
 if __name__ == "__main__":

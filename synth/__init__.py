@@ -31,8 +31,9 @@ from dataclasses import dataclass
 import numpy as np
 
 __all__ = [
-    "er", "chung_lu", "chung_lu_i0_for_max", "edges_sha256", "config_graph",
-    "GraphSpec", "batch_specs", "serve_specs", "graph_from_spec", "CONFIGS",
+    "er", "chung_lu", "chung_lu_i0_for_max", "edges_sha256", "workload_graph",
+    "GraphSpec", "batch_specs", "serve_specs", "graph_from_spec", "WORKLOADS",
+    "ER_20K", "CHUNG_LU_10M", "CHUNG_LU_100M",
     "random_small", "complete_bipartite",
 ]
 
@@ -130,36 +131,42 @@ def random_small(nu: int, nv: int, p: float, seed: int):
 
 
 # --------------------------------------------------------------------------
-# The five named workloads
+# The named workloads
 # --------------------------------------------------------------------------
 
-CONFIGS = {
-    1: dict(kind="er", nu=2000, nv=500, m=20000, seed=1, side=0),
-    2: dict(kind="cl", nu=1_000_000, nv=200_000, m=10_000_000, gamma_u=2.5,
-            gamma_v=2.1, seed=2, dmax_v=50_000, side=0),
-    3: dict(kind="cl", nu=5_000_000, nv=1_000_000, m=100_000_000, gamma_u=2.0,
-            gamma_v=2.0, seed=3, dmax_u=500_000, dmax_v=500_000, side=1),
+ER_20K = "er-2000x500-20k"
+CHUNG_LU_10M = "chung-lu-1Mx200k-10M"
+CHUNG_LU_100M = "chung-lu-5Mx1M-100M"
+
+WORKLOADS = {
+    ER_20K: dict(kind="er", nu=2000, nv=500, m=20000, seed=1, side=0),
+    CHUNG_LU_10M: dict(kind="cl", nu=1_000_000, nv=200_000, m=10_000_000, gamma_u=2.5,
+                       gamma_v=2.1, seed=2, dmax_v=50_000, side=0),
+    CHUNG_LU_100M: dict(kind="cl", nu=5_000_000, nv=1_000_000, m=100_000_000, gamma_u=2.0,
+                        gamma_v=2.0, seed=3, dmax_u=500_000, dmax_v=500_000, side=1),
 }
 
 
 def _cache_dir():
     d = os.environ.get("RECEIPT_GRAPH_CACHE")
     if not d:
-        d = os.path.join(os.path.expanduser("~"), ".cache", "receipt_graphs")
+        d = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), ".graph_cache")
     os.makedirs(d, exist_ok=True)
     return d
 
 
-def config_graph(cfg: int, cache: bool = True):
-    """Edge list of workload ``cfg`` (1: ER 2,000x500, 20k edges; 2: Chung-Lu
-    1Mx200k, 10M edges, exponents 2.5/2.1, max V degree ~50k; 3: Chung-Lu
-    5Mx1M, 100M edges, exponent 2.0 on both sides, hubs ~500k).
+def workload_graph(name: str, cache: bool = True):
+    """Edge list of a named workload: ER_20K (Erdos-Renyi 2,000x500, 20k
+    edges), CHUNG_LU_10M (Chung-Lu 1Mx200k, 10M edges, exponents 2.5/2.1, max
+    V degree ~50k), CHUNG_LU_100M (Chung-Lu 5Mx1M, 100M edges, exponent 2.0 on
+    both sides, hubs ~500k).
 
     Returns ``(eu, ev, nu, nv, side)``. Large graphs are cached as ``.npz``
-    under ``$RECEIPT_GRAPH_CACHE`` (default ``~/.cache/receipt_graphs``)."""
-    c = CONFIGS[cfg]
-    path = os.path.join(_cache_dir(), f"cfg{cfg}.npz")
-    if cache and cfg != 1 and os.path.exists(path):
+    under ``$RECEIPT_GRAPH_CACHE`` (default ``.graph_cache`` beside the package)."""
+    c = WORKLOADS[name]
+    small = c["kind"] == "er"
+    path = os.path.join(_cache_dir(), f"{name}.npz")
+    if cache and not small and os.path.exists(path):
         z = np.load(path)
         return z["eu"], z["ev"], c["nu"], c["nv"], c["side"]
     if c["kind"] == "er":
@@ -173,7 +180,7 @@ def config_graph(cfg: int, cache: bool = True):
             i0v = chung_lu_i0_for_max(c["nv"], c["gamma_v"], c["m"], c["dmax_v"])
         eu, ev = chung_lu(c["nu"], c["nv"], c["m"], c["gamma_u"], c["gamma_v"],
                           c["seed"], i0u, i0v)
-    if cache and cfg != 1:
+    if cache and not small:
         tmp = path + f".{os.getpid()}.tmp.npz"
         np.savez(tmp, eu=eu, ev=ev)
         os.replace(tmp, path)

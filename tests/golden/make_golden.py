@@ -7,7 +7,8 @@ caught before any comparison), the SHA-256 of the oracle's per-vertex
 butterfly counts on both sides and of its tip numbers for the decomposed
 side, plus a seeded sample of individual values for readable failures.
 
-Usage: python tests/golden/make_golden.py [--vp-counts] CFG [CFG ...]
+Usage: python tests/golden/make_golden.py [--vp-counts] WORKLOAD [WORKLOAD ...]
+(workload names as in synth.WORKLOADS; each is written to tests/golden/<name>.json)
 
 --vp-counts takes the initial supports from Algorithm 1 instead of the 2-hop
 definition, after checking them against the 2-hop digests already stored for
@@ -33,16 +34,16 @@ def sha(a):
     return hashlib.sha256(np.ascontiguousarray(a, dtype="<u8").tobytes()).hexdigest()
 
 
-def make(cfg, with_tips=True, vp_counts=False):
+def make(name, with_tips=True, vp_counts=False):
     t0 = time.time()
-    eu, ev, nu, nv, side = synth.config_graph(cfg)
-    rec = {"config": cfg, "nu": nu, "nv": nv, "m": int(len(eu)), "side": side,
+    eu, ev, nu, nv, side = synth.workload_graph(name)
+    rec = {"workload": name, "nu": nu, "nv": nv, "m": int(len(eu)), "side": side,
            "edges_sha256": synth.edges_sha256(eu, ev)}
     t1 = time.time()
     if vp_counts:
         # Algorithm 1 (independent of the 2-hop definition, much faster); the
         # digests must equal the stored 2-hop ones of the same graph
-        old = json.load(open(os.path.join(HERE, f"cfg{cfg}.json")))
+        old = json.load(open(os.path.join(HERE, f"{name}.json")))
         assert old["edges_sha256"] == rec["edges_sha256"], "a different graph was drawn"
         cu, cv = oracle.count_vp(eu, ev, nu, nv)
         assert sha(cu) == old["count_u_sha256"] and sha(cv) == old["count_v_sha256"], \
@@ -55,13 +56,13 @@ def make(cfg, with_tips=True, vp_counts=False):
     rec["count_u_sha256"] = sha(cu)
     rec["count_v_sha256"] = sha(cv)
     rec["butterflies"] = int(cu.sum()) // 2
-    rng = np.random.default_rng(1234 + cfg)
+    rng = np.random.default_rng(1234 + synth.WORKLOADS[name]["seed"])
     su = np.unique(rng.integers(0, nu, 64))
     sv = np.unique(rng.integers(0, nv, 64))
     rec["sample_u"] = {int(x): int(cu[x]) for x in su}
     rec["sample_v"] = {int(x): int(cv[x]) for x in sv}
     rec["oracle_threads"] = oracle.num_threads()
-    _write(cfg, rec)  # counts first: the peel of the largest workload takes hours
+    _write(name, rec)  # counts first: the peel of the largest workload takes hours
     if with_tips:
         # peel from the decomposed side's counts computed above
         tips, st = oracle.bup_from_counts(eu, ev, nu, nv, side, cu if side == 0 else cv)
@@ -74,12 +75,12 @@ def make(cfg, with_tips=True, vp_counts=False):
         rec["sample_tips"] = {int(x): int(tips[x]) for x in ss}
         rec["oracle_seconds"] = {"count": st["seconds_count"], "peel": st["seconds_peel"]}
     rec["wall_seconds"] = time.time() - t0
-    _write(cfg, rec)
+    _write(name, rec)
     print(json.dumps({k: rec[k] for k in rec if not k.startswith("sample")}))
 
 
-def _write(cfg, rec):
-    path = os.path.join(HERE, f"cfg{cfg}.json")
+def _write(name, rec):
+    path = os.path.join(HERE, f"{name}.json")
     with open(path + ".tmp", "w") as f:
         json.dump(rec, f, indent=1, sort_keys=True)
     os.replace(path + ".tmp", path)
@@ -88,4 +89,4 @@ def _write(cfg, rec):
 if __name__ == "__main__":
     args = [a for a in sys.argv[1:] if not a.startswith("--")]
     for a in args:
-        make(int(a), vp_counts="--vp-counts" in sys.argv)
+        make(a, vp_counts="--vp-counts" in sys.argv)

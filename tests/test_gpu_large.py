@@ -37,18 +37,18 @@ def R():
 
 
 @pytest.fixture(scope="module")
-def cfg3():
-    path = os.path.join(HERE, "golden", "cfg3.json")
+def chung_lu_100m():
+    path = os.path.join(HERE, "golden", synth.CHUNG_LU_100M + ".json")
     if not os.path.exists(path):
         pytest.skip("oracle digests of the 100M-edge workload not generated")
     gold = json.load(open(path))
-    eu, ev, nu, nv, side = synth.config_graph(3)
+    eu, ev, nu, nv, side = synth.workload_graph(synth.CHUNG_LU_100M)
     assert synth.edges_sha256(eu, ev) == gold["edges_sha256"], "generator drew a different graph"
     return gold, eu, ev, nu, nv, side
 
 
-def test_config3_counts_and_tips(R, cfg3):
-    gold, eu, ev, nu, nv, side = cfg3
+def test_chung_lu_100m_counts_and_tips(R, chung_lu_100m):
+    gold, eu, ev, nu, nv, side = chung_lu_100m
     g = R.Graph(eu, ev, nu, nv)
     cu, cv = g.count_butterflies()
     cu, cv = R.as_u64(cu), R.as_u64(cv)

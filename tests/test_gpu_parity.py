@@ -61,9 +61,9 @@ def test_tiny_random_graphs(R):
         _check_graph(R, eu, ev, nu, nv)
 
 
-def test_config1_er(R):
-    eu, ev, nu, nv, side = synth.config_graph(1)
-    gold = json.load(open(os.path.join(HERE, "golden", "cfg1.json")))
+def test_er_20k_golden(R):
+    eu, ev, nu, nv, side = synth.workload_graph(synth.ER_20K)
+    gold = json.load(open(os.path.join(HERE, "golden", synth.ER_20K + ".json")))
     assert synth.edges_sha256(eu, ev) == gold["edges_sha256"]
     _check_graph(R, eu, ev, nu, nv)
 
@@ -258,14 +258,14 @@ def test_batch_equals_alone(R):
 
 
 def test_host_buffer_entry(R):
-    eu, ev, nu, nv, side = synth.config_graph(1)
+    eu, ev, nu, nv, side = synth.workload_graph(synth.ER_20K)
     got = R.receipt_tip_decompose_host(eu, ev, nu, nv, 0)
     want, _ = oracle.bup(eu, ev, nu, nv, 0)
     assert np.array_equal(got, want)
 
 
 def test_stats_are_reported(R):
-    eu, ev, nu, nv, side = synth.config_graph(1)
+    eu, ev, nu, nv, side = synth.workload_graph(synth.ER_20K)
     g = R.Graph(eu, ev, nu, nv)
     g.tip_decompose(0, timing=True)
     st = g.stats()
@@ -273,12 +273,12 @@ def test_stats_are_reported(R):
     assert st["ms_total"] > 0
 
 
-def test_config2_golden(R):
-    path = os.path.join(HERE, "golden", "cfg2.json")
+def test_chung_lu_10m_golden(R):
+    path = os.path.join(HERE, "golden", synth.CHUNG_LU_10M + ".json")
     if not os.path.exists(path):
         pytest.skip("golden digests of the 10M-edge workload not generated")
     gold = json.load(open(path))
-    eu, ev, nu, nv, side = synth.config_graph(2)
+    eu, ev, nu, nv, side = synth.workload_graph(synth.CHUNG_LU_10M)
     assert synth.edges_sha256(eu, ev) == gold["edges_sha256"], "generator drew a different graph"
     import hashlib
     g = R.Graph(eu, ev, nu, nv)

@@ -136,7 +136,7 @@ def test_transpose_symmetry():
 
 
 def test_tip_bounded_by_count_and_counting_paths_agree():
-    eu, ev, nu, nv, _ = synth.config_graph(1)
+    eu, ev, nu, nv, _ = synth.workload_graph(synth.ER_20K)
     cu, cv = oracle.count_2hop(eu, ev, nu, nv)
     vu, vv = oracle.count_vp(eu, ev, nu, nv)
     assert (cu == vu).all() and (cv == vv).all()
@@ -169,7 +169,7 @@ def test_duplicates_and_edge_cases():
 
 
 def test_bounded_peel_sample():
-    eu, ev, nu, nv, _ = synth.config_graph(1)
+    eu, ev, nu, nv, _ = synth.workload_graph(synth.ER_20K)
     full, st_full = oracle.bup(eu, ev, nu, nv, 0)
     part, st = oracle.bup(eu, ev, nu, nv, 0, max_wedges=st_full["wedges"] // 3)
     assert not st["complete"] and 0 < st["peeled"] < nu
