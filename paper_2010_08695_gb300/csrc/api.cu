@@ -98,7 +98,7 @@ struct CaptureTLS {
 thread_local CaptureTLS g_capture;
 }  // namespace
 
-cudaStream_t capture_stream() {
+cudaStream_t aux_stream() {
     int d = 0;
     RC_CUDA(cudaGetDevice(&d));
     if (d < 0 || d >= 64) fail(RECEIPT_ERR_INTERNAL, "device index out of range");

@@ -1059,7 +1059,7 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
     // cannot capture) and each round is one graph launch.
     const bool graphs = opt.round_graphs != 0;
     if (graphs) {
-        cudaStream_t cs = capture_stream();
+        cudaStream_t cs = aux_stream();
         for (int par = 0; par < 2; par++) {
             RC_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
             round_body(cs, abuf[par], abuf[par ^ 1], true);

@@ -22,9 +22,9 @@ void count_noalloc(const receipt_graph *g, unsigned long long *d_cnt_u,
 // and reused across calls (no allocation per call).
 void *pinned_scratch(size_t bytes);
 
-// Non-blocking stream of the calling thread on the current device, used only
-// to capture CUDA graphs (nothing is launched on it).
-cudaStream_t capture_stream();
+// Non-blocking auxiliary stream of the calling thread on the current device:
+// CUDA graphs are captured on it, and counting runs its second pass on it.
+cudaStream_t aux_stream();
 
 // Largest key space whose CtaHybrid engine plus `extra` bytes fits in the
 // opt-in shared memory of one CTA (capped at `want`); 0 if none.
