@@ -51,8 +51,8 @@ CPU_SAMPLE_WEDGES = 1_500_000_000  # peel wedges per oracle sample (~10-20 s on 
 # bytes per algorithmic byte of the captured launch (scaled to the average
 # launch of the timed step), keyed by kernel name; valid only while the kernel
 # sources hash to the recorded digest. k_cd_update_cta: CD round 4 of the
-# 10M-edge Chung-Lu workload, 49.27 MB of DRAM for ~971 MB algorithmic.
-NCU_TRAFFIC = {"k_cd_update_cta": {"src": "7f5c9b8d619d3b8c", "dram_per_alg_byte": 0.0508}}
+# 10M-edge Chung-Lu workload, 49.26 MB of DRAM for ~971 MB algorithmic.
+NCU_TRAFFIC = {"k_cd_update_cta": {"src": "476aeb7078845e6b", "dram_per_alg_byte": 0.0507}}
 
 
 def _rank_env():
