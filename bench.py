@@ -55,6 +55,23 @@ CPU_SAMPLE_WEDGES = 1_500_000_000  # peel wedges per oracle sample (~10-20 s on 
 NCU_TRAFFIC = {"k_cd_update_cta": {"src": "476aeb7078845e6b", "dram_per_alg_byte": 0.0507}}
 
 
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The largest of the ranks' values of x (x itself without a process
+    group): the slowest replica's time decides the whole job's time."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job rate of `world` replicas that each process units_per_rank,
+    timed by the slowest one."""
+    return units_per_rank * world / seconds
+
+
 def _rank_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -243,12 +260,8 @@ def run_ours(args):
     if args.trace and rank == 0:
         with open(args.trace, "w") as f:
             json.dump(last_trace, f)
-    ms = statistics.mean(times)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = wedges * world / (ms / 1e3)
+    ms = max_over_ranks(statistics.mean(times), dist, dev)
+    value = replica_rate(wedges, world, ms / 1e3)
     tips = R.as_u64(tip)
 
     # end to end through the C ABI with host buffers
@@ -262,11 +275,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         R.receipt_tip_decompose_host(eu_h, ev_h, nu, nv, side, out=tip_h)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_s = statistics.mean(e2e_t)
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(statistics.mean(e2e_t), dist, dev)
     e2e_ok = bool(np.array_equal(tip_h, tips))
 
     if rank != 0:
@@ -326,7 +335,7 @@ def run_ours(args):
                          "frac": achieved / peak, "traffic": traffic, "kernel": names[tier],
                          "peak_source": peak_kind,
                          "bytes_per_launch": alg_bytes, "launch_ms": dur_s * 1e3},
-            "e2e": {"value": wedges * world / e2e_s, "unit": "wedges/s",
+            "e2e": {"value": replica_rate(wedges, world, e2e_s), "unit": "wedges/s",
                     "h2d_bytes_per_step": int(eu.nbytes + ev.nbytes),
                     "d2h_bytes_per_step": int(n_side * 8), "seconds": e2e_s,
                     "matches_device_path": e2e_ok},
