@@ -183,3 +183,25 @@ def test_peel_from_given_counts_equals_full_bup():
         c = oracle.count_2hop(eu, ev, 3000, 700)[side]
         again, st = oracle.bup_from_counts(eu, ev, 3000, 700, side, c)
         assert st["complete"] and (again == full).all()
+
+
+def test_stored_er_golden_reproduces():
+    """The stored values of the 20k-edge workload are the oracle's: the same
+    draw, the same count and tip digests (tests/golden/make_golden.py wrote
+    them from synth and oracle only)."""
+    import hashlib
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        synth.ER_20K + ".json")
+    gold = json.load(open(path))
+    eu, ev, nu, nv, side = synth.workload_graph(synth.ER_20K)
+    assert synth.edges_sha256(eu, ev) == gold["edges_sha256"]
+
+    def sha(a):
+        return hashlib.sha256(np.ascontiguousarray(a, dtype="<u8").tobytes()).hexdigest()
+
+    cu, cv = oracle.count_2hop(eu, ev, nu, nv)
+    assert sha(cu) == gold["count_u_sha256"] and sha(cv) == gold["count_v_sha256"]
+    t, _ = oracle.bup(eu, ev, nu, nv, side)
+    assert sha(t) == gold["tips_sha256"]
