@@ -257,6 +257,30 @@ def test_batch_equals_alone(R):
         assert np.array_equal(alone, w)
 
 
+def test_large_batch_of_small_graphs(R):
+    """Hundreds of small graphs in one union: rounds with more dense-window
+    anchors than CTAs (several anchors per pass) and FD tasks per graph part;
+    every graph's tips equal its own decomposition, a sample the oracle's."""
+    rng = np.random.default_rng(44)
+    graphs, wants, edges = [], [], []
+    for i in range(600):
+        nu = int(rng.integers(60, 900))
+        nv = int(rng.integers(20, 300))
+        m = int(min(rng.integers(200, 6000), nu * nv // 3))
+        eu, ev = synth.chung_lu(nu, nv, m, 2.3, 2.1, seed=int(rng.integers(1 << 30)))
+        graphs.append(R.Graph(eu, ev, nu, nv))
+        edges.append((eu, ev, nu, nv))
+    outs = R.receipt_decompose_batch(graphs, [0] * len(graphs))
+    st = graphs[0].stats()
+    assert st["fd_tasks"] > st["p_eff"]  # subsets were split by graph
+    for i, g in enumerate(graphs):
+        alone = R.as_u64(g.tip_decompose(0))
+        assert np.array_equal(R.as_u64(outs[i]), alone), f"graph {i}"
+    for i in range(0, len(graphs), 60):
+        eu, ev, nu, nv = edges[i]
+        assert np.array_equal(R.as_u64(outs[i]), oracle.bup(eu, ev, nu, nv, 0)[0]), f"graph {i}"
+
+
 def test_host_buffer_entry(R):
     eu, ev, nu, nv, side = synth.workload_graph(synth.ER_20K)
     got = R.receipt_tip_decompose_host(eu, ev, nu, nv, 0)
