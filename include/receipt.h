@@ -24,9 +24,13 @@
  *  - No C++ exception crosses this boundary. Every entry point returns a
  *    receipt_status; receipt_last_error() gives a thread-local message for the
  *    most recent failure on the calling thread.
- *  - Device-side anomalies (a bounded wait that gave up, an internal table
- *    overflow) are reported through a device error word and surface as
- *    RECEIPT_ERR_TIMEOUT / RECEIPT_ERR_INTERNAL from the call that saw them.
+ *  - No kernel waits on a flag or on another CTA, and every bounded
+ *    structure either is sized from exact counts or has an exact fallback
+ *    (an anchor whose repeat table overflows is redone through key slices),
+ *    so the decomposition calls have no device-side error path.
+ *    RECEIPT_ERR_TIMEOUT and RECEIPT_ERR_INTERNAL come from the serving
+ *    engine (a wait that ran out of time; a request whose decomposition
+ *    failed in a worker).
  */
 #ifndef RECEIPT_H
 #define RECEIPT_H
@@ -43,10 +47,10 @@ typedef enum {
     RECEIPT_ERR_INVALID = 1,  /* bad argument: id out of range, null pointer, bad side */
     RECEIPT_ERR_OOM = 2,      /* device allocation failed                           */
     RECEIPT_ERR_CUDA = 3,     /* a CUDA runtime call failed                          */
-    RECEIPT_ERR_TIMEOUT = 4,  /* a bounded device-side wait gave up                  */
+    RECEIPT_ERR_TIMEOUT = 4,  /* a wait for a served request ran out of time         */
     RECEIPT_ERR_OVERFLOW = 5, /* a count would exceed 2^63 or m exceeds the id space */
     RECEIPT_ERR_BUSY = 6,     /* the serving engine has no free slot or memory       */
-    RECEIPT_ERR_INTERNAL = 7  /* a device-side consistency check failed              */
+    RECEIPT_ERR_INTERNAL = 7  /* unexpected failure inside the library               */
 } receipt_status;
 
 typedef enum { RECEIPT_SIDE_U = 0, RECEIPT_SIDE_V = 1 } receipt_side;
