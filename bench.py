@@ -49,10 +49,10 @@ CPU_SAMPLE_WEDGES = 1_500_000_000  # peel wedges per oracle sample (~10-20 s on 
 
 # DRAM traffic of the dominant kernel from one full-size ncu capture, as DRAM
 # bytes per algorithmic byte of the captured launch (scaled to the average
-# launch of the timed step), keyed by kernel name; valid only while the kernel
-# sources hash to the recorded digest. k_cd_update_cta: CD round 4 of the
+# launch of the timed step), keyed by kernel name; valid only while the peel
+# kernels' sources (PEEL_SOURCES) hash to the recorded digest. k_cd_update_cta: CD round 4 of the
 # 10M-edge Chung-Lu workload, 49.26 MB of DRAM for ~971 MB algorithmic.
-NCU_TRAFFIC = {"k_cd_update_cta": {"src": "476aeb7078845e6b", "dram_per_alg_byte": 0.0507}}
+NCU_TRAFFIC = {"k_cd_update_cta": {"src": "99c4676d959b30b7", "dram_per_alg_byte": 0.0507}}
 
 
 def max_over_ranks(x: float, dist=None, device="cpu") -> float:
@@ -87,12 +87,17 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _src_digest():
+# sources the coarse-grained peel kernels are compiled from
+PEEL_SOURCES = ("cd.cu", "engine.cuh", "common.cuh", "internal.cuh")
+
+
+def _src_digest(files=PEEL_SOURCES):
+    """Digest of the named kernel sources (a recorded ncu traffic figure holds
+    while the kernel's sources are unchanged)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2010_08695_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in sorted(files):
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
