@@ -652,7 +652,16 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
                 clist = clist_next;
                 clist_next = tmp;
             }
-            const int np = s_np;
+            int np = s_np;
+            // a level with few updates makes them all in one batched pass
+            // (one pass costs less than a warp phase followed by a pass)
+            if (bk > 1 && np > 0 && np + s_nbig <= bk) {
+                const int nb0 = s_nbig;
+                for (int pi = threadIdx.x; pi < np; pi += blockDim.x) blist[nb0 + pi] = plist[pi];
+                __syncthreads();
+                if (threadIdx.x == 0) s_nbig = nb0 + np;
+                np = 0;
+            }
             // updates of the peeled vertices inside G_i. Phase A: one warp per
             // peeled vertex whose update walks at most WARP_MAX_W wedges.
             FdEmit emit{fsup, alive, &s_mn, T, clist, &s_nk};
