@@ -52,7 +52,7 @@ CPU_SAMPLE_WEDGES = 1_500_000_000  # peel wedges per oracle sample (~10-20 s on 
 # launch of the timed step), keyed by kernel name; valid only while the peel
 # kernels' sources (PEEL_SOURCES) hash to the recorded digest. k_cd_update_cta: CD round 4 of the
 # 10M-edge Chung-Lu workload, 49.26 MB of DRAM for ~971 MB algorithmic.
-NCU_TRAFFIC = {"k_cd_update_cta": {"src": "99c4676d959b30b7", "dram_per_alg_byte": 0.0507}}
+NCU_TRAFFIC = {"k_cd_update_cta": {"src": "c1a903e285db3254", "dram_per_alg_byte": 0.0507}}
 
 
 def max_over_ranks(x: float, dist=None, device="cpu") -> float:

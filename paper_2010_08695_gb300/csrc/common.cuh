@@ -230,13 +230,6 @@ __device__ __forceinline__ T warp_min(T v) {
     return v;
 }
 
-// Device error word bits.
-enum : unsigned {
-    DEVERR_HASH_PROBE = 1u,   // a bounded hash probe ran out
-    DEVERR_WAIT_TIMEOUT = 2u, // a bounded wait gave up
-    DEVERR_CAPACITY = 4u,     // a list outgrew its buffer
-};
-
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 }  // namespace receipt
