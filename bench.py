@@ -326,8 +326,12 @@ def run_ours(args):
                        else "single", "l2": "flushed between steps (256 MiB write)"},
             "seconds_per_step": ms / 1e3,
             "bit_exact_vs_oracle": gold_ok,
-            "walked_wedges_per_step": {"count": st["wedges_count"], "cd": st["wedges_cd"],
-                                       "fd": st["wedges_fd"]},
+            "walked_wedges_per_step": {"count": st["wedges_count"], "cd": sum(st["peel_wedges"]),
+                                       "cd_without_dgm": st["wedges_cd"], "fd": st["wedges_fd"]},
+            "phase_wedges_per_s": {
+                "count": st["wedges_count"] / (st["ms_count"] / 1e3) if st["ms_count"] else None,
+                "cd": sum(st["peel_wedges"]) / (st["ms_cd"] / 1e3) if st["ms_cd"] else None,
+                "fd": st["wedges_fd"] / (st["ms_fd"] / 1e3) if st["ms_fd"] else None},
             "phase_ms": {"count": st["ms_count"], "cd": st["ms_cd"], "fd": st["ms_fd"],
                          "peel_tiers": st["ms_peel"]},
             "rounds_cd": st["rounds_cd"], "levels_fd": st["levels_fd"], "subsets": st["p_eff"],
@@ -431,7 +435,8 @@ def run_batch(args):
                                 "n": batch_stats["fd_max_subset_n"],
                                 "levels": batch_stats["fd_max_subset_levels"]},
             "fd_tasks": batch_stats["fd_tasks"],
-            "walked_wedges": {"count": batch_stats["wedges_count"], "cd": batch_stats["wedges_cd"],
+            "walked_wedges": {"count": batch_stats["wedges_count"], "cd": sum(batch_stats["peel_wedges"]),
+                              "cd_without_dgm": batch_stats["wedges_cd"],
                               "fd": batch_stats["wedges_fd"]},
             "batch_equals_alone": same, "oracle_sample_ok": oracle_ok,
             "oracle_sample": len(sample)}

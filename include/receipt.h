@@ -114,7 +114,10 @@ typedef struct {
 /* Counters of the last call on a graph (Sec. 5: wedges and rounds). */
 typedef struct {
     uint64_t wedges_count;   /* wedges traversed by Algorithm 1              */
-    uint64_t wedges_cd;      /* wedges traversed by coarse-grained peeling   */
+    uint64_t wedges_cd;      /* wedges of the coarse-grained step's peeled
+                                vertices on the whole graph (their walks
+                                before dynamic graph maintenance shortens
+                                the lists; peel_wedges has what was walked) */
     uint64_t wedges_fd;      /* wedges traversed by fine-grained peeling     */
     uint64_t wedges_bup;     /* sum over the other side of d(d-1): the wedge
                                 count of bottom-up peeling, a graph property */
