@@ -236,8 +236,9 @@ def run_ours(args):
 
     def step(timing):
         g = R.Graph(eu_d, ev_d, nu, nv, stream=stream)
-        g.tip_decompose(side, timing=timing, out=tip, stream=stream,
-                        round_graphs=args.round_graphs)
+        g.tip_decompose(side, P=args.P, timing=timing, out=tip, stream=stream,
+                        round_graphs=args.round_graphs, huc=args.huc,
+                        huc_factor_1024=args.huc_factor_1024)
         st = g.stats()
         if args.trace:
             last_trace[:] = g.trace()
@@ -321,7 +322,8 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "nu": nu, "nv": nv, "m": int(len(eu)), "side": "U",
                        "round_graphs": bool(args.round_graphs),
-                       "P": tuned.get("P", 150), "tuning": tuned or "defaults",
+                       "P": args.P or tuned.get("P", 150), "tuning": tuned or "defaults",
+                       "huc": {"mode": args.huc, "factor_1024": args.huc_factor_1024 or 8192},
                        "wedges_bup": wedges, "parallelism": "replicas" if world > 1
                        else "single", "l2": "flushed between steps (256 MiB write)"},
             "seconds_per_step": ms / 1e3,
@@ -339,6 +341,8 @@ def run_ours(args):
                                 "levels": st["fd_max_subset_levels"]},
             "fd_heavy": {"subsets": st["fd_heavy_subsets"], "ms": st["ms_fd_heavy"],
                          "levels": st["levels_fd_heavy"]},
+            "huc": {"recounts": st["huc_recounts"], "wedges": st["wedges_recount"],
+                    "ms": st["ms_recount"], "cost_recount": st["cost_recount"]},
             "peel_tier_wedges": st["peel_wedges"], "peel_tier_anchors": st["peel_anchors"],
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": names[tier],
@@ -521,6 +525,12 @@ def main():
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--round-graphs", action="store_true",
                     help="run each coarse-grained round as one CUDA graph launch")
+    ap.add_argument("--P", type=int, default=0,
+                    help="subsets of the coarse-grained step (0: the tuned value)")
+    ap.add_argument("--huc", type=int, default=0, choices=[-1, 0, 1],
+                    help="recount rule (Sec. 4.1): 0 cost rule, -1 never, 1 every range")
+    ap.add_argument("--huc-factor-1024", type=int, default=0,
+                    help="factor of the recount rule in 1/1024 units (0: 8192)")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-calib", type=int, default=40)
     ap.add_argument("--serve-slots", type=int, default=4)

@@ -30,7 +30,8 @@
  *    so the decomposition calls have no device-side error path.
  *    RECEIPT_ERR_TIMEOUT and RECEIPT_ERR_INTERNAL come from the serving
  *    engine (a wait that ran out of time; a request whose decomposition
- *    failed in a worker).
+ *    failed in a worker); RECEIPT_ERR_INTERNAL also reports a failed
+ *    internal consistency check (not expected to happen).
  */
 #ifndef RECEIPT_H
 #define RECEIPT_H
@@ -101,14 +102,27 @@ typedef struct {
     /* Fine-grained step (Algorithm 4): subsets whose wedge count (the LPT key
      * of Sec. 3.2.1, sum of L(L-1) over the runs L of G_i) is at least this
      * are peeled by all CTAs level by level instead of by one CTA of the
-     * persistent queue. 0 = automatic (8 times the mean share of one CTA and
-     * at least 2^23), -1 = never. Speed only. */
+     * persistent queue. 0 = automatic (8 times the total weight divided by
+     * the smaller of the CTA count and the task count, and at least 2^23),
+     * -1 = never. Speed only. */
     int64_t fd_heavy_w;
     /* Non-zero: every synchronisation round of Algorithm 3 runs as one
      * launch of a CUDA graph captured once per call (the round's kernels,
      * the copy of its counters to the host and the advance to the next
      * activeSet) instead of separate launches. Speed only. */
     int32_t round_graphs;
+    /* Hybrid update computation (Sec. 4.1). When the first activeSet of a
+     * range of Algorithm 3 carries C_peel wedges (sum over its vertices x
+     * of sum_{y in N_x} d_y) and C_peel >= factor * C_rcnt, where C_rcnt
+     * is the sum over all edges (u, v) of min(d_u, d_v), the round
+     * recounts the butterflies of the remaining subgraph (Algorithm 1 with
+     * every assigned vertex removed) instead of applying the activeSet's
+     * updates. huc: 0 = that rule, -1 = never, 1 = recount the first
+     * round of every range (test hook). huc_factor_1024: the factor in
+     * 1/1024 units (0 = 8192, i.e. 8; 1024 is the paper's rule C_peel >
+     * C_rcnt). Speed only; results are the same. */
+    int32_t huc;
+    int32_t huc_factor_1024;
 } receipt_options;
 
 /* Counters of the last call on a graph (Sec. 5: wedges and rounds). */
@@ -150,7 +164,15 @@ typedef struct {
     /* Tasks of the fine-grained step: one per subset, or, for a batch, one
      * per packed graph's part of a subset (small parts merged). */
     int32_t fd_tasks;
-    int32_t reserved2;
+    /* Hybrid update computation (see receipt_options.huc): rounds whose
+     * updates were a recount, wedges those recounts traversed, C_rcnt of
+     * the graph (0 when the rule was not evaluated) and the recounts'
+     * device time (only if timing != 0). */
+    int32_t huc_recounts;
+    uint64_t wedges_recount;
+    uint64_t cost_recount;
+    float ms_recount;
+    int32_t reserved3;
 } receipt_stats;
 
 /* One synchronisation round of the coarse-grained step (Algorithm 3). */
@@ -161,6 +183,7 @@ typedef struct {
     uint64_t anchors[5];  /* peeled vertices with updates, per peel tier      */
     uint64_t wedges[5];   /* wedges walked, per peel tier                     */
     float ms[5];          /* device time per peel tier (only if timing != 0)  */
+    int32_t recount;      /* 1: the round's updates were a recount (HUC)      */
 } receipt_round;
 
 /* One subset of the fine-grained step (Algorithm 4, Sec. 3.2.1). */

@@ -47,7 +47,8 @@ class Options(ctypes.Structure):
                 ("h_p_eff", ctypes.POINTER(ctypes.c_int32)), ("timing", ctypes.c_int32),
                 ("warp_max_w", ctypes.c_int32), ("slice_min_w", ctypes.c_int32),
                 ("no_dgm", ctypes.c_int32), ("dgm_frac_1024", ctypes.c_int32),
-                ("fd_heavy_w", ctypes.c_int64), ("round_graphs", ctypes.c_int32)]
+                ("fd_heavy_w", ctypes.c_int64), ("round_graphs", ctypes.c_int32),
+                ("huc", ctypes.c_int32), ("huc_factor_1024", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -63,13 +64,15 @@ class Stats(ctypes.Structure):
                 ("fd_max_subset_n", ctypes.c_int32), ("fd_max_subset_levels", ctypes.c_int64),
                 ("fd_heavy_subsets", ctypes.c_int32), ("ms_fd_heavy", ctypes.c_float),
                 ("levels_fd_heavy", ctypes.c_int64), ("fd_tasks", ctypes.c_int32),
-                ("reserved2", ctypes.c_int32)]
+                ("huc_recounts", ctypes.c_int32), ("wedges_recount", ctypes.c_uint64),
+                ("cost_recount", ctypes.c_uint64), ("ms_recount", ctypes.c_float),
+                ("reserved3", ctypes.c_int32)]
 
 
 class Round(ctypes.Structure):
     _fields_ = [("range", ctypes.c_int32), ("frontier", ctypes.c_int32), ("hi", ctypes.c_uint64),
                 ("anchors", ctypes.c_uint64 * 5), ("wedges", ctypes.c_uint64 * 5),
-                ("ms", ctypes.c_float * 5)]
+                ("ms", ctypes.c_float * 5), ("recount", ctypes.c_int32)]
 
 
 class Subset(ctypes.Structure):
@@ -174,10 +177,12 @@ def _dptr(t):
 
 def _options(P=150, bounds=None, subset=None, bounds_out=None, p_eff=None, timing=False,
              warp_max_w=0, slice_min_w=0, dgm=True, dgm_frac_1024=0, fd_heavy_w=0,
-             round_graphs=False):
+             round_graphs=False, huc=0, huc_factor_1024=0):
     o = Options()
     load().receipt_options_default(ctypes.byref(o))
     o.P = int(P)
+    o.huc = int(huc)
+    o.huc_factor_1024 = int(huc_factor_1024)
     o.fd_heavy_w = int(fd_heavy_w)
     o.round_graphs = 1 if round_graphs else 0
     o.dgm_frac_1024 = int(dgm_frac_1024)
@@ -252,7 +257,8 @@ def receipt_get_trace(handle) -> list:
     buf = (Round * max(1, n.value))()
     _check(lib.receipt_get_trace(handle, buf, n.value, ctypes.byref(n)))
     return [{"range": r.range, "frontier": r.frontier, "hi": r.hi, "anchors": list(r.anchors),
-             "wedges": list(r.wedges), "ms": list(r.ms)} for r in buf[: n.value]]
+             "wedges": list(r.wedges), "ms": list(r.ms), "recount": r.recount}
+            for r in buf[: n.value]]
 
 
 def receipt_get_subsets(handle) -> list:
@@ -320,10 +326,13 @@ class Graph:
 
     def tip_decompose(self, side: int = SIDE_U, P: int = 0, bounds=None, subsets=False,
                       timing=False, out=None, stream=None, warp_max_w=0, slice_min_w=0, dgm=True,
-                      dgm_frac_1024=0, fd_heavy_w=0, round_graphs=False):
+                      dgm_frac_1024=0, fd_heavy_w=0, round_graphs=False, huc=0,
+                      huc_factor_1024=0):
         """Tip numbers of ``side`` (Algorithms 3 and 4). P = 0 takes the tuned
         value for this graph's shape class, else 150. With ``subsets=True``
-        returns ``(tips, subset_of_vertex, range_bounds)``."""
+        returns ``(tips, subset_of_vertex, range_bounds)``. ``huc``: 0 = the
+        recount rule of Sec. 4.1, -1 = never recount, 1 = recount the first
+        round of every range."""
         import torch
         n = self.nu if side == SIDE_U else self.nv
         tuned = None
@@ -342,7 +351,7 @@ class Graph:
             if subsets else None
         peff = ctypes.c_int32(0)
         o, keep = _options(P, bounds, sub, bout, peff, timing, warp_max_w, slice_min_w, dgm,
-                           dgm_frac_1024, fd_heavy_w, round_graphs)
+                           dgm_frac_1024, fd_heavy_w, round_graphs, huc, huc_factor_1024)
         receipt_tip_decompose(self._h, side, tip, o, stream)
         if subsets:
             return tip, sub, bout[: peff.value + 1]
@@ -359,7 +368,7 @@ class Graph:
 
 
 def receipt_decompose_batch(graphs, sides, outs=None, P: int = 150, stream=None, timing=False,
-                            round_graphs=False):
+                            round_graphs=False, huc=0, huc_factor_1024=0):
     """Tip numbers of many graphs in one pass (disjoint-union packing)."""
     import torch
     n = len(graphs)
@@ -369,7 +378,8 @@ def receipt_decompose_batch(graphs, sides, outs=None, P: int = 150, stream=None,
         outs = [torch.empty(g.nu if s == 0 else g.nv, dtype=torch.int64, device=g.device)
                 for g, s in zip(graphs, sides)]
     ps = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
-    o, keep = _options(P, timing=timing, round_graphs=round_graphs)
+    o, keep = _options(P, timing=timing, round_graphs=round_graphs, huc=huc,
+                       huc_factor_1024=huc_factor_1024)
     _check(load().receipt_decompose_batch(hs, ss, n, ps, ctypes.byref(o), _stream_handle(stream)))
     return outs
 

@@ -186,6 +186,8 @@ void tip_decompose_impl(receipt_graph *g, int side, uint64_t *d_tip, const recei
             if (opt.h_bounds[i] == 0 || (i && opt.h_bounds[i] <= opt.h_bounds[i - 1]))
                 fail(RECEIPT_ERR_INVALID, "h_bounds must be positive and strictly increasing");
     }
+    if (opt.huc < -1 || opt.huc > 1) fail(RECEIPT_ERR_INVALID, "huc must be -1, 0 or 1");
+    if (opt.huc_factor_1024 < 0) fail(RECEIPT_ERR_INVALID, "huc_factor_1024 must be >= 0");
     const Side &S = g->side[side];
     const int32_t n = S.n;
     if (n > 0 && !d_tip) fail(RECEIPT_ERR_INVALID, "null d_tip");
@@ -249,6 +251,10 @@ void tip_decompose_impl(receipt_graph *g, int side, uint64_t *d_tip, const recei
     st.ms_fd_heavy = D.fd_heavy_ms;
     st.levels_fd_heavy = D.fd_heavy_levels;
     st.fd_tasks = D.fd_tasks;
+    st.huc_recounts = D.huc_recounts;
+    st.wedges_recount = D.wedges_recount;
+    st.cost_recount = D.cost_recount;
+    st.ms_recount = D.ms_recount;
     g->subsets = std::move(D.subsets);
     for (int t = 0; t < 5; t++) {
         st.peel_wedges[t] = D.tier_wedges[t];

@@ -36,6 +36,11 @@ namespace {
 constexpr int NBUCKET = LOG_BUCKETS;
 constexpr int NTIER = 5;  // warp, hybrid, global, sliced, dense window
 constexpr double DGM_FRAC = 0.125;  // stale share of live entries that triggers a compaction
+// A range's first round recounts instead of peeling when its activeSet's
+// wedges reach HUC_FACTOR * C_rcnt: per unit of the two cost measures the
+// peel tiers run 4-10 times faster than the counting kernels (measured on
+// Chung-Lu graphs of 10M and 100M edges).
+constexpr double HUC_FACTOR = 8.0;
 
 __device__ __forceinline__ int bucket_of(unsigned long long k) { return log_bucket_of(k); }
 __device__ __forceinline__ unsigned long long bucket_top(int b) { return log_bucket_top(b); }
@@ -52,6 +57,7 @@ struct CdDev {
     double tgt_prev;
     unsigned long long wedges;
     unsigned long long tier_w[NTIER], tier_m[NTIER], tier_a[NTIER];  // per tier: wedges, mids, anchors
+    unsigned long long front_w;  // sum of wfull over a full-scan activeSet (C_peel)
     unsigned long long hist_w[NBUCKET];
     uint32_t hist_c[NBUCKET];
 };
@@ -176,24 +182,31 @@ __global__ void k_set_hi(CdDev *st, unsigned long long hi) {
     st->n_remaining = 1;
 }
 
-// First activeSet of a range: remaining vertices with sup < hi, compacted
-// with a warp ballot and one atomic per warp.
+// ActiveSet by a full scan (a range's first round, and the round after a
+// recount): remaining vertices with sup < hi, compacted with a warp ballot
+// and one atomic per warp on *count; their wedge total (the C_peel of
+// Sec. 4.1) is added to st->front_w.
 __global__ void k_cd_frontier(int32_t n, const int32_t *__restrict__ sub,
-                              const unsigned long long *__restrict__ sup, CdDev *st,
-                              int32_t *__restrict__ F) {
+                              const unsigned long long *__restrict__ sup,
+                              const unsigned long long *__restrict__ wfull, CdDev *st,
+                              int32_t *count, int32_t *__restrict__ F) {
     const unsigned long long hi = st->hi;
     const int lane = threadIdx.x & 31;
+    unsigned long long wsum = 0;
     for (int32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
         int32_t x = base + threadIdx.x;
         bool take = x < n && sub[x] < 0 && sup[x] < hi;
+        if (take) wsum += wfull[x];
         unsigned bal = __ballot_sync(0xffffffffu, take);
         if (bal) {
             int pos = 0;
-            if (lane == 0) pos = atomicAdd(&st->nF, __popc(bal));
+            if (lane == 0) pos = atomicAdd(count, __popc(bal));
             pos = __shfl_sync(0xffffffffu, pos, 0);
             if (take) F[pos + __popc(bal & lanemask_lt())] = x;
         }
     }
+    wsum = warp_sum(wsum);
+    if (lane == 0 && wsum) atomicAdd(&st->front_w, wsum);
 }
 
 // Assigns the activeSet to subset `range` and splits the vertices that have
@@ -858,6 +871,7 @@ __global__ void k_cd_advance(CdDev *st) {
 __global__ void k_cd_new_range(CdDev *st, int32_t range) {
     if (threadIdx.x == 0) {
         st->range = range;
+        st->front_w = 0;
         st->nF = st->nNext = 0;
         st->nLw = st->nLc = st->nLg = st->nLo = st->nLs = st->nLb = st->nLd = 0;
         for (int i = 0; i < 6; i++) st->work[i] = 0;
@@ -931,6 +945,15 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
     const bool dgm = !opt.no_dgm;
     const double dgm_frac = opt.dgm_frac_1024 > 0 ? opt.dgm_frac_1024 / 1024.0 : DGM_FRAC;
     uint64_t peeled_at_dgm = 0;
+    // hybrid update computation: C_rcnt once per call when the rule is on
+    const int huc = opt.huc;
+    const double huc_factor =
+        opt.huc_factor_1024 > 0 ? opt.huc_factor_1024 / 1024.0 : HUC_FACTOR;
+    DevBuf<unsigned long long> rcost(1, s);
+    if (huc == 0)
+        launch_recount_cost(S, O, D.m, rcost.get(), s);
+    else
+        rcost.zero();
     if (O.n > 0) {
         k_list_lengths<<<ceil_div(O.n, 256), 256, 0, s>>>(O.off, O.n, len_w.get());
         RC_LAUNCH();
@@ -972,18 +995,18 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
     CdDev *hst = reinterpret_cast<CdDev *>(hpin + 8);
     const size_t hdr = offsetof(CdDev, hist_w);
     unsigned long long prev_w[NTIER] = {}, prev_a[NTIER] = {};
-    int32_t *hi32 = reinterpret_cast<int32_t *>(hpin);
 
-    cudaEvent_t ev[NTIER + 1] = {};
+    // ev[0..NTIER]: peel tiers; ev[NTIER + 1..NTIER + 2]: a recount
+    cudaEvent_t ev[NTIER + 3] = {};
     struct EvGuard {
         cudaEvent_t *e;
         ~EvGuard() {
-            for (int i = 0; i <= NTIER; i++)
+            for (int i = 0; i < NTIER + 3; i++)
                 if (e[i]) cudaEventDestroy(e[i]);
         }
     } eg{ev};
     if (D.timing)
-        for (int i = 0; i <= NTIER; i++) RC_CUDA(cudaEventCreate(&ev[i]));
+        for (int i = 0; i < NTIER + 3; i++) RC_CUDA(cudaEventCreate(&ev[i]));
     k_init_state<<<ceil_div(n, 256), 256, 0, s>>>(D.sub, n);
     RC_LAUNCH();
     const int nb = std::min(ceil_div(n, 512), sms * 4);
@@ -1054,6 +1077,51 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
         k_cd_advance<<<1, 1, 0, q>>>(st.get());
         RC_LAUNCH();
     };
+    // A round whose updates are a recount (Sec. 4.1): assign the activeSet
+    // `cur`, drop every assigned vertex from the other side's lists (the
+    // working copy itself with DGM on, else a copy of it), recount the
+    // remaining subgraph into sup and take the next activeSet `nxt` by a
+    // full scan.
+    DevBuf<int32_t> tadj, tlen;
+    auto huc_round = [&](int32_t *cur, int32_t *nxt) {
+        k_cd_prepare<<<nb, 512, 0, s>>>(cur, st.get(), D.sub, D.sup, D.wfull, S.off, Lw.get(),
+                                        Lb.get(), warp_max_w);
+        RC_LAUNCH();
+        int32_t *la = adj_w.get(), *ll = len_w.get();
+        if (!dgm) {
+            if (!tadj.get()) {
+                tadj.alloc(D.m, s);
+                tlen.alloc(O.n, s);
+            }
+            RC_CUDA(cudaMemcpyAsync(tadj.get(), adj_w.get(), sizeof(int32_t) * D.m,
+                                    cudaMemcpyDeviceToDevice, s));
+            RC_CUDA(cudaMemcpyAsync(tlen.get(), len_w.get(), sizeof(int32_t) * O.n,
+                                    cudaMemcpyDeviceToDevice, s));
+            la = tadj.get();
+            ll = tlen.get();
+        }
+        if (O.n > 0) {
+            k_dgm_compact<<<std::min(ceil_div((int64_t)O.n * 32, 256), sms * 32), 256, 0, s>>>(
+                O.off, ll, la, O.n, D.sub);
+            RC_LAUNCH();
+            if (dgm && table) {
+                k_slice_table<<<ceil_div((int64_t)O.n * (C + 1), 256), 256, 0, s>>>(
+                    O.off, len_w.get(), adj_w.get(), O.n, C, SW, soff.get());
+                RC_LAUNCH();
+            }
+        }
+        if (D.timing) RC_CUDA(cudaEventRecord(ev[NTIER + 1], s));
+        D.wedges_recount += recount_remaining(D, ll, la, s);
+        if (D.timing) RC_CUDA(cudaEventRecord(ev[NTIER + 2], s));
+        k_cd_frontier<<<nb, 512, 0, s>>>(n, D.sub, D.sup, D.wfull, st.get(), &st.get()->nNext,
+                                         nxt);
+        RC_LAUNCH();
+        RC_CUDA(cudaMemcpyAsync(hst, st.get(), hdr, cudaMemcpyDeviceToHost, s));
+        k_cd_advance<<<1, 1, 0, s>>>(st.get());
+        RC_LAUNCH();
+        D.huc_recounts++;
+        if (dgm) D.dgm_passes++;
+    };
     // With round_graphs the body is captured once per activeSet parity (on a
     // private stream: the caller's may be the legacy default stream, which
     // cannot capture) and each round is one graph launch.
@@ -1081,6 +1149,7 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
     }
     int parity = 0;
     int32_t *cur = abuf[0];
+    uint64_t crcnt = 0;  // C_rcnt (rule on) or 0
     for (range = 0; range < nranges; range++) {
         k_cd_new_range<<<1, 256, 0, s>>>(st.get(), range);
         RC_LAUNCH();
@@ -1092,36 +1161,52 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
             k_cd_select<<<1, 1024, 0, s>>>(st.get(), range, P);
         }
         RC_LAUNCH();
-        // hi (8 B) and n_remaining (4 B) back to the host
-        RC_CUDA(cudaMemcpyAsync(hpin, &st.get()->hi, 8, cudaMemcpyDeviceToHost, s));
-        RC_CUDA(cudaMemcpyAsync(hi32 + 2, &st.get()->n_remaining, 4, cudaMemcpyDeviceToHost, s));
-        RC_CUDA(cudaStreamSynchronize(s));
-        const uint64_t hi = hpin[0];
-        if (hi32[2] == 0) break;  // nothing remains
         cur = abuf[parity];
-        k_cd_frontier<<<nb, 512, 0, s>>>(n, D.sub, D.sup, st.get(), cur);
+        k_cd_frontier<<<nb, 512, 0, s>>>(n, D.sub, D.sup, D.wfull, st.get(), &st.get()->nF, cur);
         RC_LAUNCH();
+        // the state's header (hi, n_remaining, the activeSet's C_peel) and,
+        // once, C_rcnt back to the host
+        RC_CUDA(cudaMemcpyAsync(hst, st.get(), hdr, cudaMemcpyDeviceToHost, s));
+        if (range == 0) RC_CUDA(cudaMemcpyAsync(hpin, rcost.get(), 8, cudaMemcpyDeviceToHost, s));
+        RC_CUDA(cudaStreamSynchronize(s));
+        const uint64_t hi = hst->hi;
+        if (hst->n_remaining == 0) break;  // nothing remains
+        if (range == 0) crcnt = hpin[0];
+        D.cost_recount = crcnt;
+        bool recount = huc == 1 || (huc == 0 && crcnt > 0 &&
+                                    (double)hst->front_w >= huc_factor * (double)crcnt);
         for (;;) {
-            if (graphs) {
+            if (recount) {
+                huc_round(abuf[parity], abuf[parity ^ 1]);
+            } else if (graphs) {
                 RC_CUDA(cudaGraphLaunch(round_exec[parity], s));
                 count_launches(round_kernels);
             } else {
                 round_body(s, abuf[parity], abuf[parity ^ 1], false);
             }
             RC_CUDA(cudaStreamSynchronize(s));
-            for (int t = 0; t < NTIER; t++) D.tier_launches[t]++;
+            if (!recount)
+                for (int t = 0; t < NTIER; t++) D.tier_launches[t]++;
             D.rounds++;
             receipt_round rr{};
             rr.range = range;
             rr.frontier = hst->nF;
             rr.hi = hi;
+            rr.recount = recount ? 1 : 0;
             for (int t = 0; t < NTIER; t++) {
                 rr.anchors[t] = hst->tier_a[t] - prev_a[t];
                 rr.wedges[t] = hst->tier_w[t] - prev_w[t];
                 prev_a[t] = hst->tier_a[t];
                 prev_w[t] = hst->tier_w[t];
             }
-            if (D.timing) {
+            if (recount) {
+                if (dgm) peeled_at_dgm = hst->peeled_edges;  // the lists were just compacted
+                if (D.timing) {
+                    float ms = 0;
+                    RC_CUDA(cudaEventElapsedTime(&ms, ev[NTIER + 1], ev[NTIER + 2]));
+                    D.ms_recount += ms;
+                }
+            } else if (D.timing) {
                 // launch order: warp, dense window, hybrid, global, sliced
                 static const int tier_of_gap[NTIER] = {0, 4, 1, 2, 3};
                 for (int gp = 0; gp < NTIER; gp++) {
@@ -1134,6 +1219,7 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
             D.trace.push_back(rr);
             if (hst->nNext == 0) break;
             parity ^= 1;  // the next round reads the activeSet this one wrote
+            recount = false;
         }
         D.bounds.push_back(hi);
         // dynamic graph maintenance: once the vertices assigned since the last

@@ -1042,8 +1042,8 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
     const int sms = num_sms();
     const int grid_all = sms * std::max(occ, 1);
     // Heavy tasks (peeled first by all CTAs): task weight at least the
-    // threshold. Automatic: HEAVY_SHARE times the mean share of one CTA and
-    // at least HEAVY_MIN_W.
+    // threshold. Automatic: HEAVY_SHARE times the total weight divided by
+    // min(CTAs, tasks), and at least HEAVY_MIN_W.
     int nheavy = 0;
     if (D.fd_heavy_w >= 0 && T > 0) {
         unsigned long long thr = (unsigned long long)D.fd_heavy_w;

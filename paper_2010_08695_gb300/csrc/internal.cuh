@@ -73,9 +73,24 @@ struct Decomp {
     // disjoint union (null otherwise)
     const std::vector<int64_t> *parts = nullptr;
     std::vector<receipt_subset> subsets;
+    int32_t huc_recounts = 0;        // rounds whose updates were a recount (Sec. 4.1)
+    uint64_t wedges_recount = 0;     // wedges traversed by those recounts
+    uint64_t cost_recount = 0;       // C_rcnt = sum over edges of min(d_u, d_v)
+    float ms_recount = 0;
 };
 
 void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s);
+
+// Hybrid update computation (Sec. 4.1). Enqueues *d_out = C_rcnt, the sum
+// over the edges (x, y) of min(d_x, d_y).
+void launch_recount_cost(const Side &S, const Side &O, int64_t m, unsigned long long *d_out,
+                         cudaStream_t s);
+// Recounts the butterflies of the subgraph left after removing every vertex
+// with D.sub >= 0 and stores each remaining vertex's count in D.sup.
+// len_w/adj_w: the other side's lists (original offsets) already compacted
+// to remaining vertices. Returns the wedges traversed; synchronises s.
+uint64_t recount_remaining(const Decomp &D, const int32_t *len_w, const int32_t *adj_w,
+                           cudaStream_t s);
 void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s);
 
 }  // namespace receipt

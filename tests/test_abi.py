@@ -65,3 +65,36 @@ def test_null_arguments_are_rejected_without_gpu(lib):
     assert lib.receipt_get_stats(None, None) == 1
     assert lib.receipt_graph_info(None, None, None, None) == 1
     assert lib.receipt_graph_destroy(None) == 0
+
+
+def test_struct_layouts_match_header():
+    """Every ctypes mirror of a header struct has the C size and the C offset
+    of each field (checked with offsetof in a program gcc builds from
+    include/receipt.h)."""
+    import shutil
+    import paper_2010_08695_gb300 as R
+    from paper_2010_08695_gb300 import _build
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not found")
+    pairs = [(R.Options, "receipt_options"), (R.Stats, "receipt_stats"),
+             (R.Round, "receipt_round"), (R.Subset, "receipt_subset"),
+             (R.ServerConfig, "receipt_server_config"), (R.ServerStats, "receipt_server_stats")]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "receipt.h"',
+             "int main(void) {"]
+    want = []
+    for cls, cname in pairs:
+        lines.append(f'    printf("%zu\\n", sizeof({cname}));')
+        want.append(ctypes.sizeof(cls))
+        for f, _ in cls._fields_:
+            lines.append(f'    printf("%zu\\n", offsetof({cname}, {f}));')
+            want.append(getattr(cls, f).offset)
+    lines += ["    return 0;", "}"]
+    os.makedirs(_build.BUILD_DIR, exist_ok=True)
+    src = os.path.join(_build.BUILD_DIR, "layout_probe.c")
+    exe = os.path.join(_build.BUILD_DIR, "layout_probe")
+    with open(src, "w") as fh:
+        fh.write("\n".join(lines) + "\n")
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", exe, src], check=True)
+    got = [int(x) for x in subprocess.run([exe], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    assert got == want

@@ -238,6 +238,73 @@ def test_heavy_subset_path_gives_same_tips(R):
     assert np.array_equal(got, want)
 
 
+def test_recount_rounds_give_same_tips(R):
+    """Hybrid update computation (Sec. 4.1): ranges whose first round
+    recounts the remaining subgraph instead of peeling (forced for every
+    range, or chosen by the cost rule with a tiny factor) give the oracle's
+    tips on both sides, for any P, with dynamic graph maintenance on and off,
+    with rounds as graph launches and injected ranges; C_rcnt equals the sum
+    over edges of min(d_u, d_v)."""
+    nu, nv = 20000, 4000
+    eu, ev = synth.chung_lu(nu, nv, 120000, 2.4, 2.2, seed=35)
+    du, dv = np.bincount(eu, minlength=nu), np.bincount(ev, minlength=nv)
+    crcnt = int(np.minimum(du[eu], dv[ev]).sum())
+    g = R.Graph(eu, ev, nu, nv)
+    for side in (0, 1):
+        want, _ = oracle.bup(eu, ev, nu, nv, side)
+        for P in (1, 3, 40, 150):
+            for dgm in (True, False):
+                t = R.as_u64(g.tip_decompose(side, P=P, huc=1, dgm=dgm, timing=True))
+                assert np.array_equal(t, want), f"side {side} P={P} dgm={dgm}"
+                st, tr = g.stats(), g.trace()
+                ranges = sorted({r["range"] for r in tr})
+                assert st["huc_recounts"] == len(ranges) >= 1
+                firsts = {}
+                for r in tr:
+                    firsts.setdefault(r["range"], r)
+                assert all(r["recount"] == (firsts[r["range"]] is r) for r in tr)
+                assert all(sum(r["wedges"]) == 0 for r in tr if r["recount"])
+                if P > 1:  # with one range the first activeSet takes every vertex
+                    assert st["wedges_recount"] > 0 and st["ms_recount"] > 0
+        t = R.as_u64(g.tip_decompose(side, huc=1, round_graphs=True))
+        assert np.array_equal(t, want), f"side {side} graph rounds"
+        b = np.array([3, 50, 400, 5000], np.uint64)
+        t = R.as_u64(g.tip_decompose(side, P=len(b), bounds=b, huc=1))
+        assert np.array_equal(t, want), f"side {side} injected ranges"
+        t = R.as_u64(g.tip_decompose(side, P=20, huc=0, huc_factor_1024=1))
+        assert np.array_equal(t, want), f"side {side} rule with factor 1/1024"
+        st = g.stats()
+        assert st["cost_recount"] == crcnt and st["huc_recounts"] >= 1
+        g.tip_decompose(side, huc=-1)
+        st = g.stats()
+        assert st["huc_recounts"] == 0 and st["cost_recount"] == 0
+    # a hub of degree >= 2^16 on the other side: the recount goes through the
+    # counting kernels' global-counter tier
+    rng = np.random.default_rng(36)
+    nu, nv = 80000, 40
+    eu = [np.arange(70000, dtype=np.int32)]
+    ev = [np.zeros(70000, np.int32)]
+    for v in range(1, nv):
+        us = rng.choice(nu, 900, replace=False).astype(np.int32)
+        eu.append(us)
+        ev.append(np.full(len(us), v, np.int32))
+    eu, ev = np.concatenate(eu), np.concatenate(ev)
+    want, _ = oracle.bup(eu, ev, nu, nv, 1)
+    got, _ = _gpu_tips(R, eu, ev, nu, nv, 1, P=4, huc=1)
+    assert np.array_equal(got, want), "hub graph"
+    # a batch of graphs packed into one union
+    specs = synth.batch_specs(16, seed=37)
+    graphs, wants = [], []
+    for s in specs:
+        beu, bev = synth.graph_from_spec(s)
+        graphs.append(R.Graph(beu, bev, s.nu, s.nv))
+        wants.append(oracle.bup(beu, bev, s.nu, s.nv, 0)[0])
+    outs = R.receipt_decompose_batch(graphs, [0] * len(graphs), huc=1)
+    for i, (o, w) in enumerate(zip(outs, wants)):
+        assert np.array_equal(R.as_u64(o), w), f"batch graph {i}"
+    assert graphs[0].stats()["huc_recounts"] >= 1
+
+
 def test_batch_equals_alone(R):
     specs = synth.batch_specs(24, seed=4)
     graphs, sides, wants = [], [], []
