@@ -205,3 +205,33 @@ def test_stored_er_golden_reproduces():
     assert sha(cu) == gold["count_u_sha256"] and sha(cv) == gold["count_v_sha256"]
     t, _ = oracle.bup(eu, ev, nu, nv, side)
     assert sha(t) == gold["tips_sha256"]
+
+
+def test_count_without_peeled_vertices_is_support_after_peeling():
+    """The identity the recount of Sec. 4.1 rests on: after any set A of one
+    side's vertices is peeled, a remaining vertex's raw support (its count
+    minus the butterflies it shares with each vertex of A, Lemma 2) equals
+    its butterfly count in the graph without A. Shared butterflies come from
+    enumerated 2x2 bicliques; the count without A from the oracle."""
+    rng = np.random.default_rng(41)
+    for eu, ev, nu, nv in _rand_graphs(120, max_u=9, max_v=8, seed=42):
+        bfs = bf.butterflies(eu, ev)
+        for side in (0, 1):
+            n = nu if side == 0 else nv
+            A = set(int(a) for a in np.nonzero(rng.random(n) < 0.4)[0])
+            full = bf.counts(eu, ev, nu, nv)[side]
+            raw = list(full)
+            for u1, u2, v1, v2 in bfs:
+                p, q = (u1, u2) if side == 0 else (v1, v2)
+                # a butterfly of two remaining vertices is never subtracted;
+                # one with a peeled vertex is subtracted once from the other
+                if p in A and q not in A:
+                    raw[q] -= 1
+                elif q in A and p not in A:
+                    raw[p] -= 1
+            ends = eu if side == 0 else ev
+            keep = np.array([int(x) not in A for x in ends], dtype=bool)
+            sub = oracle.count_2hop(eu[keep], ev[keep], nu, nv)[side]
+            for x in range(n):
+                if x not in A:
+                    assert raw[x] == int(sub[x]), (side, x)
