@@ -14,6 +14,11 @@ OpenMP for the per-vertex counting loop only):
 * ``bup``          -- Algorithm 2: sequential bottom-up peeling, with a
   monotone radix heap and the literal clamp of the support update.
 
+``wing.c`` holds the edge analogue (wing decomposition, Sec. 7):
+
+* ``edge_count``   -- butterflies of every edge by their definition;
+* ``wing_bup``     -- sequential bottom-up edge peeling with the same clamp.
+
 All functions take original-id edge lists ``(eu, ev)`` and return arrays
 indexed by original id.
 """
@@ -29,6 +34,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "wing.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -38,11 +44,11 @@ def build(force: bool = False) -> str:
     """Compile ``liboracle.so`` next to the source (gcc, -O2, OpenMP)."""
     with _lock:
         if (not force and os.path.exists(_LIB)
-                and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+                and all(os.path.getmtime(_LIB) >= os.path.getmtime(f) for f in _SRCS)):
             return _LIB
         tmp = _LIB + f".{os.getpid()}.tmp"
         cmd = ["gcc", "-O2", "-std=c11", "-D_POSIX_C_SOURCE=199309L", "-fopenmp",
-               "-shared", "-fPIC", "-o", tmp, _SRC]
+               "-shared", "-fPIC", "-o", tmp, *_SRCS]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
         return _LIB
@@ -52,6 +58,11 @@ class BupStats(ctypes.Structure):
     _fields_ = [("wedges", ctypes.c_uint64), ("peeled", ctypes.c_int64),
                 ("seconds_count", ctypes.c_double), ("seconds_peel", ctypes.c_double),
                 ("complete", ctypes.c_int64)]
+
+
+class WingStats(ctypes.Structure):
+    _fields_ = [("butterflies_visited", ctypes.c_uint64), ("edges_scanned", ctypes.c_uint64),
+                ("peeled", ctypes.c_int64), ("complete", ctypes.c_int64)]
 
 
 def _load():
@@ -73,6 +84,13 @@ def _load():
         lib.oracle_bup_from_counts.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
                                                i32p, i32p, ctypes.c_int, u64p, u64p,
                                                ctypes.c_uint64, ctypes.POINTER(BupStats)]
+        lib.oracle_edge_count.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                          i32p, i32p, i32p, i32p, u64p,
+                                          ctypes.POINTER(ctypes.c_int64)]
+        lib.oracle_wing_bup.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                        i32p, i32p, i32p, i32p, u64p,
+                                        ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(WingStats)]
         lib.oracle_num_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -155,6 +173,39 @@ def bup_from_counts(eu, ev, nu, nv, side, sup0, max_wedges: int = 0):
     return tips, {"wedges": int(st.wedges), "peeled": int(st.peeled),
                   "seconds_count": st.seconds_count, "seconds_peel": st.seconds_peel,
                   "complete": bool(st.complete)}
+
+
+def edge_count(eu, ev, nu, nv):
+    """Butterflies of every edge. Returns ``(eu, ev, cnt)`` over the
+    duplicate-free edges in ascending ``(u, v)`` order."""
+    eu, ev = _prep(eu, ev)
+    ou = np.zeros(max(1, len(eu)), np.int32)
+    ov = np.zeros(max(1, len(eu)), np.int32)
+    cnt = np.zeros(max(1, len(eu)), np.uint64)
+    mo = ctypes.c_int64(0)
+    _check(_load().oracle_edge_count(nu, nv, len(eu), eu, ev, ou, ov, _ptr(cnt),
+                                     ctypes.byref(mo)))
+    k = mo.value
+    return ou[:k], ov[:k], cnt[:k]
+
+
+def wing_bup(eu, ev, nu, nv):
+    """Wing numbers by sequential bottom-up edge peeling. Returns ``(eu, ev,
+    wing, stats)`` over the duplicate-free edges in ascending ``(u, v)``
+    order."""
+    eu, ev = _prep(eu, ev)
+    ou = np.zeros(max(1, len(eu)), np.int32)
+    ov = np.zeros(max(1, len(eu)), np.int32)
+    wing = np.zeros(max(1, len(eu)), np.uint64)
+    mo = ctypes.c_int64(0)
+    st = WingStats()
+    _check(_load().oracle_wing_bup(nu, nv, len(eu), eu, ev, ou, ov, _ptr(wing),
+                                   ctypes.byref(mo), ctypes.byref(st)))
+    k = mo.value
+    return ou[:k], ov[:k], wing[:k], {"butterflies": int(st.butterflies_visited),
+                                      "edges_scanned": int(st.edges_scanned),
+                                      "peeled": int(st.peeled),
+                                      "complete": bool(st.complete)}
 
 
 def num_threads() -> int:

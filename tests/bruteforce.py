@@ -60,3 +60,36 @@ def tip_numbers(eu, ev, nu, nv, side=0):
             if k > best[x]:
                 best[x] = k
     return best
+
+
+def edge_counts(eu, ev):
+    """Butterflies containing each edge, by enumeration: {(u, v): count}."""
+    E = set(zip((int(a) for a in eu), (int(b) for b in ev)))
+    cnt = {e: 0 for e in E}
+    for u1, u2, v1, v2 in butterflies(eu, ev):
+        for e in ((u1, v1), (u1, v2), (u2, v1), (u2, v2)):
+            cnt[e] += 1
+    return cnt
+
+
+def wing_numbers(eu, ev):
+    """Wing numbers {(u, v): k} by maximising over all edge subsets H: the
+    largest k such that e lies in some H whose every edge takes part in at
+    least k butterflies of H (the edge analogue of Definition 1; as for tips,
+    connectivity and maximality do not change the value). Tiny graphs only."""
+    E = sorted(set(zip((int(a) for a in eu), (int(b) for b in ev))))
+    idx = {e: i for i, e in enumerate(E)}
+    bfs = [tuple(idx[e] for e in ((u1, v1), (u1, v2), (u2, v1), (u2, v2)))
+           for u1, u2, v1, v2 in butterflies(eu, ev)]
+    best = [0] * len(E)
+    for mask in range(1, 1 << len(E)):
+        sup = {i: 0 for i in range(len(E)) if mask >> i & 1}
+        for b in bfs:
+            if all(mask >> i & 1 for i in b):
+                for i in b:
+                    sup[i] += 1
+        k = min(sup.values())
+        for i in sup:
+            if k > best[i]:
+                best[i] = k
+    return {e: best[i] for e, i in idx.items()}

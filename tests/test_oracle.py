@@ -235,3 +235,98 @@ def test_count_without_peeled_vertices_is_support_after_peeling():
             for x in range(n):
                 if x not in A:
                     assert raw[x] == int(sub[x]), (side, x)
+
+
+# ---------------------------------------------------------------------------
+# Wing decomposition (edge peeling, Sec. 7): per-edge counts and wing numbers
+# ---------------------------------------------------------------------------
+
+def _as_dict(ou, ov, vals):
+    return {(int(a), int(b)): int(c) for a, b, c in zip(ou, ov, vals)}
+
+
+def test_edge_counts_match_biclique_enumeration():
+    for eu, ev, nu, nv in _rand_graphs(150, max_u=9, max_v=8, seed=50):
+        ou, ov, cnt = oracle.edge_count(eu, ev, nu, nv)
+        assert _as_dict(ou, ov, cnt) == bf.edge_counts(eu, ev)
+
+
+def test_edge_counts_sum_to_vertex_counts():
+    """Each butterfly has four edges, two at each of its vertices: the edge
+    counts sum to 4x the butterflies, and over a vertex's edges to twice the
+    vertex's count."""
+    for eu, ev, nu, nv in _rand_graphs(40, max_u=40, max_v=30, seed=51):
+        ou, ov, cnt = oracle.edge_count(eu, ev, nu, nv)
+        cu, cv = oracle.count_2hop(eu, ev, nu, nv)
+        assert int(cnt.sum()) == 2 * int(cu.sum())
+        su = np.bincount(ou, weights=cnt.astype(np.float64), minlength=nu)
+        sv = np.bincount(ov, weights=cnt.astype(np.float64), minlength=nv)
+        assert (su.astype(np.uint64) == 2 * cu).all()
+        assert (sv.astype(np.uint64) == 2 * cv).all()
+
+
+def test_wing_numbers_match_subset_definition():
+    rng = np.random.default_rng(52)
+    done = 0
+    while done < 120:
+        nu, nv = int(rng.integers(2, 6)), int(rng.integers(2, 6))
+        eu, ev = synth.random_small(nu, nv, float(rng.uniform(0.4, 0.95)),
+                                    int(rng.integers(1 << 30)))
+        if len(set(zip(eu.tolist(), ev.tolist()))) > 13:
+            continue
+        ou, ov, wing, st = oracle.wing_bup(eu, ev, nu, nv)
+        assert st["complete"] and st["peeled"] == len(ou)
+        assert _as_dict(ou, ov, wing) == bf.wing_numbers(eu, ev)
+        done += 1
+
+
+@pytest.mark.parametrize("a,b", [(2, 2), (3, 5), (6, 4), (9, 2)])
+def test_wing_complete_bipartite_and_pendants(a, b):
+    eu, ev = synth.complete_bipartite(a, b)
+    ou, ov, wing, _ = oracle.wing_bup(eu, ev, a, b)
+    assert (wing == (a - 1) * (b - 1)).all()
+    _, _, cnt = oracle.edge_count(eu, ev, a, b)
+    assert (cnt == (a - 1) * (b - 1)).all()
+    # pendant U vertices on V vertex 0 and pendant V vertices on U vertex 0
+    eu2 = np.concatenate([eu, np.arange(a, a + 3, dtype=np.int32), np.zeros(2, np.int32)])
+    ev2 = np.concatenate([ev, np.zeros(3, np.int32), np.arange(b, b + 2, dtype=np.int32)])
+    ou, ov, wing, _ = oracle.wing_bup(eu2, ev2, a + 3, b + 2)
+    core = (ou < a) & (ov < b)
+    assert (wing[core] == (a - 1) * (b - 1)).all() and (wing[~core] == 0).all()
+
+
+def test_wing_bounded_by_count_transpose_and_union():
+    parts = []
+    rng = np.random.default_rng(53)
+    for g in range(4):
+        nu, nv = int(rng.integers(5, 30)), int(rng.integers(5, 25))
+        m = int(rng.integers(1, nu * nv // 2 + 1))
+        eu, ev = synth.er(nu, nv, m, int(rng.integers(1 << 30)))
+        parts.append((eu, ev, nu, nv))
+        ou, ov, wing, _ = oracle.wing_bup(eu, ev, nu, nv)
+        _, _, cnt = oracle.edge_count(eu, ev, nu, nv)
+        assert (wing <= cnt).all()
+        # transposed graph: same edges, same wing numbers
+        tv, tu, twing, _ = oracle.wing_bup(ev, eu, nv, nu)
+        assert _as_dict(ou, ov, wing) == _as_dict(tu, tv, twing)
+    ou0 = ov0 = 0
+    EU, EV, want = [], [], {}
+    for eu, ev, nu, nv in parts:
+        pu, pv, pw, _ = oracle.wing_bup(eu, ev, nu, nv)
+        want.update({(int(a) + ou0, int(b) + ov0): int(c) for a, b, c in zip(pu, pv, pw)})
+        EU.append(eu + ou0)
+        EV.append(ev + ov0)
+        ou0 += nu
+        ov0 += nv
+    wu, wv, ww, _ = oracle.wing_bup(np.concatenate(EU), np.concatenate(EV), ou0, ov0)
+    assert _as_dict(wu, wv, ww) == want
+
+
+def test_wing_forest_and_empty():
+    eu = np.zeros(6, np.int32)
+    ev = np.arange(6, dtype=np.int32)
+    ou, ov, wing, st = oracle.wing_bup(eu, ev, 1, 6)
+    assert len(ou) == 6 and (wing == 0).all() and st["butterflies"] == 0
+    e = np.zeros(0, np.int32)
+    ou, ov, wing, st = oracle.wing_bup(e, e, 3, 4)
+    assert len(ou) == 0 and st["complete"]
