@@ -1043,16 +1043,17 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
     const int grid_all = sms * std::max(occ, 1);
     // Heavy tasks (peeled first by all CTAs): task weight at least the
     // threshold. Automatic: HEAVY_SHARE times the total weight divided by
-    // min(CTAs, tasks), and at least HEAVY_MIN_W.
+    // min(CTAs, tasks), and at least HEAVY_MIN_W; with at most half as many
+    // tasks as CTAs (most CTAs would idle) the divisor is the CTA count.
     int nheavy = 0;
     if (D.fd_heavy_w >= 0 && T > 0) {
         unsigned long long thr = (unsigned long long)D.fd_heavy_w;
         if (D.fd_heavy_w == 0) {
             unsigned long long tot = 0;
             for (int k = 0; k < T; k++) tot += tw[k];
+            const int div = 2 * T <= grid_all ? grid_all : std::min(grid_all, T);
             thr = std::max<unsigned long long>(HEAVY_MIN_W,
-                                               tot / (unsigned long long)std::min(grid_all, T) *
-                                                   HEAVY_SHARE);
+                                               tot / (unsigned long long)div * HEAVY_SHARE);
         }
         std::vector<int32_t> front, back;
         for (int k = 0; k < T; k++) {
