@@ -118,8 +118,9 @@ typedef struct {
      * is the sum over all edges (u, v) of min(d_u, d_v), the round
      * recounts the butterflies of the remaining subgraph (Algorithm 1 with
      * every assigned vertex removed) instead of applying the activeSet's
-     * updates. huc: 0 = that rule, -1 = never, 1 = recount the first
-     * round of every range (test hook). huc_factor_1024: the factor in
+     * updates (when free device memory holds the recount's temporaries).
+     * huc: 0 = that rule, -1 = never, 1 = recount the first round of every
+     * range (test hook). huc_factor_1024: the factor in
      * 1/1024 units (0 = 8192, i.e. 8; 1024 is the paper's rule C_peel >
      * C_rcnt). Speed only; results are the same. */
     int32_t huc;

@@ -1173,8 +1173,10 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
         if (hst->n_remaining == 0) break;  // nothing remains
         if (range == 0) crcnt = hpin[0];
         D.cost_recount = crcnt;
+        // the rule also skips a recount whose temporaries would not fit
         bool recount = huc == 1 || (huc == 0 && crcnt > 0 &&
-                                    (double)hst->front_w >= huc_factor * (double)crcnt);
+                                    (double)hst->front_w >= huc_factor * (double)crcnt &&
+                                    recount_fits(D));
         for (;;) {
             if (recount) {
                 huc_round(abuf[parity], abuf[parity ^ 1]);

@@ -19,6 +19,8 @@
 // Cost model of the rule (Sec. 4.1): peeling an activeSet walks the sum over
 // its vertices x of sum_{y in N_x} d_y wedges; a count walks at most
 // C_rcnt = sum over edges (x, y) of min(d_x, d_y).
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace receipt {
@@ -127,6 +129,22 @@ void launch_recount_cost(const Side &S, const Side &O, int64_t m, unsigned long 
     if (m == 0 || S.n == 0) return;
     k_rcnt_cost<<<chunk_blocks(m), 256, 0, s>>>(S.off, S.n, S.adj, O.off, m, d_out);
     RC_LAUNCH();
+}
+
+bool recount_fits(const Decomp &D) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    // the subgraph's lists and offsets, the counts, the counting pass's
+    // temporaries (prefix lengths and scans, tier lists, the global tier's
+    // per-CTA counters) and a copy of the other side's lists
+    const size_t n_all = (size_t)D.S->n + (size_t)D.O->n;
+    const size_t n_max = (size_t)std::max(D.S->n, D.O->n);
+    const size_t need = 40 * (size_t)D.m + 48 * n_all + 8 * (size_t)num_sms() * n_max +
+                        ((size_t)64 << 20);
+    return need <= fr;
 }
 
 uint64_t recount_remaining(const Decomp &D, const int32_t *len_w, const int32_t *adj_w,

@@ -85,6 +85,8 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s);
 // over the edges (x, y) of min(d_x, d_y).
 void launch_recount_cost(const Side &S, const Side &O, int64_t m, unsigned long long *d_out,
                          cudaStream_t s);
+// Whether free device memory holds a recount's temporaries (upper estimate).
+bool recount_fits(const Decomp &D);
 // Recounts the butterflies of the subgraph left after removing every vertex
 // with D.sub >= 0 and stores each remaining vertex's count in D.sup.
 // len_w/adj_w: the other side's lists (original offsets) already compacted
