@@ -270,16 +270,26 @@ def run_ours(args):
     value = replica_rate(wedges, world, ms / 1e3)
     tips = R.as_u64(tip)
 
-    # end to end through the C ABI with host buffers
+    # end to end through the C ABI with host buffers, with the options the
+    # device-timed steps used (the shape class's tuned values)
+    from paper_2010_08695_gb300 import autotune
+    g0 = R.Graph(eu_d, ev_d, nu, nv, stream=stream)
+    tuned = autotune.lookup(g0.shape_class(side)) or {}
+    g0.close()
+    e2e_opt = {"warp_max_w": tuned.get("warp_max_w", 0),
+               "slice_min_w": tuned.get("slice_min_w", 0),
+               "dgm_frac_1024": tuned.get("dgm_frac_1024", 0), "huc": args.huc,
+               "huc_factor_1024": args.huc_factor_1024, "round_graphs": args.round_graphs}
+    e2e_P = args.P or tuned.get("P", 150)
     eu_h = torch.from_numpy(eu).pin_memory().numpy()
     ev_h = torch.from_numpy(ev).pin_memory().numpy()
     tip_h = torch.empty(n_side, dtype=torch.int64).pin_memory().numpy().view(np.uint64)
-    R.receipt_tip_decompose_host(eu_h, ev_h, nu, nv, side, out=tip_h)
+    R.receipt_tip_decompose_host(eu_h, ev_h, nu, nv, side, P=e2e_P, out=tip_h, **e2e_opt)
     e2e_t = []
     for _ in range(max(1, min(args.steps, 3))):
         barrier()
         t0 = time.perf_counter()
-        R.receipt_tip_decompose_host(eu_h, ev_h, nu, nv, side, out=tip_h)
+        R.receipt_tip_decompose_host(eu_h, ev_h, nu, nv, side, P=e2e_P, out=tip_h, **e2e_opt)
         e2e_t.append(time.perf_counter() - t0)
     e2e_s = max_over_ranks(statistics.mean(e2e_t), dist, dev)
     e2e_ok = bool(np.array_equal(tip_h, tips))
@@ -312,10 +322,6 @@ def run_ours(args):
         gold = json.load(open(gpath))
         gold_ok = hashlib.sha256(tips.astype("<u8").tobytes()).hexdigest() == gold["tips_sha256"]
 
-    from paper_2010_08695_gb300 import autotune
-    g0 = R.Graph(eu_d, ev_d, nu, nv, stream=stream)
-    tuned = autotune.lookup(g0.shape_class(side)) or {}
-    g0.close()
     line = {"metric": METRIC, "value": value, "unit": "wedges/s", "n_gpus": world,
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",

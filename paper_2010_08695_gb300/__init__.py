@@ -385,13 +385,16 @@ def receipt_decompose_batch(graphs, sides, outs=None, P: int = 150, stream=None,
 
 
 def receipt_tip_decompose_host(eu, ev, nu: int, nv: int, side: int, P: int = 150, stream=None,
-                               out=None):
-    """End to end over host buffers: copies in, builds, decomposes, copies out."""
+                               out=None, **options):
+    """End to end over host buffers: copies in, builds, decomposes, copies out.
+    ``options`` are the keyword options of ``Graph.tip_decompose`` that only
+    change speed (warp_max_w, slice_min_w, dgm, dgm_frac_1024, fd_heavy_w,
+    round_graphs, huc, huc_factor_1024)."""
     eu = np.ascontiguousarray(eu, dtype=np.int32)
     ev = np.ascontiguousarray(ev, dtype=np.int32)
     n = nu if side == SIDE_U else nv
     tip = out if out is not None else np.zeros(n, np.uint64)
-    o, keep = _options(P)
+    o, keep = _options(P, **options)
     _check(load().receipt_tip_decompose_host(eu.ctypes.data_as(ctypes.c_void_p),
                                              ev.ctypes.data_as(ctypes.c_void_p), len(eu), int(nu),
                                              int(nv), int(side), tip.ctypes.data_as(ctypes.c_void_p),
