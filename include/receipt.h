@@ -114,7 +114,7 @@ typedef struct {
     int32_t round_graphs;
     /* Hybrid update computation (Sec. 4.1). When the first activeSet of a
      * range of Algorithm 3 carries C_peel wedges (sum over its vertices x
-     * of sum_{y in N_x} d_y) and C_peel >= factor * C_rcnt, where C_rcnt
+     * of sum_{y in N_x} d_y) and C_peel > factor * C_rcnt, where C_rcnt
      * is the sum over all edges (u, v) of min(d_u, d_v), the round
      * recounts the butterflies of the remaining subgraph (Algorithm 1 with
      * every assigned vertex removed) instead of applying the activeSet's

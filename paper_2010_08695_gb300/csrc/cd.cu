@@ -37,7 +37,7 @@ constexpr int NBUCKET = LOG_BUCKETS;
 constexpr int NTIER = 5;  // warp, hybrid, global, sliced, dense window
 constexpr double DGM_FRAC = 0.125;  // stale share of live entries that triggers a compaction
 // A range's first round recounts instead of peeling when its activeSet's
-// wedges reach HUC_FACTOR * C_rcnt: per unit of the two cost measures the
+// wedges exceed HUC_FACTOR * C_rcnt: per unit of the two cost measures the
 // peel tiers run 4-10 times faster than the counting kernels (measured on
 // Chung-Lu graphs of 10M and 100M edges).
 constexpr double HUC_FACTOR = 8.0;
@@ -1175,7 +1175,7 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
         D.cost_recount = crcnt;
         // the rule also skips a recount whose temporaries would not fit
         bool recount = huc == 1 || (huc == 0 && crcnt > 0 &&
-                                    (double)hst->front_w >= huc_factor * (double)crcnt &&
+                                    (double)hst->front_w > huc_factor * (double)crcnt &&
                                     recount_fits(D));
         for (;;) {
             if (recount) {
