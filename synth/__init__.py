@@ -82,15 +82,60 @@ def chung_lu_i0_for_max(n: int, gamma: float, m: int, dmax: float) -> float:
     return hi
 
 
+# Above this many draws the inverse-CDF search and the distinct-edge
+# bookkeeping of ``chung_lu`` run on torch's multi-threaded CPU sort and
+# search (exact comparisons: the same results as numpy's).
+_TORCH_MIN_DRAWS = 1 << 20
+
+
 def _draw(cdf: np.ndarray, rng: np.random.Generator, k: int) -> np.ndarray:
     r = rng.random(k)
-    idx = np.searchsorted(cdf, r, side="right")
+    if k >= _TORCH_MIN_DRAWS:
+        import torch
+        idx = torch.searchsorted(torch.from_numpy(cdf), torch.from_numpy(r), right=True).numpy()
+    else:
+        idx = np.searchsorted(cdf, r, side="right")
     return np.minimum(idx, len(cdf) - 1).astype(np.int64)
+
+
+def _first_new(keys_sorted, cand):
+    """Positions (ascending) of the first occurrence of every value of `cand`
+    that is absent from all the sorted arrays in `keys_sorted`."""
+    if len(cand) >= _TORCH_MIN_DRAWS:
+        import torch
+        c = torch.from_numpy(cand)
+        fresh = torch.ones(len(c), dtype=torch.bool)
+        for ks in keys_sorted:
+            if len(ks) == 0:
+                continue
+            t = torch.from_numpy(ks)
+            pos = torch.clamp_max(torch.searchsorted(t, c), len(t) - 1)
+            fresh &= t[pos] != c
+        idx = torch.nonzero(fresh).flatten()
+        sk, perm = torch.sort(c[idx], stable=True)
+        first = torch.ones(len(sk), dtype=torch.bool)
+        first[1:] = sk[1:] != sk[:-1]
+        out, _ = torch.sort(idx[perm[first]])
+        return out.numpy()
+    fresh = np.ones(len(cand), dtype=bool)
+    for ks in keys_sorted:
+        if len(ks) == 0:
+            continue
+        pos = np.minimum(np.searchsorted(ks, cand), len(ks) - 1)
+        fresh &= ks[pos] != cand
+    idx = np.nonzero(fresh)[0]
+    _, first = np.unique(cand[idx], return_index=True)
+    return np.sort(idx[first])
 
 
 def chung_lu(nu: int, nv: int, m: int, gamma_u: float, gamma_v: float,
              seed: int, i0_u: float = 1.0, i0_v: float = 1.0):
-    """Chung-Lu bipartite graph with exactly ``m`` distinct edges."""
+    """Chung-Lu bipartite graph with exactly ``m`` distinct edges.
+
+    Rounds of independent endpoint draws (inverse CDF) continue until ``m``
+    distinct edges exist; the graph is the first ``m`` distinct edges in draw
+    order. Each round only checks its own draws against the edges kept so
+    far (kept as sorted runs), so a round costs its own size."""
     if m > nu * nv:
         raise ValueError("more edges than cells")
     rng = np.random.default_rng(seed)
@@ -98,20 +143,22 @@ def chung_lu(nu: int, nv: int, m: int, gamma_u: float, gamma_v: float,
     cv = np.cumsum(_probs(nv, gamma_v, i0_v, m, nu))
     cu /= cu[-1]
     cv /= cv[-1]
-    keys = np.empty(0, dtype=np.int64)
+    parts, runs, have = [], [], 0
     for _ in range(1000):
-        need = m - len(keys)
+        need = m - have
         if need <= 0:
             break
         k = int(need * 1.15) + 1024
         u = _draw(cu, rng, k)
         v = _draw(cv, rng, k)
-        allk = np.concatenate([keys, u * nv + v])
-        _, first = np.unique(allk, return_index=True)
-        first.sort()
-        keys = allk[first[:m]]
-    if len(keys) < m:
+        cand = u * nv + v
+        new = cand[_first_new(runs, cand)[:need]]
+        parts.append(new)
+        runs.append(np.sort(new))
+        have += len(new)
+    if have < m:
         raise RuntimeError("could not draw enough distinct edges")
+    keys = np.concatenate(parts) if parts else np.empty(0, dtype=np.int64)
     return (keys // nv).astype(np.int32), (keys % nv).astype(np.int32)
 
 
