@@ -10,7 +10,8 @@ OpenMP for the per-vertex counting loop only):
 * ``count_2hop``   -- butterflies per vertex by their definition
   (sum over same-side x' of C(common neighbours, 2)), both sides;
 * ``count_vp``     -- Algorithm 1 (pvBcnt), an independent cross-check;
-* ``count_vertex`` -- the same definition for a list of vertices;
+* ``count_vertex`` -- the same definition for a list of vertices
+  (``Graph.count_vertex`` on adjacency built once);
 * ``bup``          -- Algorithm 2: sequential bottom-up peeling, with a
   monotone radix heap and the literal clamp of the support update.
 
@@ -91,6 +92,13 @@ def _load():
                                         i32p, i32p, i32p, i32p, u64p,
                                         ctypes.POINTER(ctypes.c_int64),
                                         ctypes.POINTER(WingStats)]
+        lib.oracle_graph_new.restype = ctypes.c_void_p
+        lib.oracle_graph_new.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, i32p,
+                                         i32p, ctypes.POINTER(ctypes.c_int)]
+        lib.oracle_graph_count_vertex.argtypes = [ctypes.c_void_p, ctypes.c_int, i32p,
+                                                  ctypes.c_int64, u64p,
+                                                  ctypes.POINTER(ctypes.c_uint64)]
+        lib.oracle_graph_free.argtypes = [ctypes.c_void_p]
         lib.oracle_num_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -139,6 +147,39 @@ def count_vertex(eu, ev, nu, nv, side, xs):
     _check(_load().oracle_count_vertex(nu, nv, len(eu), eu, ev, int(side), xs, len(xs),
                                        _ptr(out)))
     return out
+
+
+class Graph:
+    """Adjacency of both sides built once, for repeated ``count_vertex``
+    calls (e.g. a timed sample of vertices) without rebuilding it."""
+
+    def __init__(self, eu, ev, nu, nv):
+        eu, ev = _prep(eu, ev)
+        rc = ctypes.c_int(0)
+        self._h = _load().oracle_graph_new(nu, nv, len(eu), eu, ev, ctypes.byref(rc))
+        _check(rc.value)
+        self.nu, self.nv = nu, nv
+
+    def count_vertex(self, side, xs):
+        """``(counts, walked)``: butterflies of the listed vertices of ``side``
+        and the 2-hop entries visited (sum over y in N_x of d_y)."""
+        xs = np.ascontiguousarray(xs, dtype=np.int32)
+        out = np.zeros(len(xs), np.uint64)
+        walked = ctypes.c_uint64(0)
+        _check(_load().oracle_graph_count_vertex(self._h, int(side), xs, len(xs), _ptr(out),
+                                                 ctypes.byref(walked)))
+        return out, int(walked.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _load().oracle_graph_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def bup(eu, ev, nu, nv, side, max_wedges: int = 0):

@@ -13,9 +13,10 @@
  *                            i.e. sum over same-side x' of C(|N_x n N_x'|, 2).
  *   oracle_count_vp       -- Algorithm 1 (pvBcnt), the vertex-priority counter,
  *                            written independently as a cross-check.
- *   oracle_count_vertex   -- one vertex's count by the definition (used to
- *                            sample outputs of graphs too large for the
- *                            full oracle).
+ *   oracle_count_vertex   -- listed vertices' counts by the definition (used
+ *                            to sample outputs of graphs too large for the
+ *                            full oracle); oracle_graph_* keep the adjacency
+ *                            built between such calls.
  *   oracle_bup            -- Algorithm 2 (BUP): sequential bottom-up peeling
  *                            with the update of Algorithm 2 (support of every
  *                            2-hop neighbour u' drops by C(wdg[u'],2), clamped
@@ -53,11 +54,6 @@ typedef struct {
     int32_t *adj;   /* ids of the other side */
 } side_adj;
 
-static int cmp_u64(const void *a, const void *b) {
-    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
-    return (x > y) - (x < y);
-}
-
 static void free_side(side_adj *s) {
     free(s->off);
     free(s->adj);
@@ -65,36 +61,41 @@ static void free_side(side_adj *s) {
     s->adj = NULL;
 }
 
-/* Sort (a, b) pairs, drop duplicates and write the CSR of side "a". */
+static int cmp_i32(const void *a, const void *b) {
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* CSR of side "a" from the (a, b) pairs: place every b in its a's list
+ * (counting by a), sort each list, drop repeated entries. */
 static int build_side(int64_t na, int64_t nb, int64_t m, const int32_t *ea,
                       const int32_t *eb, side_adj *out) {
-    uint64_t *key = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(m > 0 ? m : 1));
-    if (!key) return ORC_ENOMEM;
-    for (int64_t i = 0; i < m; i++) {
-        if (ea[i] < 0 || ea[i] >= na || eb[i] < 0 || eb[i] >= nb) {
-            free(key);
-            return ORC_EINVAL;
-        }
-        key[i] = ((uint64_t)(uint32_t)ea[i] << 32) | (uint32_t)eb[i];
-    }
-    qsort(key, (size_t)m, sizeof(uint64_t), cmp_u64);
-    int64_t k = 0;
     for (int64_t i = 0; i < m; i++)
-        if (i == 0 || key[i] != key[i - 1]) key[k++] = key[i];
+        if (ea[i] < 0 || ea[i] >= na || eb[i] < 0 || eb[i] >= nb) return ORC_EINVAL;
     out->n = na;
     out->off = (int64_t *)calloc((size_t)na + 1, sizeof(int64_t));
-    out->adj = (int32_t *)malloc(sizeof(int32_t) * (size_t)(k > 0 ? k : 1));
-    if (!out->off || !out->adj) {
-        free(key);
+    out->adj = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+    int64_t *pos = (int64_t *)malloc(sizeof(int64_t) * (size_t)(na > 0 ? na : 1));
+    if (!out->off || !out->adj || !pos) {
+        free(pos);
         free_side(out);
         return ORC_ENOMEM;
     }
-    for (int64_t i = 0; i < k; i++) {
-        out->off[(key[i] >> 32) + 1]++;
-        out->adj[i] = (int32_t)(key[i] & 0xffffffffu);
-    }
+    for (int64_t i = 0; i < m; i++) out->off[ea[i] + 1]++;
     for (int64_t a = 0; a < na; a++) out->off[a + 1] += out->off[a];
-    free(key);
+    for (int64_t a = 0; a < na; a++) pos[a] = out->off[a];
+    for (int64_t i = 0; i < m; i++) out->adj[pos[ea[i]]++] = eb[i];
+    free(pos);
+    /* sort every list and keep one copy of each entry, compacting in place */
+    int64_t k = 0;
+    for (int64_t a = 0; a < na; a++) {
+        const int64_t b0 = out->off[a], b1 = out->off[a + 1];
+        qsort(out->adj + b0, (size_t)(b1 - b0), sizeof(int32_t), cmp_i32);
+        out->off[a] = k;
+        for (int64_t i = b0; i < b1; i++)
+            if (i == b0 || out->adj[i] != out->adj[i - 1]) out->adj[k++] = out->adj[i];
+    }
+    out->off[na] = k;
     return ORC_OK;
 }
 
@@ -166,14 +167,12 @@ int oracle_count_2hop(int32_t nu, int32_t nv, int64_t m, const int32_t *eu,
     return rc;
 }
 
-/* One vertex x of side `side` (0 = U, 1 = V), by the same definition. */
-int oracle_count_vertex(int32_t nu, int32_t nv, int64_t m, const int32_t *eu,
-                        const int32_t *ev, int side, const int32_t *xs, int64_t nx,
-                        uint64_t *out) {
-    side_adj U, V;
-    int rc = build_both(nu, nv, m, eu, ev, &U, &V);
-    if (rc) return rc;
-    const side_adj *S = side ? &V : &U, *O = side ? &U : &V;
+/* The listed vertices xs[0..nx) of side S, by the same definition;
+ * *walked receives the 2-hop entries visited (sum over y in N_x of d_y). */
+static int count_listed(const side_adj *S, const side_adj *O, const int32_t *xs, int64_t nx,
+                        uint64_t *out, uint64_t *walked) {
+    int rc = ORC_OK;
+    uint64_t w = 0;
     uint32_t *c = (uint32_t *)calloc((size_t)(S->n > 0 ? S->n : 1), sizeof(uint32_t));
     int32_t *touched = (int32_t *)malloc(sizeof(int32_t) * (size_t)(S->n > 0 ? S->n : 1));
     if (!c || !touched) rc = ORC_ENOMEM;
@@ -186,6 +185,7 @@ int oracle_count_vertex(int32_t nu, int32_t nv, int64_t m, const int32_t *eu,
         int64_t nt = 0;
         for (int64_t i = S->off[x]; i < S->off[x + 1]; i++) {
             int32_t y = S->adj[i];
+            w += (uint64_t)(O->off[y + 1] - O->off[y]);
             for (int64_t j = O->off[y]; j < O->off[y + 1]; j++) {
                 int32_t xp = O->adj[j];
                 if (xp == x) continue;
@@ -201,9 +201,57 @@ int oracle_count_vertex(int32_t nu, int32_t nv, int64_t m, const int32_t *eu,
     }
     free(c);
     free(touched);
+    if (walked) *walked = w;
+    return rc;
+}
+
+/* Vertices x of side `side` (0 = U, 1 = V), by the same definition. */
+int oracle_count_vertex(int32_t nu, int32_t nv, int64_t m, const int32_t *eu,
+                        const int32_t *ev, int side, const int32_t *xs, int64_t nx,
+                        uint64_t *out) {
+    side_adj U, V;
+    int rc = build_both(nu, nv, m, eu, ev, &U, &V);
+    if (rc) return rc;
+    rc = count_listed(side ? &V : &U, side ? &U : &V, xs, nx, out, NULL);
     free_side(&U);
     free_side(&V);
     return rc;
+}
+
+/* The same count on a graph whose adjacency is built once and kept, so that
+ * repeated calls (a timed sample of vertices) do not rebuild it. */
+typedef struct {
+    side_adj U, V;
+} oracle_graph;
+
+void *oracle_graph_new(int32_t nu, int32_t nv, int64_t m, const int32_t *eu, const int32_t *ev,
+                       int *rc) {
+    oracle_graph *g = (oracle_graph *)calloc(1, sizeof(oracle_graph));
+    if (!g) {
+        *rc = ORC_ENOMEM;
+        return NULL;
+    }
+    *rc = build_both(nu, nv, m, eu, ev, &g->U, &g->V);
+    if (*rc) {
+        free(g);
+        return NULL;
+    }
+    return g;
+}
+
+int oracle_graph_count_vertex(void *h, int side, const int32_t *xs, int64_t nx, uint64_t *out,
+                              uint64_t *walked) {
+    oracle_graph *g = (oracle_graph *)h;
+    if (!g) return ORC_EINVAL;
+    return count_listed(side ? &g->V : &g->U, side ? &g->U : &g->V, xs, nx, out, walked);
+}
+
+void oracle_graph_free(void *h) {
+    oracle_graph *g = (oracle_graph *)h;
+    if (!g) return;
+    free_side(&g->U);
+    free_side(&g->V);
+    free(g);
 }
 
 /* ------------------------------------------------------------------ */
@@ -221,11 +269,6 @@ static int cmp_vkey(const void *a, const void *b) {
     if (x->deg != y->deg) return x->deg > y->deg ? -1 : 1; /* descending degree */
     if (x->side != y->side) return x->side < y->side ? -1 : 1;
     return (x->id > y->id) - (x->id < y->id);
-}
-
-static int cmp_i32(const void *a, const void *b) {
-    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
-    return (x > y) - (x < y);
 }
 
 int oracle_count_vp(int32_t nu, int32_t nv, int64_t m, const int32_t *eu,

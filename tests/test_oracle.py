@@ -152,6 +152,18 @@ def test_chung_lu_counting_paths_agree():
     cu, cv = oracle.count_2hop(eu, ev, 3000, 800)
     vu, vv = oracle.count_vp(eu, ev, 3000, 800)
     assert (cu == vu).all() and (cv == vv).all()
+    # listed vertices on adjacency built once: same counts, and the walk
+    # visits sum_{y in N_x} d_y entries per vertex
+    g = oracle.Graph(eu, ev, 3000, 800)
+    du = np.bincount(eu, minlength=3000)
+    dv = np.bincount(ev, minlength=800)
+    for side, c, n in ((0, cu, 3000), (1, cv, 800)):
+        xs = np.random.default_rng(side).choice(n, 50, replace=False).astype(np.int32)
+        got, walked = g.count_vertex(side, xs)
+        assert (got == c[xs]).all()
+        a, b, d_o = (eu, ev, dv) if side == 0 else (ev, eu, du)
+        assert walked == sum(int(d_o[b[a == x]].sum()) for x in xs)
+    g.close()
 
 
 def test_duplicates_and_edge_cases():
