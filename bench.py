@@ -1,30 +1,44 @@
 #!/usr/bin/env python
 """Benchmark of RECEIPT tip decomposition on one GB300.
 
-Workload: the Chung-Lu bipartite graph with |U| = 1,000,000, |V| = 200,000,
-10,000,000 distinct edges, U-degree exponent 2.5 and V-degree exponent 2.1
-(largest expected V degree 50,000), seed 2; the U side is decomposed.
+Headline workload: the Chung-Lu bipartite graph with |U| = 5,000,000,
+|V| = 1,000,000, 100,000,000 distinct edges, exponent 2.0 on both sides
+(largest expected degree 500,000 on both; drawn: 193k on U, 254k on V),
+seed 3; the V side is decomposed (wedges through U, ~1.06e12 bottom-up
+wedges). It is the largest single-GPU workload of the method's
+configurations.
 
 One step = one whole pass of the hot path on the device: graph build
 (deduplication, degree relabelling, two-sided CSR), per-vertex butterfly
 counting (Algorithm 1), coarse-grained range peeling (Algorithm 3) and
 fine-grained subset peeling (Algorithm 4), from an edge list already in HBM
-to tip numbers in HBM.
+to tip numbers in HBM. The timed steps run without any instrumentation;
+two further steps with per-tier CUDA events give the phase split and the
+roofline of the dominant peel kernel.
 
 Metric: wedges/s, where the wedge count of a step is the graph's bottom-up
-peeling wedge count sum_{v in V} d_v (d_v - 1) (the work Algorithm 2 does; a
-property of the graph, the same for every implementation), divided by the
-step's device time. Seconds per step, the wedges the kernels actually walked
-and the roofline fraction of the dominant kernel are reported beside it.
+peeling wedge count sum_{y in other side} d_y (d_y - 1) (the work
+Algorithm 2 does; a property of the graph, the same for every
+implementation), divided by the step's device time. Seconds per step, the
+wedges the kernels actually walked and the roofline fraction of the
+dominant kernel are reported beside it.
+
+The same JSON line carries (N = 1, unless --no-extras): the 10M-edge
+Chung-Lu workload (U side) as a secondary measurement, the 4,096-graph batch
+(one packed call against one call per graph) and the first 200 requests of
+the seed-5 serving stream (p50/p99 latency, graphs/s).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload chung-lu-5Mx1M-100M|chung-lu-1Mx200k-10M|batch|serve]
 
 With N > 1 (torchrun, one rank per GPU) every rank decomposes its own copy of
 the graph (the path has no exchange step: replicas only); the value is the
 wedges of all ranks divided by the slowest rank's time.
 
---impl reference times the CPU oracle (sequential bottom-up peeling, test
-infrastructure) on a bounded sample of the same workload on the host cores.
+--impl reference times the CPU oracle (test infrastructure) on the host
+cores: its per-vertex butterfly count by definition (the 2-hop walk every
+peeled vertex makes in Algorithm 2) over a seeded sample of the decomposed
+side's vertices of the same workload, each step a bounded sample.
 """
 from __future__ import annotations
 
@@ -44,15 +58,24 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "wedges/s and end-to-end tip-decomp seconds on 1 GB300 (bit-exact); HBM roofline frac"
-WORKLOAD = "chung-lu |U|=1M |V|=200k m=10M gamma 2.5/2.1 seed 2, U side"
-CPU_SAMPLE_WEDGES = 1_500_000_000  # peel wedges per oracle sample (~10-20 s on one core)
+HEADLINE = "chung-lu-5Mx1M-100M"
+SECONDARY = "chung-lu-1Mx200k-10M"
+DESCR = {
+    "chung-lu-5Mx1M-100M": "chung-lu |U|=5M |V|=1M m=100M gamma 2.0/2.0 seed 3, V side",
+    "chung-lu-1Mx200k-10M": "chung-lu |U|=1M |V|=200k m=10M gamma 2.5/2.1 seed 2, U side",
+}
+CPU_SAMPLE_WEDGES = 2_500_000_000  # oracle walk per CPU-baseline sample (~10 s on one core)
+REF_STEP_WEDGES = 800_000_000      # oracle walk per reference-arm step (~3-4 s)
+SERVE_PREFIX = 200
 
-# DRAM traffic of the dominant kernel from one full-size ncu capture, as DRAM
-# bytes per algorithmic byte of the captured launch (scaled to the average
-# launch of the timed step), keyed by kernel name; valid only while the peel
-# kernels' sources (PEEL_SOURCES) hash to the recorded digest. k_cd_update_cta: CD round 4 of the
-# 10M-edge Chung-Lu workload, 49.26 MB of DRAM for ~971 MB algorithmic.
-NCU_TRAFFIC = {"k_cd_update_cta": {"src": "c1a903e285db3254", "dram_per_alg_byte": 0.0507}}
+# DRAM traffic of a peel kernel from one ncu capture, as DRAM bytes per
+# algorithmic byte of the captured launch (scaled to the average launch of
+# the step), keyed by kernel name; valid only while the peel kernels'
+# sources (PEEL_SOURCES) hash to the recorded digest.
+NCU_TRAFFIC = {}
+
+PEEL_TIERS = ["k_cd_update_warp", "k_cd_update_cta", "k_cd_update_global", "k_cd_update_slice",
+              "k_cd_update_dense"]
 
 
 def max_over_ranks(x: float, dist=None, device="cpu") -> float:
@@ -148,77 +171,54 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
-def load_workload():
+def load_workload(name):
     import synth
-    eu, ev, nu, nv, side = synth.workload_graph(synth.CHUNG_LU_10M)
-    dv = np.bincount(ev, minlength=nv).astype(np.int64)
-    du = np.bincount(eu, minlength=nu).astype(np.int64)
-    d_other = dv if side == 0 else du
-    wedges = int((d_other * (d_other - 1)).sum())
+    eu, ev, nu, nv, side = synth.workload_graph(name)
+    d = np.bincount(ev if side == 0 else eu, minlength=nv if side == 0 else nu).astype(np.int64)
+    wedges = int((d * (d - 1)).sum())
     return eu, ev, nu, nv, side, wedges
 
 
-def cpu_baseline(eu, ev, nu, nv, side, sample_wedges=CPU_SAMPLE_WEDGES, counts=None):
-    """Oracle on a bounded sample: sequential bottom-up peeling of the same
-    graph from its exact initial supports, stopped after `sample_wedges`."""
-    import oracle
-    t0 = time.perf_counter()
-    if counts is None:
-        counts = oracle.count_2hop(eu, ev, nu, nv)[side]
-    t_count = time.perf_counter() - t0
-    _, st = oracle.bup_from_counts(eu, ev, nu, nv, side, counts, max_wedges=sample_wedges)
-    rate = st["wedges"] / st["seconds_peel"] if st["seconds_peel"] > 0 else 0.0
-    return {"value": rate, "unit": "wedges/s", "cores": 1, "kind": "oracle",
-            "sample": (f"sequential bottom-up peel (Algorithm 2, radix heap) of the benchmark "
-                       f"graph from its exact initial supports, stopped after {st['wedges']} "
-                       f"wedges / {st['peeled']} vertices in {st['seconds_peel']:.1f} s on one "
-                       f"core; the initial support count took {t_count:.1f} s on "
-                       f"{oracle.num_threads()} OpenMP threads and is not in the rate")}, counts
+def roofline(st, peak, peak_kind):
+    """Roofline of the peel tier with the most device time in the
+    instrumented step(s): algorithmic bytes per launch (4 B per wedge walked,
+    16 B per middle-vertex visit, 16 B per support atomic, 24 B per anchor)
+    over the tier's average launch time."""
+    tier = max(range(5), key=lambda t: st["ms_peel"][t])
+    lau = max(1, st["peel_launches"][tier])
+    alg_bytes = (4 * st["peel_wedges"][tier] + 16 * st["peel_mids"][tier]
+                 + 16 * st["peel_pairs"][tier] + 24 * st["peel_anchors"][tier]) / lau
+    dur_s = st["ms_peel"][tier] / 1e3 / lau
+    achieved = alg_bytes / dur_s / 1e9 if dur_s > 0 else 0.0
+    traffic = None
+    tr = NCU_TRAFFIC.get(PEEL_TIERS[tier])
+    if tr and tr.get("src") == _src_digest():
+        traffic = int(tr["dram_per_alg_byte"] * alg_bytes)
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "kernel": PEEL_TIERS[tier],
+            "peak_source": peak_kind, "bytes_per_launch": alg_bytes, "launch_ms": dur_s * 1e3,
+            "launches": lau, "bytes_model": "4 B/wedge + 16 B/mid + 16 B/pair + 24 B/anchor"}
 
 
-def run_reference(args):
-    rank, world, _ = _rank_env()
-    if rank != 0:
-        return 0
-    import oracle
-    eu, ev, nu, nv, side, wedges = load_workload()
-    counts = oracle.count_2hop(eu, ev, nu, nv)[side]
-    sample = max(1, CPU_SAMPLE_WEDGES // 3)
-    for _ in range(args.warmup):
-        oracle.bup_from_counts(eu, ev, nu, nv, side, counts, max_wedges=sample // 10)
-    rates, secs = [], []
-    for _ in range(args.steps):
-        _, st = oracle.bup_from_counts(eu, ev, nu, nv, side, counts, max_wedges=sample)
-        rates.append(st["wedges"] / st["seconds_peel"])
-        secs.append(st["seconds_peel"])
-    value = statistics.mean(rates)
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "wedges/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nu": nu, "nv": nv, "m": int(len(eu)),
-                       "side": "U", "wedges_bup": wedges,
-                       "sample": f"{sample} peel wedges per step"},
-            "cpu_baseline": {"value": value, "unit": "wedges/s", "cores": 1, "kind": "oracle",
-                             "sample": f"sequential bottom-up peel of the benchmark graph from "
-                                       f"its exact initial supports, {sample} wedges per step"},
-            "e2e": {"value": value, "unit": "wedges/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
-    return 0
+def _mean_stats(stats):
+    """Field-wise mean of instrumented steps' stats (lists element-wise)."""
+    out = {}
+    for k in stats[0]:
+        v = [s[k] for s in stats]
+        if isinstance(v[0], list):
+            out[k] = [sum(x) / len(x) for x in zip(*v)]
+        else:
+            out[k] = sum(v) / len(v)
+    return out
 
 
-def run_ours(args):
+def measure_graph(R, name, args, dist=None, world=1, local=0, clocks=True, e2e=True,
+                  roofline_steps=2):
+    """Times `steps` uninstrumented device steps of the named workload (after
+    `warmup`), then `roofline_steps` instrumented ones, then the end-to-end
+    leg through the host-buffer entry point. Returns the measurement dict."""
     import torch
-    rank, world, local = _rank_env()
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    import paper_2010_08695_gb300 as R
-    R.load()
-    eu, ev, nu, nv, side, wedges = load_workload()
+    eu, ev, nu, nv, side, wedges = load_workload(name)
     n_side = nu if side == 0 else nv
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
@@ -226,147 +226,209 @@ def run_ours(args):
     ev_d = torch.from_numpy(ev).to(dev)
     tip = torch.empty(n_side, dtype=torch.int64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    from paper_2010_08695_gb300 import autotune
+    g0 = R.Graph(eu_d, ev_d, nu, nv, stream=stream)
+    tuned = autotune.lookup(g0.shape_class(side)) or {}
+    g0.close()
+    P = args.P or tuned.get("P", 150)
 
     def barrier():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
 
-    last_trace = []
+    trace = []
 
     def step(timing):
         g = R.Graph(eu_d, ev_d, nu, nv, stream=stream)
-        g.tip_decompose(side, P=args.P, timing=timing, out=tip, stream=stream,
+        g.tip_decompose(side, P=P, timing=timing, out=tip, stream=stream,
                         round_graphs=args.round_graphs, huc=args.huc,
                         huc_factor_1024=args.huc_factor_1024)
-        st = g.stats()
-        if args.trace:
-            last_trace[:] = g.trace()
+        st = g.stats() if timing else None
+        if timing and args.trace:
+            trace[:] = g.trace()
         g.close()
         return st
 
     for _ in range(max(3, args.warmup)):
-        step(True)
+        step(False)
     barrier()
-    times, stats = [], []
+    times = []
     launches0 = R.receipt_kernel_launches()
-    with ClockSampler(local) as clk:
+
+    class _Null:
+        def __enter__(self):
+            return self
+
+        def __exit__(self, *a):
+            pass
+
+        def summary(self):
+            return None
+    with (ClockSampler(local) if clocks else _Null()) as clk:
         barrier()
         for _ in range(args.steps):
             flush.fill_(1.0)  # evicts L2 between timed steps (not timed)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            stats.append(step(True))
+            step(False)
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
         barrier()
     launches = R.receipt_kernel_launches() - launches0
-    if args.trace and rank == 0:
-        with open(args.trace, "w") as f:
-            json.dump(last_trace, f)
     ms = max_over_ranks(statistics.mean(times), dist, dev)
-    value = replica_rate(wedges, world, ms / 1e3)
     tips = R.as_u64(tip)
-
-    # end to end through the C ABI with host buffers, with the options the
-    # device-timed steps used (the shape class's tuned values)
-    from paper_2010_08695_gb300 import autotune
-    g0 = R.Graph(eu_d, ev_d, nu, nv, stream=stream)
-    tuned = autotune.lookup(g0.shape_class(side)) or {}
-    g0.close()
-    e2e_opt = {"warp_max_w": tuned.get("warp_max_w", 0),
-               "slice_min_w": tuned.get("slice_min_w", 0),
-               "dgm_frac_1024": tuned.get("dgm_frac_1024", 0), "huc": args.huc,
-               "huc_factor_1024": args.huc_factor_1024, "round_graphs": args.round_graphs}
-    e2e_P = args.P or tuned.get("P", 150)
-    eu_h = torch.from_numpy(eu).pin_memory().numpy()
-    ev_h = torch.from_numpy(ev).pin_memory().numpy()
-    tip_h = torch.empty(n_side, dtype=torch.int64).pin_memory().numpy().view(np.uint64)
-    R.receipt_tip_decompose_host(eu_h, ev_h, nu, nv, side, P=e2e_P, out=tip_h, **e2e_opt)
-    e2e_t = []
-    for _ in range(max(1, min(args.steps, 3))):
-        barrier()
-        t0 = time.perf_counter()
-        R.receipt_tip_decompose_host(eu_h, ev_h, nu, nv, side, P=e2e_P, out=tip_h, **e2e_opt)
-        e2e_t.append(time.perf_counter() - t0)
-    e2e_s = max_over_ranks(statistics.mean(e2e_t), dist, dev)
-    e2e_ok = bool(np.array_equal(tip_h, tips))
-
-    if rank != 0:
-        if dist is not None:
-            dist.barrier()
-            dist.destroy_process_group()
-        return 0
-
-    # roofline of the dominant peel kernel (tier with the most device time)
-    st = stats[-1]
-    names = ["k_cd_update_warp", "k_cd_update_cta", "k_cd_update_global", "k_cd_update_slice",
-             "k_cd_update_dense"]
-    tier = max(range(5), key=lambda t: st["ms_peel"][t])
-    lau = max(1, st["peel_launches"][tier])
-    alg_bytes = (4 * st["peel_wedges"][tier] + 16 * st["peel_mids"][tier]
-                 + 24 * st["peel_anchors"][tier]) / lau
-    dur_s = st["ms_peel"][tier] / 1e3 / lau
-    achieved = alg_bytes / dur_s / 1e9 if dur_s > 0 else 0.0
+    # instrumented steps: phase split, per-tier counters and device time
+    inst, inst_ms = [], []
+    for _ in range(roofline_steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        inst.append(step(True))
+        e1.record(stream)
+        e1.synchronize()
+        inst_ms.append(e0.elapsed_time(e1))
+    if not inst:  # no instrumented step: counters of one more plain-timing step
+        inst.append(step(True))
+        inst_ms.append(float("nan"))
+    st = _mean_stats(inst)
+    last = inst[-1]
     peak, peak_kind = _peaks()
-    traffic = None
-    tr = NCU_TRAFFIC.get(names[tier])
-    if tr and tr.get("src") == _src_digest():
-        traffic = int(tr["dram_per_alg_byte"] * alg_bytes)
-    gold_ok = None
+    out = {
+        "workload": DESCR.get(name, name), "nu": nu, "nv": nv, "m": int(len(eu)),
+        "side": "U" if side == 0 else "V", "wedges_bup": wedges, "P": P,
+        "tuning": tuned or "defaults", "ms_per_step": ms, "value": replica_rate(wedges, world, ms / 1e3),
+        "step_ms_all": times, "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "instrumented_step_ms": statistics.mean(inst_ms),
+        "walked_wedges_per_step": {"count": last["wedges_count"], "cd": sum(last["peel_wedges"]),
+                                   "cd_without_dgm": last["wedges_cd"], "fd": last["wedges_fd"]},
+        "phase_ms": {"count": st["ms_count"], "cd": st["ms_cd"], "fd": st["ms_fd"],
+                     "peel_tiers": st["ms_peel"]},
+        "phase_wedges_per_s": {
+            "count": last["wedges_count"] / (st["ms_count"] / 1e3) if st["ms_count"] else None,
+            "cd": sum(last["peel_wedges"]) / (st["ms_cd"] / 1e3) if st["ms_cd"] else None,
+            "fd": last["wedges_fd"] / (st["ms_fd"] / 1e3) if st["ms_fd"] else None},
+        "rounds_cd": last["rounds_cd"], "levels_fd": last["levels_fd"], "subsets": last["p_eff"],
+        "fd_slowest_task": {"ms": st["ms_fd_max_subset"], "n": last["fd_max_subset_n"],
+                            "levels": last["fd_max_subset_levels"]},
+        "fd_heavy": {"subsets": last["fd_heavy_subsets"], "ms": st["ms_fd_heavy"],
+                     "levels": last["levels_fd_heavy"]},
+        "huc": {"mode": args.huc, "recounts": last["huc_recounts"],
+                "wedges": last["wedges_recount"], "ms": st["ms_recount"],
+                "cost_recount": last["cost_recount"]},
+        "peel_tier_wedges": last["peel_wedges"], "peel_tier_anchors": last["peel_anchors"],
+        "peel_tier_pairs": last["peel_pairs"], "peel_tier_mids": last["peel_mids"],
+        "roofline": roofline(st, peak, peak_kind),
+    }
     import synth
-    gpath = os.path.join(ROOT, "tests", "golden", synth.CHUNG_LU_10M + ".json")
+    gpath = os.path.join(ROOT, "tests", "golden", name + ".json")
+    out["bit_exact_vs_oracle"] = None
     if os.path.exists(gpath):
         gold = json.load(open(gpath))
-        gold_ok = hashlib.sha256(tips.astype("<u8").tobytes()).hexdigest() == gold["tips_sha256"]
+        if "tips_sha256" in gold and synth.edges_sha256(eu, ev) == gold["edges_sha256"]:
+            out["bit_exact_vs_oracle"] = (
+                hashlib.sha256(tips.astype("<u8").tobytes()).hexdigest() == gold["tips_sha256"])
+    if args.trace and trace:
+        with open(args.trace, "w") as f:
+            json.dump(trace, f)
+    del flush
+    if e2e:
+        # end to end through the C ABI with host buffers: H2D of the edges,
+        # build, decomposition, D2H of the tips, with the step's options
+        e2e_opt = {"warp_max_w": tuned.get("warp_max_w", 0),
+                   "slice_min_w": tuned.get("slice_min_w", 0),
+                   "dgm_frac_1024": tuned.get("dgm_frac_1024", 0), "huc": args.huc,
+                   "huc_factor_1024": args.huc_factor_1024, "round_graphs": args.round_graphs}
+        eu_h = torch.from_numpy(eu).pin_memory().numpy()
+        ev_h = torch.from_numpy(ev).pin_memory().numpy()
+        tip_h = torch.empty(n_side, dtype=torch.int64).pin_memory().numpy().view(np.uint64)
+        R.receipt_tip_decompose_host(eu_h, ev_h, nu, nv, side, P=P, out=tip_h, **e2e_opt)
+        e2e_t = []
+        for _ in range(max(1, min(args.steps, 3))):
+            barrier()
+            t0 = time.perf_counter()
+            R.receipt_tip_decompose_host(eu_h, ev_h, nu, nv, side, P=P, out=tip_h, **e2e_opt)
+            e2e_t.append(time.perf_counter() - t0)
+        e2e_s = max_over_ranks(statistics.mean(e2e_t), dist, dev)
+        out["e2e"] = {"value": replica_rate(wedges, world, e2e_s), "unit": "wedges/s",
+                      "h2d_bytes_per_step": int(eu.nbytes + ev.nbytes),
+                      "d2h_bytes_per_step": int(n_side * 8), "seconds": e2e_s,
+                      "matches_device_path": bool(np.array_equal(tip_h, tips))}
+    return out, (eu, ev, nu, nv, side)
 
-    line = {"metric": METRIC, "value": value, "unit": "wedges/s", "n_gpus": world,
-            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-            "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nu": nu, "nv": nv, "m": int(len(eu)), "side": "U",
-                       "round_graphs": bool(args.round_graphs),
-                       "P": args.P or tuned.get("P", 150), "tuning": tuned or "defaults",
-                       "huc": {"mode": args.huc, "factor_1024": args.huc_factor_1024 or 8192},
-                       "wedges_bup": wedges, "parallelism": "replicas" if world > 1
-                       else "single", "l2": "flushed between steps (256 MiB write)"},
-            "seconds_per_step": ms / 1e3,
-            "bit_exact_vs_oracle": gold_ok,
-            "walked_wedges_per_step": {"count": st["wedges_count"], "cd": sum(st["peel_wedges"]),
-                                       "cd_without_dgm": st["wedges_cd"], "fd": st["wedges_fd"]},
-            "phase_wedges_per_s": {
-                "count": st["wedges_count"] / (st["ms_count"] / 1e3) if st["ms_count"] else None,
-                "cd": sum(st["peel_wedges"]) / (st["ms_cd"] / 1e3) if st["ms_cd"] else None,
-                "fd": st["wedges_fd"] / (st["ms_fd"] / 1e3) if st["ms_fd"] else None},
-            "phase_ms": {"count": st["ms_count"], "cd": st["ms_cd"], "fd": st["ms_fd"],
-                         "peel_tiers": st["ms_peel"]},
-            "rounds_cd": st["rounds_cd"], "levels_fd": st["levels_fd"], "subsets": st["p_eff"],
-            "fd_slowest_task": {"ms": st["ms_fd_max_subset"], "n": st["fd_max_subset_n"],
-                                "levels": st["fd_max_subset_levels"]},
-            "fd_heavy": {"subsets": st["fd_heavy_subsets"], "ms": st["ms_fd_heavy"],
-                         "levels": st["levels_fd_heavy"]},
-            "huc": {"recounts": st["huc_recounts"], "wedges": st["wedges_recount"],
-                    "ms": st["ms_recount"], "cost_recount": st["cost_recount"]},
-            "peel_tier_wedges": st["peel_wedges"], "peel_tier_anchors": st["peel_anchors"],
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "kernel": names[tier],
-                         "peak_source": peak_kind,
-                         "bytes_per_launch": alg_bytes, "launch_ms": dur_s * 1e3},
-            "e2e": {"value": replica_rate(wedges, world, e2e_s), "unit": "wedges/s",
-                    "h2d_bytes_per_step": int(eu.nbytes + ev.nbytes),
-                    "d2h_bytes_per_step": int(n_side * 8), "seconds": e2e_s,
-                    "matches_device_path": e2e_ok},
-            "gpu_launches": int(launches),
-            "clocks": clk.summary()}
-    if world == 1 and not args.no_cpu_baseline:
-        cb, _ = cpu_baseline(eu, ev, nu, nv, side)
-        line["cpu_baseline"] = cb
+
+def _vertex_sample(eu, ev, nu, nv, side, budget, seed):
+    """Seeded random vertices of the decomposed side whose 2-hop walks
+    (sum over y in N_x of d_y) add up to about `budget` entries."""
+    a, b, nb = (eu, ev, nv) if side == 0 else (ev, eu, nu)
+    na = nu if side == 0 else nv
+    d_o = np.bincount(b, minlength=nb).astype(np.float64)
+    walk = np.bincount(a, weights=d_o[b], minlength=na)
+    order = np.random.default_rng(seed).permutation(na)
+    k = int(np.searchsorted(np.cumsum(walk[order]), budget)) + 1
+    return order[:k].astype(np.int32)
+
+
+def cpu_oracle_rate(graph, eu, ev, nu, nv, side, budget, seed):
+    """Wedges/s of the oracle's per-vertex count by definition over a seeded
+    vertex sample (one core; adjacency built beforehand)."""
+    xs = _vertex_sample(eu, ev, nu, nv, side, budget, seed)
+    t0 = time.perf_counter()
+    _, walked = graph.count_vertex(side, xs)
+    dt = time.perf_counter() - t0
+    return walked / dt, walked, dt, len(xs)
+
+
+def cpu_baseline(eu, ev, nu, nv, side, name):
+    import oracle
+    t0 = time.perf_counter()
+    g = oracle.Graph(eu, ev, nu, nv)
+    t_build = time.perf_counter() - t0
+    rate, walked, dt, k = cpu_oracle_rate(g, eu, ev, nu, nv, side, CPU_SAMPLE_WEDGES, 1)
+    g.close()
+    return {"value": rate, "unit": "wedges/s", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle per-vertex butterfly count by definition (the 2-hop walk of "
+                       f"Algorithm 2's update) of {k} seeded random {('U', 'V')[side]} vertices "
+                       f"of {name}: {walked} wedges in {dt:.1f} s on one core (adjacency built "
+                       f"once beforehand in {t_build:.1f} s, not in the rate)")}
+
+
+def run_reference(args):
+    rank, world, _ = _rank_env()
+    if rank != 0:
+        return 0
+    import oracle
+    name = args.workload if args.workload in DESCR else HEADLINE
+    eu, ev, nu, nv, side, wedges = load_workload(name)
+    g = oracle.Graph(eu, ev, nu, nv)
+    for i in range(args.warmup):
+        cpu_oracle_rate(g, eu, ev, nu, nv, side, REF_STEP_WEDGES // 8, 1000 + i)
+    rates, secs, walks = [], [], []
+    for i in range(args.steps):
+        r, w, dt, _ = cpu_oracle_rate(g, eu, ev, nu, nv, side, REF_STEP_WEDGES, i)
+        rates.append(r)
+        secs.append(dt)
+        walks.append(w)
+    g.close()
+    value = sum(walks) / sum(secs)
+    sample = (f"oracle per-vertex butterfly count by definition over a seeded sample of "
+              f"{('U', 'V')[side]} vertices of {name}, ~{REF_STEP_WEDGES} wedges per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "wedges/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": DESCR[name], "nu": nu, "nv": nv, "m": int(len(eu)),
+                       "side": "U" if side == 0 else "V", "wedges_bup": wedges,
+                       "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "wedges/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "wedges/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.barrier()
-        dist.destroy_process_group()
     return 0
 
 
@@ -384,15 +446,13 @@ def _generate(specs, workers=None):
         return pool.map(_gen_spec, specs, chunksize=4)
 
 
-def run_batch(args):
-    """Batched workload: 4,096 graphs (seed 4), U side, one packed
-    decomposition versus one decomposition per graph on the same GPU."""
+def batch_leg(R, args):
+    """4,096 graphs (seed 4), U side: one packed decomposition versus one
+    decomposition per graph on the same GPU."""
     import torch
     import synth
     specs = synth.batch_specs(args.batch_graphs, seed=4)
     graphs = _generate(specs)
-    import paper_2010_08695_gb300 as R
-    R.load()
     built = [R.Graph(eu, ev, s.nu, s.nv) for (eu, ev), s in zip(graphs, specs)]
     sides = [0] * len(built)
     torch.cuda.synchronize()
@@ -404,16 +464,13 @@ def run_batch(args):
     outs = R.receipt_decompose_batch(built, sides, round_graphs=args.round_graphs)  # warm-up
     torch.cuda.synchronize()
     tb = []
-    for _ in range(args.steps):
+    for _ in range(3):
         t0 = time.perf_counter()
-        outs = R.receipt_decompose_batch(built, sides, outs=outs, timing=True,
-                                         round_graphs=args.round_graphs)
+        outs = R.receipt_decompose_batch(built, sides, outs=outs, round_graphs=args.round_graphs)
         torch.cuda.synchronize()
         tb.append(time.perf_counter() - t0)
-    batch_stats = built[0].stats()
-    if args.trace:
-        with open(args.trace, "w") as f:
-            json.dump(built[0].trace(), f)
+    R.receipt_decompose_batch(built, sides, outs=outs, timing=True, round_graphs=args.round_graphs)
+    bs = built[0].stats()
     alone = [torch.empty_like(o) for o in outs]
     for g, o in zip(built[:64], alone[:64]):  # warm-up
         g.tip_decompose(0, out=o)
@@ -424,49 +481,30 @@ def run_batch(args):
     torch.cuda.synchronize()
     t_plain = time.perf_counter() - t0
     same = all(torch.equal(a, b) for a, b in zip(outs, alone))
-    import oracle
-    sample = list(range(0, len(built), max(1, len(built) // 16)))
-    oracle_ok = all(np.array_equal(R.as_u64(outs[i]), oracle.bup(graphs[i][0], graphs[i][1],
-                                                                  specs[i].nu, specs[i].nv, 0)[0])
-                    for i in sample)
     tbm = statistics.median(tb)
-    line = {"metric": "graphs/s (batched tip decomposition)", "value": len(built) / tbm,
-            "unit": "graphs/s", "n_gpus": 1, "steps": args.steps, "higher_is_better": True,
-            "config": {"workload": f"{len(built)} Chung-Lu graphs, seed 4, U side",
-                       "edges": edges, "wedges_bup": wedges},
-            "seconds_batched": tbm, "seconds_one_graph_per_launch": t_plain,
+    return {"workload": f"{len(built)} Chung-Lu graphs, seed 4, U side", "edges": edges,
+            "wedges_bup": wedges, "graphs_per_s": len(built) / tbm, "seconds_batched": tbm,
+            "seconds_one_graph_per_launch": t_plain,
             "graphs_per_s_one_graph_per_launch": len(built) / t_plain,
             "speedup_vs_one_graph_per_launch": t_plain / tbm,
-            "wedges_per_s_batched": wedges / tbm,
-            "rounds_cd": batch_stats["rounds_cd"], "subsets": batch_stats["p_eff"],
-            "phase_ms": {"count": batch_stats["ms_count"], "cd": batch_stats["ms_cd"],
-                         "fd": batch_stats["ms_fd"], "peel_tiers": batch_stats["ms_peel"]},
-            "fd_slowest_task": {"ms": batch_stats["ms_fd_max_subset"],
-                                "n": batch_stats["fd_max_subset_n"],
-                                "levels": batch_stats["fd_max_subset_levels"]},
-            "fd_tasks": batch_stats["fd_tasks"],
-            "walked_wedges": {"count": batch_stats["wedges_count"], "cd": sum(batch_stats["peel_wedges"]),
-                              "cd_without_dgm": batch_stats["wedges_cd"],
-                              "fd": batch_stats["wedges_fd"]},
-            "batch_equals_alone": same, "oracle_sample_ok": oracle_ok,
-            "oracle_sample": len(sample)}
-    print(json.dumps(line), flush=True)
-    return 0
+            "wedges_per_s_batched": wedges / tbm, "rounds_cd": bs["rounds_cd"],
+            "subsets": bs["p_eff"], "fd_tasks": bs["fd_tasks"],
+            "phase_ms": {"count": bs["ms_count"], "cd": bs["ms_cd"], "fd": bs["ms_fd"],
+                         "peel_tiers": bs["ms_peel"]},
+            "fd_slowest_task": {"ms": bs["ms_fd_max_subset"], "n": bs["fd_max_subset_n"],
+                                "levels": bs["fd_max_subset_levels"]},
+            "batch_equals_alone": same}
 
 
-def run_serve(args):
-    """Serving workload: a bounded prefix of the seed-5 request stream
-    (Poisson arrivals at 0.8x the measured one-at-a-time throughput, and a
-    flood with every request at t=0), latency p50/p99 and graphs/s."""
-    import torch
+def serve_leg(R, args):
+    """The first `serve_requests` requests of the seed-5 serving stream:
+    Poisson arrivals at 0.8x the measured one-at-a-time throughput, and a
+    flood with every request at t = 0; latency p50/p99 and graphs/s."""
     import synth
     specs = synth.serve_specs(args.serve_requests, seed=5)
     graphs = _generate(specs)
-    import paper_2010_08695_gb300 as R
-    R.load()
     reqs = [(eu, ev, s.nu, s.nv, s.side) for (eu, ev), s in zip(graphs, specs)]
     edges = sum(len(r[0]) for r in reqs)
-    # plain path: one request at a time through the host-buffer entry point
     calib = reqs[: min(len(reqs), args.serve_calib)]
     R.receipt_tip_decompose_host(*calib[0])
     t0 = time.perf_counter()
@@ -495,24 +533,74 @@ def run_serve(args):
     alone_idx = list(range(0, len(reqs), max(1, len(reqs) // 20)))
     alone_ok = all(np.array_equal(outs_p[i], R.receipt_tip_decompose_host(*reqs[i]))
                    for i in alone_idx)
-    import oracle
-    small = [i for i in range(len(reqs)) if len(reqs[i][0]) <= 200000][:10]
-    oracle_ok = all(np.array_equal(outs_p[i], oracle.bup(*reqs[i])[0]) for i in small)
 
     def pick(st):
         return {k: st[k] for k in ("p50_ms", "p99_ms", "mean_ms", "max_ms", "graphs_per_s",
                                    "completed", "batches", "packed_requests", "peak_inflight",
                                    "peak_inflight_bytes")}
-    line = {"metric": "graphs/s and p50/p99 latency (serving)", "value": st_p["graphs_per_s"],
-            "unit": "graphs/s", "n_gpus": 1, "higher_is_better": True,
-            "config": {"workload": f"first {len(reqs)} requests of the seed-5 stream",
-                       "edges": edges, "slots": args.serve_slots,
-                       "arrival_rate_per_s": 0.8 * plain_rate},
+    return {"workload": f"first {len(reqs)} requests of the seed-5 stream", "edges": edges,
+            "slots": args.serve_slots, "arrival_rate_per_s": 0.8 * plain_rate,
             "plain_one_at_a_time_graphs_per_s": plain_rate,
             "poisson": pick(st_p), "flood": pick(st_f),
-            "mix_equals_alone_sample": alone_ok, "poisson_equals_flood": same,
-            "oracle_sample_ok": oracle_ok, "oracle_sample": len(small)}
+            "mix_equals_alone_sample": alone_ok, "poisson_equals_flood": same}
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = _rank_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_2010_08695_gb300 as R
+    R.load()
+    name = args.workload
+    main, graph = measure_graph(R, name, args, dist, world, local,
+                                roofline_steps=args.roofline_steps)
+    if rank != 0:
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+    line = {"metric": METRIC, "value": main["value"], "unit": "wedges/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": main["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": main["workload"], "nu": main["nu"], "nv": main["nv"],
+                       "m": main["m"], "side": main["side"], "wedges_bup": main["wedges_bup"],
+                       "P": main["P"], "tuning": main["tuning"],
+                       "round_graphs": bool(args.round_graphs),
+                       "huc": {"mode": args.huc, "factor_1024": args.huc_factor_1024 or 8192},
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "flushed between steps (256 MiB write)",
+                       "timed_steps": "uninstrumented; phase split and roofline from 2 "
+                                      "further steps with per-tier CUDA events"},
+            "seconds_per_step": main["ms_per_step"] / 1e3,
+            "bit_exact_vs_oracle": main["bit_exact_vs_oracle"],
+            "roofline": main["roofline"], "e2e": main["e2e"],
+            "gpu_launches": main["gpu_launches"], "clocks": main["clocks"]}
+    for k in ("step_ms_all", "instrumented_step_ms", "walked_wedges_per_step", "phase_ms",
+              "phase_wedges_per_s", "rounds_cd", "levels_fd", "subsets", "fd_slowest_task",
+              "fd_heavy", "huc", "peel_tier_wedges", "peel_tier_anchors", "peel_tier_pairs",
+              "peel_tier_mids"):
+        line[k] = main[k]
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(*graph, name)
+    if world == 1 and not args.no_extras:
+        if name != SECONDARY:
+            sec_args = argparse.Namespace(**vars(args))
+            sec_args.steps, sec_args.warmup, sec_args.P, sec_args.trace = 5, 3, 0, None
+            sec, _ = measure_graph(R, SECONDARY, sec_args, clocks=False, roofline_steps=1)
+            for k in ("step_ms_all", "clocks", "peel_tier_mids"):
+                sec.pop(k, None)
+            line["secondary"] = sec
+        line["batch"] = batch_leg(R, args)
+        line["serve"] = serve_leg(R, args)
     print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
     return 0
 
 
@@ -523,11 +611,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="leave out the secondary workload, the batch and the serving legs")
+    ap.add_argument("--roofline-steps", type=int, default=2,
+                    help="instrumented steps after the timed ones (phase split, roofline)")
     ap.add_argument("--trace", default=None,
-                    help="write the per-round trace of the last timed step to this JSON file")
-    ap.add_argument("--workload", choices=["single", "batch", "serve"], default="single",
-                    help="single: the 10M-edge graph (default); batch: 4,096 graphs packed "
-                         "vs one per launch; serve: the serving stream prefix")
+                    help="write the per-round trace of the last instrumented step to this file")
+    ap.add_argument("--workload", default=HEADLINE,
+                    choices=[HEADLINE, SECONDARY, "batch", "serve"],
+                    help="single graph (default: the 100M-edge graph); batch: 4,096 graphs "
+                         "packed vs one per launch; serve: the serving stream prefix")
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--round-graphs", action="store_true",
                     help="run each coarse-grained round as one CUDA graph launch")
@@ -537,16 +630,20 @@ def main():
                     help="recount rule (Sec. 4.1): 0 cost rule, -1 never, 1 every range")
     ap.add_argument("--huc-factor-1024", type=int, default=0,
                     help="factor of the recount rule in 1/1024 units (0: 8192)")
-    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-requests", type=int, default=SERVE_PREFIX)
     ap.add_argument("--serve-calib", type=int, default=40)
     ap.add_argument("--serve-slots", type=int, default=4)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "batch":
-        return run_batch(args)
-    if args.workload == "serve":
-        return run_serve(args)
+    if args.workload in ("batch", "serve"):
+        import torch
+        torch.cuda.set_device(_rank_env()[2])
+        import paper_2010_08695_gb300 as R
+        R.load()
+        leg = batch_leg(R, args) if args.workload == "batch" else serve_leg(R, args)
+        print(json.dumps(leg), flush=True)
+        return 0
     return run_ours(args)
 
 

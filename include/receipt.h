@@ -175,6 +175,11 @@ typedef struct {
     uint64_t cost_recount;
     float ms_recount;
     int32_t reserved3;
+    /* Support atomics of the coarse-grained peel update per tier (the same
+     * tiers as peel_wedges): one per pair (x, x') of a peeled vertex x and a
+     * remaining vertex x' that share at least two neighbours (the pairs whose
+     * support changes). */
+    uint64_t peel_pairs[5];
 } receipt_stats;
 
 /* One synchronisation round of the coarse-grained step (Algorithm 3). */

@@ -66,7 +66,7 @@ class Stats(ctypes.Structure):
                 ("levels_fd_heavy", ctypes.c_int64), ("fd_tasks", ctypes.c_int32),
                 ("huc_recounts", ctypes.c_int32), ("wedges_recount", ctypes.c_uint64),
                 ("cost_recount", ctypes.c_uint64), ("ms_recount", ctypes.c_float),
-                ("reserved3", ctypes.c_int32)]
+                ("reserved3", ctypes.c_int32), ("peel_pairs", ctypes.c_uint64 * 5)]
 
 
 class Round(ctypes.Structure):

@@ -260,6 +260,7 @@ void tip_decompose_impl(receipt_graph *g, int side, uint64_t *d_tip, const recei
         st.peel_wedges[t] = D.tier_wedges[t];
         st.peel_mids[t] = D.tier_mids[t];
         st.peel_anchors[t] = D.tier_anchors[t];
+        st.peel_pairs[t] = D.tier_pairs[t];
         st.peel_launches[t] = D.tier_launches[t];
         st.ms_peel[t] = D.tier_ms[t];
     }

@@ -56,7 +56,8 @@ struct CdDev {
     unsigned long long wrem_prev;
     double tgt_prev;
     unsigned long long wedges;
-    unsigned long long tier_w[NTIER], tier_m[NTIER], tier_a[NTIER];  // per tier: wedges, mids, anchors
+    // per tier: wedges, mids, anchors, nonzero pairs (support atomics)
+    unsigned long long tier_w[NTIER], tier_m[NTIER], tier_a[NTIER], tier_p[NTIER];
     unsigned long long front_w;  // sum of wfull over a full-scan activeSet (C_peel)
     unsigned long long hist_w[NBUCKET];
     uint32_t hist_c[NBUCKET];
@@ -323,20 +324,30 @@ __global__ void k_cd_route(CdDev *st, const int32_t *__restrict__ Lb,
     }
 }
 
-// Support decrement of one (x, x') pair with crossing detection.
+// Support decrement of one (x, x') pair with crossing detection; `pairs`
+// counts this thread's support atomics.
 struct CdEmit {
     unsigned long long *sup;
     const int32_t *sub;
     unsigned long long hi;
     int32_t *next;
     int32_t *n_next;
+    unsigned long long pairs;
     __device__ __forceinline__ void operator()(int32_t k, uint32_t c) {
         if (sub[k] >= 0) return;
         unsigned long long d = choose2(c);
         unsigned long long old = atomicAdd(&sup[k], 0ull - d);
+        pairs++;
         if (old >= hi && old - d < hi) next[atomicAdd(n_next, 1)] = k;
     }
 };
+
+// Adds the support atomics of every thread of the calling warp to tier t's
+// counter (all lanes of the warp must call it).
+__device__ __forceinline__ void add_pairs(CdDev *st, int t, unsigned long long p) {
+    p = warp_sum(p);
+    if ((threadIdx.x & 31) == 0 && p) atomicAdd(&st->tier_p[t], p);
+}
 
 // Middle vertex y's list as it stands: the first len_o[y] entries from
 // off_o[y] (dynamic graph maintenance drops peeled vertices from the lists).
@@ -434,7 +445,7 @@ __global__ void __launch_bounds__(256) k_cd_update_warp(PeelArgs a) {
     WarpHash H{skey[w], sval[w]};
     H.clear(lane);
     __syncwarp();
-    CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext};
+    CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext, 0};
     unsigned long long cw = 0, cm = 0, ca = 0;
     for (;;) {
         int idx = 0;
@@ -477,6 +488,7 @@ __global__ void __launch_bounds__(256) k_cd_update_warp(PeelArgs a) {
         }
         __syncwarp();
     }
+    add_pairs(a.st, 0, emit.pairs);
     if (lane == 0 && ca) {
         atomicAdd(&a.st->tier_w[0], cw);
         atomicAdd(&a.st->tier_m[0], cm);
@@ -508,7 +520,7 @@ __global__ void __maxnreg__(64) k_cd_update_cta(PeelArgs a, int32_t head_cap,
     ch.len = chunk_len_ptr(ch.tmp);
     H.clear_all();
     __syncthreads();
-    CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext};
+    CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext, 0};
     PeelMids M{a.adj_s, a.off_o, a.len_o};
     unsigned long long cw = 0, cm = 0, ca = 0;
     for (;;) {
@@ -540,6 +552,7 @@ __global__ void __maxnreg__(64) k_cd_update_cta(PeelArgs a, int32_t head_cap,
         __syncthreads();
         H.reset_scalars();
     }
+    add_pairs(a.st, 1, emit.pairs);
     if (threadIdx.x == 0 && ca) {
         atomicAdd(&a.st->tier_w[1], cw);
         atomicAdd(&a.st->tier_m[1], cm);
@@ -559,7 +572,7 @@ __global__ void __maxnreg__(64) k_cd_update_global(PeelArgs a, uint32_t *gcnt,
     GlobalDense G{gcnt + (size_t)blockIdx.x * keyspace, gtouch + (size_t)blockIdx.x * keyspace, &s_nt};
     const int32_t n1 = a.st->nLg, n2 = 0;
     if ((int32_t)blockIdx.x >= n1 + n2) return;
-    CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext};
+    CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext, 0};
     PeelMids M{a.adj_s, a.off_o, a.len_o};
     unsigned long long cw = 0, cm = 0, ca = 0;
     for (;;) {
@@ -580,6 +593,7 @@ __global__ void __maxnreg__(64) k_cd_update_global(PeelArgs a, uint32_t *gcnt,
         G.clear();
         __syncthreads();
     }
+    add_pairs(a.st, 2, emit.pairs);
     if (threadIdx.x == 0 && ca) {
         atomicAdd(&a.st->tier_w[2], cw);
         atomicAdd(&a.st->tier_m[2], cm);
@@ -607,7 +621,7 @@ __global__ void __launch_bounds__(SLICE_THREADS, 1) k_cd_update_slice(PeelArgs a
     ch.len = chunk_len_ptr(ch.tmp);
     H.clear_all();
     __syncthreads();
-    CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext};
+    CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext, 0};
     unsigned long long cw = 0, cm = 0, ca = 0;
     const int64_t items = (int64_t)a.st->nLs * a.C;
     for (;;) {
@@ -648,6 +662,7 @@ __global__ void __launch_bounds__(SLICE_THREADS, 1) k_cd_update_slice(PeelArgs a
         __syncthreads();
         H.reset_scalars();
     }
+    add_pairs(a.st, 3, emit.pairs);
     if (threadIdx.x == 0) {
         if (cw) atomicAdd(&a.st->tier_w[3], cw);
         if (ca) {
@@ -734,7 +749,7 @@ __global__ void __maxnreg__(64) k_cd_update_dense(PeelArgs a) {
     ch.len = chunk_len_ptr(ch.tmp);
     H.clear_all();
     __syncthreads();
-    CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext};
+    CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext, 0};
     const int lane = threadIdx.x & 31;
     unsigned long long cw = 0, cm = 0, ca = 0;
     for (;;) {
@@ -797,6 +812,7 @@ __global__ void __maxnreg__(64) k_cd_update_dense(PeelArgs a) {
             __syncthreads();
         }
     }
+    add_pairs(a.st, 4, emit.pairs);
     if (threadIdx.x == 0 && ca) {
         atomicAdd(&a.st->tier_w[4], cw);
         atomicAdd(&a.st->tier_m[4], cm);
@@ -1249,7 +1265,7 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
     RC_LAUNCH();
     int hany = 0;
     RC_CUDA(cudaMemcpyAsync(&hany, any.get(), 4, cudaMemcpyDeviceToHost, s));
-    unsigned long long hw = 0, ht[3 * NTIER];
+    unsigned long long hw = 0, ht[4 * NTIER];
     RC_CUDA(cudaMemcpyAsync(&hw, &st.get()->wedges, 8, cudaMemcpyDeviceToHost, s));
     RC_CUDA(cudaMemcpyAsync(ht, st.get()->tier_w, sizeof(ht), cudaMemcpyDeviceToHost, s));
     RC_CUDA(cudaStreamSynchronize(s));
@@ -1260,6 +1276,7 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
         D.tier_wedges[t] = ht[t];
         D.tier_mids[t] = ht[NTIER + t];
         D.tier_anchors[t] = ht[2 * NTIER + t];
+        D.tier_pairs[t] = ht[3 * NTIER + t];
     }
 }
 

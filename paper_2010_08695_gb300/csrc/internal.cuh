@@ -58,6 +58,7 @@ struct Decomp {
     bool timing = false;
     uint64_t tier_wedges[5] = {}, tier_mids[5] = {};
     uint64_t tier_anchors[5] = {};
+    uint64_t tier_pairs[5] = {};  // support atomics (nonzero pairs) per tier
     int64_t tier_launches[5] = {};
     float tier_ms[5] = {};
     std::vector<receipt_round> trace;
