@@ -369,6 +369,23 @@ receipt_status receipt_server_get_stats(receipt_server *sv, receipt_server_stats
  * dropped. */
 receipt_status receipt_server_destroy(receipt_server *sv);
 
+/*
+ * Upper bound of the butterfly count of any vertex on a side with n_side
+ * vertices of degree at most max_deg_side, whose neighbours have degree at
+ * most max_deg_other, in a graph of m edges (the count of x is the sum over
+ * x' != x of C(|N_x n N_x'|, 2), Sec. 2; every support of Algorithms 2-4
+ * starts at the count and only falls). *bound receives the minimum of
+ * (n_side - 1) C(max_deg_side, 2), max_deg_side (max_deg_other - 1)
+ * (max_deg_side - 1) / 2 and m (max_deg_side - 1) / 2 (UINT64_MAX if above
+ * it). Host arithmetic only; no device is needed.
+ * Errors: RECEIPT_ERR_OVERFLOW when the bound reaches 2^63 (then counting and
+ * decomposition refuse the graph with the same status; with the library's
+ * limit m < 2^31 the third term stays below 2^61, so a built graph never
+ * does), RECEIPT_ERR_INVALID for negative arguments.
+ */
+receipt_status receipt_support_bound(int64_t n_side, int32_t max_deg_side,
+                                     int32_t max_deg_other, int64_t m, uint64_t *bound);
+
 /* Counters of the last count/decompose call on g. */
 receipt_status receipt_get_stats(const receipt_graph *g, receipt_stats *out);
 

@@ -145,6 +145,9 @@ def load(build_if_missing: bool = True):
                                             ctypes.POINTER(ctypes.c_double)]
         lib.receipt_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
         lib.receipt_server_destroy.argtypes = [vp]
+        lib.receipt_support_bound.argtypes = [i64, i32, i32, i64,
+                                              ctypes.POINTER(ctypes.c_uint64)]
+        lib.receipt_support_bound.restype = ctypes.c_int
         for f in ("receipt_server_create", "receipt_server_submit", "receipt_server_wait",
                   "receipt_server_get_stats", "receipt_server_destroy"):
             getattr(lib, f).restype = ctypes.c_int
@@ -270,6 +273,16 @@ def receipt_get_subsets(handle) -> list:
     _check(lib.receipt_get_subsets(handle, buf, n.value, ctypes.byref(n)))
     return [{"n": r.n, "heavy": bool(r.heavy), "levels": r.levels, "wedges_est": r.wedges_est,
              "ms": r.ms} for r in buf[: n.value]]
+
+
+def receipt_support_bound(n_side: int, max_deg_side: int, max_deg_other: int, m: int) -> int:
+    """Upper bound of any vertex's butterfly count on a side of that shape
+    (host arithmetic, no device needed). Raises ReceiptError with
+    RECEIPT_ERR_OVERFLOW (5) when it reaches 2^63."""
+    b = ctypes.c_uint64(0)
+    _check(load().receipt_support_bound(int(n_side), int(max_deg_side), int(max_deg_other),
+                                        int(m), ctypes.byref(b)))
+    return int(b.value)
 
 
 def receipt_kernel_launches() -> int:

@@ -126,6 +126,38 @@ void allow_max_smem(const void *kernel) {
 void compute_wfull(const Side &S, const Side &O, int64_t m, unsigned long long *wfull,
                    cudaStream_t s);
 
+// Upper bound of the butterfly count (Sec. 2: sum over x' != x of
+// C(|N_x n N_x'|, 2)) of any vertex of a side with n_s vertices of degree at
+// most ds, whose neighbours have degree at most d_o, in a graph of m edges.
+// Every support of Algorithms 2-4 starts at such a count and only falls, so
+// the bound covers every 64-bit support and count the library keeps:
+//  (a) at most n_s - 1 partners x', each sharing c <= ds neighbours;
+//  (b) the partners' c add up to the wedges leaving x, sum over y in N_x of
+//      (d_y - 1) <= ds (d_o - 1), and C(c, 2) <= c (ds - 1) / 2;
+//  (c) those wedges are also at most m.
+unsigned __int128 count_bound(int64_t n_s, int64_t ds, int64_t d_o, int64_t m) {
+    typedef unsigned __int128 u128;
+    if (n_s < 2 || ds < 2) return 0;
+    const u128 c2 = (u128)ds * (u128)(ds - 1) / 2;
+    const u128 a = (u128)(n_s - 1) * c2;
+    const u128 b = (u128)ds * (u128)(d_o > 0 ? d_o - 1 : 0) * (u128)(ds - 1) / 2;
+    const u128 c = (u128)(m > 0 ? m : 0) * (u128)(ds - 1) / 2;
+    u128 r = a < b ? a : b;
+    return r < c ? r : c;
+}
+
+// Fails with RECEIPT_ERR_OVERFLOW when a count of either side of g could
+// reach 2^63 (never with m < 2^31, where bound (c) stays below 2^61).
+void check_count_bound(const receipt_graph *g) {
+    for (int t = 0; t < 2; t++) {
+        const unsigned __int128 b =
+            count_bound(g->side[t].n, g->max_deg[t], g->max_deg[1 - t], g->m);
+        if (b >> 63)
+            fail(RECEIPT_ERR_OVERFLOW, std::string("butterfly counts of side ") + "UV"[t] +
+                                           " could exceed 2^63");
+    }
+}
+
 namespace {
 
 __global__ void k_scatter_i32(const int32_t *__restrict__ v, const int32_t *__restrict__ new2old,
@@ -191,6 +223,7 @@ void tip_decompose_impl(receipt_graph *g, int side, uint64_t *d_tip, const recei
     const Side &S = g->side[side];
     const int32_t n = S.n;
     if (n > 0 && !d_tip) fail(RECEIPT_ERR_INVALID, "null d_tip");
+    check_count_bound(g);
     Timer T(opt.timing != 0, s);
     T.mark();
     Decomp D;
@@ -515,6 +548,7 @@ receipt_status receipt_count_butterflies(receipt_graph *g, uint64_t *d_cnt_u, ui
     return guarded([&] {
         if (!g) fail(RECEIPT_ERR_INVALID, "null graph");
         DeviceGuard dg(g->device);
+        check_count_bound(g);
         cudaStream_t s = (cudaStream_t)stream;
         DevBuf<unsigned long long> cu(g->nu, s), cv(g->nv, s);
         uint64_t w = count_local(g, cu.get(), cv.get(), s);
@@ -532,6 +566,7 @@ receipt_status receipt_count_butterflies_noalloc(receipt_graph *g, uint64_t *d_c
     return guarded([&] {
         if (!g) fail(RECEIPT_ERR_INVALID, "null graph");
         DeviceGuard dg(g->device);
+        check_count_bound(g);
         count_noalloc(g, (unsigned long long *)d_cnt_u, (unsigned long long *)d_cnt_v,
                       (cudaStream_t)stream);
     });
@@ -585,6 +620,17 @@ receipt_status receipt_tip_decompose_host(const int32_t *h_eu, const int32_t *h_
         tip_decompose_impl(g, (int)side, (uint64_t *)tip.get(), opt, s);
         if (n > 0) RC_CUDA(cudaMemcpyAsync(h_tip, tip.get(), 8 * (size_t)n, cudaMemcpyDeviceToHost, s));
         RC_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+receipt_status receipt_support_bound(int64_t n_side, int32_t max_deg_side,
+                                     int32_t max_deg_other, int64_t m, uint64_t *bound) {
+    return guarded([&] {
+        if (n_side < 0 || max_deg_side < 0 || max_deg_other < 0 || m < 0)
+            fail(RECEIPT_ERR_INVALID, "negative size");
+        const unsigned __int128 b = count_bound(n_side, max_deg_side, max_deg_other, m);
+        if (bound) *bound = (b >> 64) ? ~0ull : (uint64_t)b;
+        if (b >> 63) fail(RECEIPT_ERR_OVERFLOW, "the bound reaches 2^63");
     });
 }
 

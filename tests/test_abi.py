@@ -67,13 +67,12 @@ def test_null_arguments_are_rejected_without_gpu(lib):
     assert lib.receipt_graph_destroy(None) == 0
 
 
-def test_struct_layouts_match_header():
+def test_struct_layouts_match_header(tmp_path):
     """Every ctypes mirror of a header struct has the C size and the C offset
     of each field (checked with offsetof in a program gcc builds from
     include/receipt.h)."""
     import shutil
     import paper_2010_08695_gb300 as R
-    from paper_2010_08695_gb300 import _build
     if not shutil.which("gcc"):
         pytest.skip("gcc not found")
     pairs = [(R.Options, "receipt_options"), (R.Stats, "receipt_stats"),
@@ -89,12 +88,45 @@ def test_struct_layouts_match_header():
             lines.append(f'    printf("%zu\\n", offsetof({cname}, {f}));')
             want.append(getattr(cls, f).offset)
     lines += ["    return 0;", "}"]
-    os.makedirs(_build.BUILD_DIR, exist_ok=True)
-    src = os.path.join(_build.BUILD_DIR, "layout_probe.c")
-    exe = os.path.join(_build.BUILD_DIR, "layout_probe")
+    src = str(tmp_path / "layout_probe.c")
+    exe = str(tmp_path / "layout_probe")
     with open(src, "w") as fh:
         fh.write("\n".join(lines) + "\n")
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", exe, src], check=True)
     got = [int(x) for x in subprocess.run([exe], capture_output=True, text=True,
                                           check=True).stdout.split()]
     assert got == want
+
+
+def test_support_bound_without_gpu():
+    """The count bound behind RECEIPT_ERR_OVERFLOW (host arithmetic): it
+    holds on random graphs against the oracle's counts, is exact for the
+    U side of K_{a,b}, and reports overflow once it reaches 2^63."""
+    import numpy as np
+    import oracle
+    import paper_2010_08695_gb300 as R
+    import synth
+    for seed in range(40):
+        rng = np.random.default_rng(seed)
+        nu, nv = int(rng.integers(2, 40)), int(rng.integers(2, 40))
+        eu, ev = synth.random_small(nu, nv, float(rng.uniform(0.05, 0.9)), seed)
+        if len(eu) == 0:
+            continue
+        cu, cv = oracle.count_2hop(eu, ev, nu, nv)
+        du = np.bincount(eu, minlength=nu)
+        dv = np.bincount(ev, minlength=nv)
+        assert int(cu.max()) <= R.receipt_support_bound(nu, du.max(), dv.max(), len(eu))
+        assert int(cv.max()) <= R.receipt_support_bound(nv, dv.max(), du.max(), len(eu))
+    for a, b in ((2, 2), (5, 3), (7, 11), (30, 4)):
+        eu, ev = synth.complete_bipartite(a, b)
+        cu, _ = oracle.count_2hop(eu, ev, a, b)
+        assert R.receipt_support_bound(a, b, a, a * b) == int(cu.max()) == (a - 1) * b * (b - 1) // 2
+    # the library's own limits (m < 2^31) keep every count below 2^61
+    big = 2 ** 31 - 1
+    assert R.receipt_support_bound(big, big, big, big - 1) < 2 ** 61
+    with pytest.raises(R.ReceiptError) as ei:
+        R.receipt_support_bound(big, big, big, 2 ** 40)
+    assert ei.value.status == 5
+    with pytest.raises(R.ReceiptError) as ei:
+        R.receipt_support_bound(-1, 1, 1, 1)
+    assert ei.value.status == 1
