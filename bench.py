@@ -63,6 +63,8 @@ SECONDARY = "chung-lu-1Mx200k-10M"
 DESCR = {
     "chung-lu-5Mx1M-100M": "chung-lu |U|=5M |V|=1M m=100M gamma 2.0/2.0 seed 3, V side",
     "chung-lu-1Mx200k-10M": "chung-lu |U|=1M |V|=200k m=10M gamma 2.5/2.1 seed 2, U side",
+    "chung-lu-2Mx400k-20M": "chung-lu |U|=2M |V|=400k m=20M gamma 2.0/2.0 seed 33, V side "
+                            "(the 100M-edge graph's shape at a fifth of its size)",
 }
 CPU_SAMPLE_WEDGES = 2_500_000_000  # oracle walk per CPU-baseline sample (~10 s on one core)
 REF_STEP_WEDGES = 800_000_000      # oracle walk per reference-arm step (~3-4 s)
@@ -545,6 +547,93 @@ def serve_leg(R, args):
             "mix_equals_alone_sample": alone_ok, "poisson_equals_flood": same}
 
 
+def run_single(args):
+    """One decomposition of a single-graph workload (for profiler captures):
+    prints its seconds and, with --trace, writes its per-round trace."""
+    import torch
+    import paper_2010_08695_gb300 as R
+    torch.cuda.set_device(_rank_env()[2])
+    R.load()
+    eu, ev, nu, nv, side, wedges = load_workload(args.workload)
+    g = R.Graph(eu, ev, nu, nv)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tip = g.tip_decompose(side, P=args.P, timing=bool(args.trace))
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    st = g.stats()
+    if args.trace:
+        with open(args.trace, "w") as f:
+            json.dump(g.trace(), f)
+    print(json.dumps({"workload": args.workload, "seconds": dt, "rounds_cd": st["rounds_cd"],
+                      "peel_wedges": st["peel_wedges"], "peel_pairs": st["peel_pairs"],
+                      "tips_sha256": hashlib.sha256(R.as_u64(tip).astype("<u8").tobytes())
+                      .hexdigest()}), flush=True)
+    return 0
+
+
+def run_experiments(args):
+    """The paper's experiments on the synthetic workloads (Sec. 5): a sweep of
+    P (Fig. 4), the ablation of the recount (Sec. 4.1) and of dynamic graph
+    maintenance (Sec. 4.2) (Figs. 5-6: RECEIPT, without the recount, without
+    both) and the phase breakup (Sec. 5.2.3), one instrumented step per
+    setting after a warm-up step, tip numbers checked against the first
+    setting's. Writes one JSON record per workload to args.experiments."""
+    import torch
+    import paper_2010_08695_gb300 as R
+    torch.cuda.set_device(_rank_env()[2])
+    R.load()
+    names = [args.workload] if args.workload in DESCR else [SECONDARY, HEADLINE]
+    out = {}
+    for name in names:
+        eu, ev, nu, nv, side, wedges = load_workload(name)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        eu_d = torch.from_numpy(eu).to(dev)
+        ev_d = torch.from_numpy(ev).to(dev)
+        n_side = nu if side == 0 else nv
+        tip = torch.empty(n_side, dtype=torch.int64, device=dev)
+        ref = None
+        settings = [("P", {"P": p}) for p in (4, 25, 50, 100, 150, 300, 600)]
+        settings += [("receipt", {"P": 150}), ("receipt-paper-huc-factor", {"P": 150, "huc_factor_1024": 1024}),
+                     ("receipt-no-huc", {"P": 150, "huc": -1}),
+                     ("receipt-no-huc-no-dgm", {"P": 150, "huc": -1, "dgm": False}),
+                     ("receipt-P4", {"P": 4}), ("receipt-P4-no-huc", {"P": 4, "huc": -1}),
+                     ("receipt-P4-no-huc-no-dgm", {"P": 4, "huc": -1, "dgm": False})]
+        recs = []
+        for label, kw in settings:
+            rec = {"setting": label, **{k: v for k, v in kw.items()}}
+            for t in (False, True):
+                g = R.Graph(eu_d, ev_d, nu, nv)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                g.tip_decompose(side, out=tip, timing=t, **kw)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                st = g.stats()
+                g.close()
+            tips = R.as_u64(tip).copy()
+            if ref is None:
+                ref = tips
+            rec.update({"seconds": dt, "ms_count": st["ms_count"], "ms_cd": st["ms_cd"],
+                        "ms_fd": st["ms_fd"], "rounds_cd": st["rounds_cd"],
+                        "levels_fd": st["levels_fd"], "subsets": st["p_eff"],
+                        "wedges_count": st["wedges_count"],
+                        "wedges_cd_walked": sum(st["peel_wedges"]),
+                        "wedges_cd_without_dgm": st["wedges_cd"], "wedges_fd": st["wedges_fd"],
+                        "recounts": st["huc_recounts"], "wedges_recount": st["wedges_recount"],
+                        "ms_recount": st["ms_recount"], "fd_slowest_task_ms": st["ms_fd_max_subset"],
+                        "fd_heavy_subsets": st["fd_heavy_subsets"],
+                        "same_tips_as_first": bool(np.array_equal(tips, ref))})
+            recs.append(rec)
+            print(json.dumps({"workload": name, **rec}), flush=True)
+        out[name] = {"workload": DESCR[name], "wedges_bup": wedges, "records": recs,
+                     "note": "seconds: one step with per-phase CUDA events, after an "
+                             "uninstrumented warm-up step of the same setting"}
+    with open(args.experiments, "w") as f:
+        json.dump(out, f, indent=1)
+    return 0
+
+
 def run_ours(args):
     import torch
     rank, world, local = _rank_env()
@@ -618,7 +707,7 @@ def main():
     ap.add_argument("--trace", default=None,
                     help="write the per-round trace of the last instrumented step to this file")
     ap.add_argument("--workload", default=HEADLINE,
-                    choices=[HEADLINE, SECONDARY, "batch", "serve"],
+                    choices=[HEADLINE, SECONDARY, "chung-lu-2Mx400k-20M", "batch", "serve"],
                     help="single graph (default: the 100M-edge graph); batch: 4,096 graphs "
                          "packed vs one per launch; serve: the serving stream prefix")
     ap.add_argument("--batch-graphs", type=int, default=4096)
@@ -630,12 +719,21 @@ def main():
                     help="recount rule (Sec. 4.1): 0 cost rule, -1 never, 1 every range")
     ap.add_argument("--huc-factor-1024", type=int, default=0,
                     help="factor of the recount rule in 1/1024 units (0: 8192)")
+    ap.add_argument("--single", action="store_true",
+                    help="one decomposition of the workload and nothing else (profiling runs)")
+    ap.add_argument("--experiments", default=None,
+                    help="run the P sweep and the recount/maintenance ablation and write "
+                         "them to this JSON file (instead of the benchmark)")
     ap.add_argument("--serve-requests", type=int, default=SERVE_PREFIX)
     ap.add_argument("--serve-calib", type=int, default=40)
     ap.add_argument("--serve-slots", type=int, default=4)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.experiments:
+        return run_experiments(args)
+    if args.single:
+        return run_single(args)
     if args.workload in ("batch", "serve"):
         import torch
         torch.cuda.set_device(_rank_env()[2])

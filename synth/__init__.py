@@ -33,7 +33,7 @@ import numpy as np
 __all__ = [
     "er", "chung_lu", "chung_lu_i0_for_max", "edges_sha256", "workload_graph",
     "GraphSpec", "batch_specs", "serve_specs", "graph_from_spec", "WORKLOADS",
-    "ER_20K", "CHUNG_LU_10M", "CHUNG_LU_100M",
+    "ER_20K", "CHUNG_LU_10M", "CHUNG_LU_100M", "CHUNG_LU_20M",
     "random_small", "complete_bipartite",
 ]
 
@@ -184,6 +184,8 @@ def random_small(nu: int, nv: int, p: float, seed: int):
 ER_20K = "er-2000x500-20k"
 CHUNG_LU_10M = "chung-lu-1Mx200k-10M"
 CHUNG_LU_100M = "chung-lu-5Mx1M-100M"
+# the 100M-edge graph's shape at a fifth of its size (profiling stand-in)
+CHUNG_LU_20M = "chung-lu-2Mx400k-20M"
 
 WORKLOADS = {
     ER_20K: dict(kind="er", nu=2000, nv=500, m=20000, seed=1, side=0),
@@ -191,6 +193,8 @@ WORKLOADS = {
                        gamma_v=2.1, seed=2, dmax_v=50_000, side=0),
     CHUNG_LU_100M: dict(kind="cl", nu=5_000_000, nv=1_000_000, m=100_000_000, gamma_u=2.0,
                         gamma_v=2.0, seed=3, dmax_u=500_000, dmax_v=500_000, side=1),
+    CHUNG_LU_20M: dict(kind="cl", nu=2_000_000, nv=400_000, m=20_000_000, gamma_u=2.0,
+                       gamma_v=2.0, seed=33, dmax_u=100_000, dmax_v=100_000, side=1),
 }
 
 
