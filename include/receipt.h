@@ -125,6 +125,34 @@ typedef struct {
      * C_rcnt). Speed only; results are the same. */
     int32_t huc;
     int32_t huc_factor_1024;
+    /* Shape of the key-sliced tier of the peel update (anchors with many
+     * wedges, aggregated one key slice at a time): 1 = one 1,024-thread CTA
+     * per SM over 102,400-key slices, 2 = two 512-thread CTAs per SM over
+     * 51,200-key slices, 4 (or 0) = four 256-thread CTAs per SM over
+     * 25,344-key slices. Speed only. */
+    int32_t slice_ctas;
+    /* How the activeSet of a range's later rounds is found: >= 0 (default)
+     * by a scan of the remaining vertices after each round (support <
+     * theta(i+1)), so the support decrements need no returned value; -1 from
+     * the support atomics' returned values (a vertex joins when its own
+     * decrement crosses theta(i+1)). Speed only. */
+    int32_t scan_frontier;
+    /* Hybrid update computation inside the fine-grained step (Sec. 4.1, its
+     * last paragraph), for the tasks peeled by all CTAs (see fd_heavy_w): a
+     * member's support is the butterflies it shares with higher subsets
+     * (init minus its count inside G_i) plus its count among the task's
+     * members still alive, so a level may recount those instead of
+     * applying its updates. 0 = a level recounts when its peeled members'
+     * walks inside G_i exceed factor * C_rcnt(G_i) (the factor of huc),
+     * -1 = never, 1 = every level with updates recounts (test hook). Speed
+     * only; results are the same. */
+    int32_t fd_huc;
+    /* At most this many vertices per range of Algorithm 3 (the range bound
+     * stops early when the remaining vertices below it reach the cap):
+     * 0 = 2 n / P, -1 = no cap (wedges alone decide, Sec. 3.1.1). A range of
+     * many vertices with small walks holds few wedges but as many levels of
+     * Algorithm 4 as distinct supports. Speed only (Theorem 2). */
+    int32_t range_max_n;
 } receipt_options;
 
 /* Counters of the last call on a graph (Sec. 5: wedges and rounds). */
@@ -180,6 +208,16 @@ typedef struct {
      * remaining vertex x' that share at least two neighbours (the pairs whose
      * support changes). */
     uint64_t peel_pairs[5];
+    /* Start points of Algorithm 1 per aggregation tier, both sides: warp
+     * table, shared-memory hybrid, global counters (degree >= 65535 or a key
+     * space beyond shared memory), global counters after the hybrid's repeat
+     * table overflowed. */
+    int64_t count_points[4];
+    /* Levels of the fine-grained step's heavy tasks whose updates were a
+     * recount (see receipt_options.fd_huc), and the wedges those recounts
+     * traversed. */
+    int64_t fd_recounts;
+    uint64_t wedges_fd_recount;
 } receipt_stats;
 
 /* One synchronisation round of the coarse-grained step (Algorithm 3). */

@@ -48,7 +48,9 @@ class Options(ctypes.Structure):
                 ("warp_max_w", ctypes.c_int32), ("slice_min_w", ctypes.c_int32),
                 ("no_dgm", ctypes.c_int32), ("dgm_frac_1024", ctypes.c_int32),
                 ("fd_heavy_w", ctypes.c_int64), ("round_graphs", ctypes.c_int32),
-                ("huc", ctypes.c_int32), ("huc_factor_1024", ctypes.c_int32)]
+                ("huc", ctypes.c_int32), ("huc_factor_1024", ctypes.c_int32),
+                ("slice_ctas", ctypes.c_int32), ("scan_frontier", ctypes.c_int32),
+                ("fd_huc", ctypes.c_int32), ("range_max_n", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -66,7 +68,9 @@ class Stats(ctypes.Structure):
                 ("levels_fd_heavy", ctypes.c_int64), ("fd_tasks", ctypes.c_int32),
                 ("huc_recounts", ctypes.c_int32), ("wedges_recount", ctypes.c_uint64),
                 ("cost_recount", ctypes.c_uint64), ("ms_recount", ctypes.c_float),
-                ("reserved3", ctypes.c_int32), ("peel_pairs", ctypes.c_uint64 * 5)]
+                ("reserved3", ctypes.c_int32), ("peel_pairs", ctypes.c_uint64 * 5),
+                ("count_points", ctypes.c_int64 * 4), ("fd_recounts", ctypes.c_int64),
+                ("wedges_fd_recount", ctypes.c_uint64)]
 
 
 class Round(ctypes.Structure):
@@ -180,10 +184,15 @@ def _dptr(t):
 
 def _options(P=150, bounds=None, subset=None, bounds_out=None, p_eff=None, timing=False,
              warp_max_w=0, slice_min_w=0, dgm=True, dgm_frac_1024=0, fd_heavy_w=0,
-             round_graphs=False, huc=0, huc_factor_1024=0):
+             round_graphs=False, huc=0, huc_factor_1024=0, slice_ctas=0, scan_frontier=0,
+             fd_huc=0, range_max_n=0):
     o = Options()
     load().receipt_options_default(ctypes.byref(o))
     o.P = int(P)
+    o.fd_huc = int(fd_huc)
+    o.range_max_n = int(range_max_n)
+    o.slice_ctas = int(slice_ctas)
+    o.scan_frontier = int(scan_frontier)
     o.huc = int(huc)
     o.huc_factor_1024 = int(huc_factor_1024)
     o.fd_heavy_w = int(fd_heavy_w)
@@ -340,7 +349,8 @@ class Graph:
     def tip_decompose(self, side: int = SIDE_U, P: int = 0, bounds=None, subsets=False,
                       timing=False, out=None, stream=None, warp_max_w=0, slice_min_w=0, dgm=True,
                       dgm_frac_1024=0, fd_heavy_w=0, round_graphs=False, huc=0,
-                      huc_factor_1024=0):
+                      huc_factor_1024=0, slice_ctas=0, scan_frontier=None, fd_huc=0,
+                      range_max_n=None):
         """Tip numbers of ``side`` (Algorithms 3 and 4). P = 0 takes the tuned
         value for this graph's shape class, else 150. With ``subsets=True``
         returns ``(tips, subset_of_vertex, range_bounds)``. ``huc``: 0 = the
@@ -357,6 +367,11 @@ class Graph:
             slice_min_w = slice_min_w or tuned["slice_min_w"]
             P = P or tuned.get("P", 150)
             dgm_frac_1024 = dgm_frac_1024 or tuned.get("dgm_frac_1024", 0)
+            slice_ctas = slice_ctas or tuned.get("slice_ctas", 0)
+            if scan_frontier is None:
+                scan_frontier = tuned.get("scan_frontier", 0)
+            if range_max_n is None:
+                range_max_n = tuned.get("range_max_n", 0)
         P = P or 150
         tip = out if out is not None else torch.empty(n, dtype=torch.int64, device=self.device)
         sub = torch.empty(n, dtype=torch.int32, device=self.device) if subsets else None
@@ -364,7 +379,8 @@ class Graph:
             if subsets else None
         peff = ctypes.c_int32(0)
         o, keep = _options(P, bounds, sub, bout, peff, timing, warp_max_w, slice_min_w, dgm,
-                           dgm_frac_1024, fd_heavy_w, round_graphs, huc, huc_factor_1024)
+                           dgm_frac_1024, fd_heavy_w, round_graphs, huc, huc_factor_1024,
+                           slice_ctas, int(scan_frontier or 0), fd_huc, int(range_max_n or 0))
         receipt_tip_decompose(self._h, side, tip, o, stream)
         if subsets:
             return tip, sub, bout[: peff.value + 1]
@@ -380,11 +396,21 @@ class Graph:
         return receipt_get_subsets(self._h)
 
 
-def receipt_decompose_batch(graphs, sides, outs=None, P: int = 150, stream=None, timing=False,
-                            round_graphs=False, huc=0, huc_factor_1024=0):
-    """Tip numbers of many graphs in one pass (disjoint-union packing)."""
+def receipt_decompose_batch(graphs, sides, outs=None, P: int = 0, stream=None, timing=False,
+                            round_graphs=False, huc=0, huc_factor_1024=0, tuned=True, **options):
+    """Tip numbers of many graphs in one pass (disjoint-union packing). With
+    `tuned`, options not given take the autotuner's values for the union's
+    shape class (P = 0: tuned, else 150)."""
     import torch
     n = len(graphs)
+    if tuned and n > 0:
+        from . import autotune
+        rec = autotune.lookup(autotune.batch_shape_class(graphs, sides)) or {}
+        for k in ("warp_max_w", "slice_min_w", "dgm_frac_1024", "slice_ctas", "range_max_n"):
+            if k in rec and not options.get(k):
+                options[k] = rec[k]
+        P = P or rec.get("P", 0)
+    P = P or 150
     hs = (ctypes.c_void_p * n)(*[g.handle for g in graphs])
     ss = (ctypes.c_int * n)(*[int(s) for s in sides])
     if outs is None:
@@ -392,7 +418,7 @@ def receipt_decompose_batch(graphs, sides, outs=None, P: int = 150, stream=None,
                 for g, s in zip(graphs, sides)]
     ps = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
     o, keep = _options(P, timing=timing, round_graphs=round_graphs, huc=huc,
-                       huc_factor_1024=huc_factor_1024)
+                       huc_factor_1024=huc_factor_1024, **options)
     _check(load().receipt_decompose_batch(hs, ss, n, ps, ctypes.byref(o), _stream_handle(stream)))
     return outs
 

@@ -220,6 +220,7 @@ void tip_decompose_impl(receipt_graph *g, int side, uint64_t *d_tip, const recei
     }
     if (opt.huc < -1 || opt.huc > 1) fail(RECEIPT_ERR_INVALID, "huc must be -1, 0 or 1");
     if (opt.huc_factor_1024 < 0) fail(RECEIPT_ERR_INVALID, "huc_factor_1024 must be >= 0");
+    if (opt.fd_huc < -1 || opt.fd_huc > 1) fail(RECEIPT_ERR_INVALID, "fd_huc must be -1, 0 or 1");
     const Side &S = g->side[side];
     const int32_t n = S.n;
     if (n > 0 && !d_tip) fail(RECEIPT_ERR_INVALID, "null d_tip");
@@ -235,6 +236,8 @@ void tip_decompose_impl(receipt_graph *g, int side, uint64_t *d_tip, const recei
     D.timing = opt.timing != 0;
     D.max_deg_s = g->max_deg[side];
     D.fd_heavy_w = opt.fd_heavy_w;
+    D.fd_huc = opt.fd_huc;
+    D.huc_factor = opt.huc_factor_1024 > 0 ? opt.huc_factor_1024 / 1024.0 : 8.0;
     D.parts = (side == 0 && !g->parts.empty()) ? &g->parts : nullptr;
     DevBuf<unsigned long long> cu(g->nu, s), cv(g->nv, s), init(n, s), wfull(n, s);
     DevBuf<int32_t> sub(n, s);
@@ -247,7 +250,8 @@ void tip_decompose_impl(receipt_graph *g, int side, uint64_t *d_tip, const recei
     }
     unsigned long long h_wbup = 0;
     RC_CUDA(cudaMemcpyAsync(&h_wbup, wbup.get(), 8, cudaMemcpyDeviceToHost, s));
-    uint64_t wc = count_local(g, cu.get(), cv.get(), s);
+    int64_t cpoints[4] = {0, 0, 0, 0};
+    uint64_t wc = count_local(g, cu.get(), cv.get(), s, cpoints);
     T.mark();
     D.sup = side ? cv.get() : cu.get();
     D.init = init.get();
@@ -270,6 +274,7 @@ void tip_decompose_impl(receipt_graph *g, int side, uint64_t *d_tip, const recei
     receipt_stats &st = g->stats;
     st = receipt_stats{};
     st.wedges_count = wc;
+    for (int t = 0; t < 4; t++) st.count_points[t] = cpoints[t];
     st.wedges_bup = h_wbup;
     st.wedges_cd = D.wedges_cd;
     st.wedges_fd = D.wedges_fd;
@@ -285,6 +290,8 @@ void tip_decompose_impl(receipt_graph *g, int side, uint64_t *d_tip, const recei
     st.levels_fd_heavy = D.fd_heavy_levels;
     st.fd_tasks = D.fd_tasks;
     st.huc_recounts = D.huc_recounts;
+    st.fd_recounts = D.fd_recounts;
+    st.wedges_fd_recount = D.wedges_fd_recount;
     st.wedges_recount = D.wedges_recount;
     st.cost_recount = D.cost_recount;
     st.ms_recount = D.ms_recount;
@@ -551,13 +558,15 @@ receipt_status receipt_count_butterflies(receipt_graph *g, uint64_t *d_cnt_u, ui
         check_count_bound(g);
         cudaStream_t s = (cudaStream_t)stream;
         DevBuf<unsigned long long> cu(g->nu, s), cv(g->nv, s);
-        uint64_t w = count_local(g, cu.get(), cv.get(), s);
+        int64_t cpoints[4] = {0, 0, 0, 0};
+        uint64_t w = count_local(g, cu.get(), cv.get(), s, cpoints);
         if (d_cnt_u)
             scatter_to_original(cu.get(), g->side[0].new2old, g->nu, (unsigned long long *)d_cnt_u, s);
         if (d_cnt_v)
             scatter_to_original(cv.get(), g->side[1].new2old, g->nv, (unsigned long long *)d_cnt_v, s);
         g->stats = receipt_stats{};
         g->stats.wedges_count = w;
+        for (int t = 0; t < 4; t++) g->stats.count_points[t] = cpoints[t];
     });
 }
 

@@ -36,11 +36,6 @@ namespace {
 constexpr int NBUCKET = LOG_BUCKETS;
 constexpr int NTIER = 5;  // warp, hybrid, global, sliced, dense window
 constexpr double DGM_FRAC = 0.125;  // stale share of live entries that triggers a compaction
-// A range's first round recounts instead of peeling when its activeSet's
-// wedges exceed HUC_FACTOR * C_rcnt: per unit of the two cost measures the
-// peel tiers run 4-10 times faster than the counting kernels (measured on
-// Chung-Lu graphs of 10M and 100M edges).
-constexpr double HUC_FACTOR = 8.0;
 
 __device__ __forceinline__ int bucket_of(unsigned long long k) { return log_bucket_of(k); }
 __device__ __forceinline__ unsigned long long bucket_top(int b) { return log_bucket_top(b); }
@@ -118,8 +113,12 @@ __global__ void k_cd_hist(int32_t n, const int32_t *__restrict__ sub,
 }
 
 // findHi with the adaptive target (one block). range = 0-based index i-1,
-// P = subsets requested.
-__global__ void __launch_bounds__(1024) k_cd_select(CdDev *st, int range, int P) {
+// P = subsets requested. With cap > 0 the bound also stops at the first
+// bucket where the remaining vertices below it reach cap: a range of many
+// vertices with small walks would hold few wedges but as many peeling levels
+// as distinct supports, all peeled one after another by one fine-grained
+// task.
+__global__ void __launch_bounds__(1024) k_cd_select(CdDev *st, int range, int P, int32_t cap) {
     __shared__ unsigned long long tmpw[33];
     __shared__ uint32_t tmpc[33];
     __shared__ int s_pick, s_first, s_last;
@@ -143,7 +142,7 @@ __global__ void __launch_bounds__(1024) k_cd_select(CdDev *st, int range, int P)
     unsigned long long wtot;
     uint32_t ctot;
     unsigned long long wpre = block_exclusive_scan<unsigned long long>(wsum, tmpw, &wtot);
-    block_exclusive_scan<uint32_t>(csum, tmpc, &ctot);
+    uint32_t cpre = block_exclusive_scan<uint32_t>(csum, tmpc, &ctot);
     // adaptive target: tgt_i = s_{i-1} * W_rem / (P - i + 1)
     double s_prev = 1.0;
     if (range > 0) {
@@ -154,13 +153,15 @@ __global__ void __launch_bounds__(1024) k_cd_select(CdDev *st, int range, int P)
     if (left < 1) left = 1;
     double tgt = s_prev * (double)wtot / (double)left;
     unsigned long long run = wpre;
+    uint32_t crun = cpre;
     for (int j = 0; j < PER; j++) {
         int b = threadIdx.x * PER + j;
         run += w[j];
+        crun += c[j];
         if (c[j]) {
             atomicMin(&s_first, b);
             atomicMax(&s_last, b);
-            if ((double)run >= tgt) atomicMin(&s_pick, b);
+            if ((double)run >= tgt || (cap > 0 && crun >= (uint32_t)cap)) atomicMin(&s_pick, b);
         }
     }
     __syncthreads();
@@ -324,8 +325,11 @@ __global__ void k_cd_route(CdDev *st, const int32_t *__restrict__ Lb,
     }
 }
 
-// Support decrement of one (x, x') pair with crossing detection; `pairs`
-// counts this thread's support atomics.
+// Support decrement of one (x, x') pair; `pairs` counts this thread's
+// support atomics. With crossing detection (next != null) the atomic's
+// returned old value tells whether this decrement took the support below hi
+// (the vertex joins the next activeSet); without it the decrement needs no
+// returned value and the next activeSet comes from a scan after the round.
 struct CdEmit {
     unsigned long long *sup;
     const int32_t *sub;
@@ -336,9 +340,13 @@ struct CdEmit {
     __device__ __forceinline__ void operator()(int32_t k, uint32_t c) {
         if (sub[k] >= 0) return;
         unsigned long long d = choose2(c);
-        unsigned long long old = atomicAdd(&sup[k], 0ull - d);
         pairs++;
-        if (old >= hi && old - d < hi) next[atomicAdd(n_next, 1)] = k;
+        if (next) {
+            unsigned long long old = atomicAdd(&sup[k], 0ull - d);
+            if (old >= hi && old - d < hi) next[atomicAdd(n_next, 1)] = k;
+        } else {
+            atomicAdd(&sup[k], 0ull - d);
+        }
     }
 };
 
@@ -433,6 +441,7 @@ struct PeelArgs {
     int32_t C;             // key slices
     int32_t SW;            // keys per slice
     int32_t n_keys;        // keys of the side
+    int32_t scan;          // next activeSet by a scan after the round (no crossing detection)
 };
 
 __global__ void __launch_bounds__(256) k_cd_update_warp(PeelArgs a) {
@@ -445,7 +454,7 @@ __global__ void __launch_bounds__(256) k_cd_update_warp(PeelArgs a) {
     WarpHash H{skey[w], sval[w]};
     H.clear(lane);
     __syncwarp();
-    CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext, 0};
+    CdEmit emit{a.sup, a.sub, a.st->hi, a.scan ? nullptr : a.next, &a.st->nNext, 0};
     unsigned long long cw = 0, cm = 0, ca = 0;
     for (;;) {
         int idx = 0;
@@ -520,7 +529,7 @@ __global__ void __maxnreg__(64) k_cd_update_cta(PeelArgs a, int32_t head_cap,
     ch.len = chunk_len_ptr(ch.tmp);
     H.clear_all();
     __syncthreads();
-    CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext, 0};
+    CdEmit emit{a.sup, a.sub, a.st->hi, a.scan ? nullptr : a.next, &a.st->nNext, 0};
     PeelMids M{a.adj_s, a.off_o, a.len_o};
     unsigned long long cw = 0, cm = 0, ca = 0;
     for (;;) {
@@ -572,7 +581,7 @@ __global__ void __maxnreg__(64) k_cd_update_global(PeelArgs a, uint32_t *gcnt,
     GlobalDense G{gcnt + (size_t)blockIdx.x * keyspace, gtouch + (size_t)blockIdx.x * keyspace, &s_nt};
     const int32_t n1 = a.st->nLg, n2 = 0;
     if ((int32_t)blockIdx.x >= n1 + n2) return;
-    CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext, 0};
+    CdEmit emit{a.sup, a.sub, a.st->hi, a.scan ? nullptr : a.next, &a.st->nNext, 0};
     PeelMids M{a.adj_s, a.off_o, a.len_o};
     unsigned long long cw = 0, cm = 0, ca = 0;
     for (;;) {
@@ -604,24 +613,40 @@ __global__ void __maxnreg__(64) k_cd_update_global(PeelArgs a, uint32_t *gcnt,
 // Anchors with many wedges: the key space is cut into C slices of SW keys and
 // every (anchor, slice) pair is one work item, so the slices of a heavy
 // anchor run on different CTAs. Each item aggregates its slice with dense
-// 16-bit counters in shared memory.
-using SliceEngine = DenseSliceT<SLICE_WORDS>;
+// 16-bit counters in shared memory. Three shapes: one 1,024-thread CTA per
+// SM with 102,400-key slices, or two 512-thread (51,200 keys) or four
+// 256-thread (25,344 keys) CTAs per SM, whose items' barrier-separated
+// phases (staging, walk, sweep) overlap on the SM. Each shape's counters,
+// touched-word bitmap and staging fill the SM's shared memory.
+template <int THREADS, int WORDS>
+struct SliceShape {
+    static constexpr int threads = THREADS;
+    static constexpr int keys = 2 * WORDS;
+    using Engine = DenseSliceT<WORDS>;
+    static constexpr size_t smem() { return Engine::bytes() + chunk_bytes(THREADS); }
+};
+using Slice1 = SliceShape<SLICE_THREADS, 51200>;
+using Slice2 = SliceShape<512, 25600>;
+using Slice4 = SliceShape<256, 12672>;
 
-__global__ void __launch_bounds__(SLICE_THREADS, 1) k_cd_update_slice(PeelArgs a, int32_t n) {
+template <class Shape>
+__global__ void __launch_bounds__(Shape::threads, 1024 / Shape::threads)
+    k_cd_update_slice(PeelArgs a, int32_t n) {
+    using Engine = typename Shape::Engine;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_idx;
     __shared__ int s_nt;
     if (a.st->nLs == 0) return;
-    SliceEngine H;
+    Engine H;
     unsigned char *p = H.bind(smem, &s_nt);
     Chunk ch;
     ch.beg = (int64_t *)p;
-    ch.pre = (int32_t *)(ch.beg + MID_CHUNK);
-    ch.tmp = ch.pre + MID_CHUNK + 1;
+    ch.pre = (int32_t *)(ch.beg + Shape::threads);
+    ch.tmp = ch.pre + Shape::threads + 1;
     ch.len = chunk_len_ptr(ch.tmp);
     H.clear_all();
     __syncthreads();
-    CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext, 0};
+    CdEmit emit{a.sup, a.sub, a.st->hi, a.scan ? nullptr : a.next, &a.st->nNext, 0};
     unsigned long long cw = 0, cm = 0, ca = 0;
     const int64_t items = (int64_t)a.st->nLs * a.C;
     for (;;) {
@@ -653,12 +678,12 @@ __global__ void __launch_bounds__(SLICE_THREADS, 1) k_cd_update_slice(PeelArgs a
         H.set_width(w);
         SlicedMids M{a.adj_s, a.off_o, a.soff, a.len_o, a.adj_o, a.C + 1, j, a.SW};
         const int32_t self = (x >= base && x < base + w) ? x - base : -1;
-        SliceVisit<SliceEngine> v{&H, self, base};
+        SliceVisit<Engine> v{&H, self, base};
         int64_t walked = cta_walk(M, q0, q1, a.adj_o, ch, v);
         cw += walked;
         if (walked == 0) continue;
         SliceEmit em{&emit, base};
-        H.sweep<true, true>(em);
+        H.template sweep<true, true>(em);
         __syncthreads();
         H.reset_scalars();
     }
@@ -749,7 +774,7 @@ __global__ void __maxnreg__(64) k_cd_update_dense(PeelArgs a) {
     ch.len = chunk_len_ptr(ch.tmp);
     H.clear_all();
     __syncthreads();
-    CdEmit emit{a.sup, a.sub, a.st->hi, a.next, &a.st->nNext, 0};
+    CdEmit emit{a.sup, a.sub, a.st->hi, a.scan ? nullptr : a.next, &a.st->nNext, 0};
     const int lane = threadIdx.x & 31;
     unsigned long long cw = 0, cm = 0, ca = 0;
     for (;;) {
@@ -948,8 +973,22 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
     const int32_t warp_max_w =
         opt.warp_max_w > 0 ? std::min(opt.warp_max_w, WARP_MAX_W) : WARP_MAX_W;
     const int32_t slice_min_w = opt.slice_min_w > 0 ? opt.slice_min_w : SLICE_MIN_W;
-    // key slices for anchors with many wedges
-    const int32_t SW = SLICE_KEYS;
+    // key slices for anchors with many wedges; the sliced tier's shape
+    const int slice_ctas = opt.slice_ctas == 1 || opt.slice_ctas == 2 ? opt.slice_ctas : 4;
+    const void *slice_fn = slice_ctas == 4   ? (const void *)k_cd_update_slice<Slice4>
+                           : slice_ctas == 2 ? (const void *)k_cd_update_slice<Slice2>
+                                             : (const void *)k_cd_update_slice<Slice1>;
+    const int slice_threads = slice_ctas == 4 ? Slice4::threads
+                              : slice_ctas == 2 ? Slice2::threads : Slice1::threads;
+    const size_t smem_slice = slice_ctas == 4   ? Slice4::smem()
+                              : slice_ctas == 2 ? Slice2::smem() : Slice1::smem();
+    const int32_t SW = slice_ctas == 4 ? Slice4::keys : slice_ctas == 2 ? Slice2::keys : Slice1::keys;
+    const bool scan_next = opt.scan_frontier >= 0;
+    // vertices per range: at most range_max_n (0: 2 n / P, -1: no bound)
+    const int32_t range_cap =
+        opt.range_max_n < 0 ? 0
+                            : (opt.range_max_n > 0 ? opt.range_max_n
+                                                   : (int32_t)std::max<int64_t>(1, 2 * (int64_t)n / P));
     const int32_t C = std::max(1, ceil_div(n, SW));
     // slice table (C + 1 starts per list) only while slices are few
     const bool table = C <= 64;
@@ -963,8 +1002,7 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
     uint64_t peeled_at_dgm = 0;
     // hybrid update computation: C_rcnt once per call when the rule is on
     const int huc = opt.huc;
-    const double huc_factor =
-        opt.huc_factor_1024 > 0 ? opt.huc_factor_1024 / 1024.0 : HUC_FACTOR;
+    const double huc_factor = D.huc_factor;
     DevBuf<unsigned long long> rcost(1, s);
     if (huc == 0)
         launch_recount_cost(S, O, D.m, rcost.get(), s);
@@ -979,10 +1017,9 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
             RC_LAUNCH();
         }
     }
-    const size_t smem_slice = SliceEngine::bytes() + CHUNK_BYTES;
-    allow_max_smem((const void *)k_cd_update_slice);
+    allow_max_smem(slice_fn);
     int occ_s = 1;
-    RC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, k_cd_update_slice, SLICE_THREADS,
+    RC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, slice_fn, slice_threads,
                                                           smem_slice));
     const int sblocks = sms * std::max(1, occ_s);
     // tiers available for peel anchors (key space = whole side)
@@ -1067,7 +1104,7 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
         PeelArgs a{S.off,     S.adj,      O.off,       len_w.get(), adj_w.get(), D.sup, D.sub,
                    st.get(),  Lw.get(),   Lc.get(),    Lg.get(),    Ls.get(), nxt,
                    Lc_k.get(), Lc_w.get(), Ls_lo.get(), Ls_hi.get(), Ld.get(), Ld_k.get(),
-                   Ld_w.get(), table ? soff.get() : nullptr, C, SW, n};
+                   Ld_w.get(), table ? soff.get() : nullptr, C, SW, n, scan_next ? 1 : 0};
         mark(0);
         k_cd_update_warp<<<sms * 8, 256, 0, q>>>(a);
         RC_LAUNCH();
@@ -1086,9 +1123,19 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
             RC_LAUNCH();
         }
         mark(4);
-        k_cd_update_slice<<<sblocks, SLICE_THREADS, smem_slice, q>>>(a, n);
-        RC_LAUNCH();
+        {
+            void *args[] = {&a, (void *)&n};
+            RC_CUDA(cudaLaunchKernel(slice_fn, dim3(sblocks), dim3(slice_threads), args, smem_slice,
+                                     q));
+            RC_LAUNCH();
+        }
         mark(5);
+        if (scan_next) {
+            // next activeSet: remaining vertices whose support is now below hi
+            k_cd_frontier<<<nb, 512, 0, q>>>(n, D.sub, D.sup, D.wfull, st.get(), &st.get()->nNext,
+                                             nxt);
+            RC_LAUNCH();
+        }
         RC_CUDA(cudaMemcpyAsync(hst, st.get(), hdr, cudaMemcpyDeviceToHost, q));
         k_cd_advance<<<1, 1, 0, q>>>(st.get());
         RC_LAUNCH();
@@ -1174,7 +1221,7 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
         if (opt.n_bounds > 0) {
             k_set_hi<<<1, 1, 0, s>>>(st.get(), opt.h_bounds[range]);
         } else {
-            k_cd_select<<<1, 1024, 0, s>>>(st.get(), range, P);
+            k_cd_select<<<1, 1024, 0, s>>>(st.get(), range, P, range_cap);
         }
         RC_LAUNCH();
         cur = abuf[parity];
@@ -1278,6 +1325,20 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
         D.tier_anchors[t] = ht[2 * NTIER + t];
         D.tier_pairs[t] = ht[3 * NTIER + t];
     }
+}
+
+void compact_lists(const int64_t *off_o, int32_t *len_w, int32_t *adj_w, int32_t n_o,
+                   const int32_t *sub, cudaStream_t s) {
+    if (n_o <= 0) return;
+    k_dgm_compact<<<std::min(ceil_div((int64_t)n_o * 32, 256), num_sms() * 32), 256, 0, s>>>(
+        off_o, len_w, adj_w, n_o, sub);
+    RC_LAUNCH();
+}
+
+void list_lengths(const int64_t *off, int32_t n, int32_t *len, cudaStream_t s) {
+    if (n <= 0) return;
+    k_list_lengths<<<ceil_div(n, 256), 256, 0, s>>>(off, n, len);
+    RC_LAUNCH();
 }
 
 // wfull for side s

@@ -351,7 +351,7 @@ size_t count_cta_smem(int64_t keyspace, int32_t *head_cap, int32_t *bm_cap) {
 // Counts butterflies of both sides into cnt_local[side] (local ids, zeroed
 // here). Returns wedges traversed.
 uint64_t count_local(const receipt_graph *g, unsigned long long *cnt_u,
-                     unsigned long long *cnt_v, cudaStream_t s) {
+                     unsigned long long *cnt_v, cudaStream_t s, int64_t *points) {
     const int64_t m = g->m;
     RC_CUDA(cudaMemsetAsync(cnt_u, 0, sizeof(unsigned long long) * (g->nu > 0 ? g->nu : 1), s));
     RC_CUDA(cudaMemsetAsync(cnt_v, 0, sizeof(unsigned long long) * (g->nv > 0 ? g->nv : 1), s));
@@ -405,6 +405,8 @@ uint64_t count_local(const receipt_graph *g, unsigned long long *cnt_u,
         int32_t hn[4];
         RC_CUDA(cudaMemcpyAsync(hn, nl, sizeof(hn), cudaMemcpyDeviceToHost, s));
         RC_CUDA(cudaStreamSynchronize(s));
+        if (points)
+            for (int t = 0; t < 4; t++) points[t] += hn[t];
         if (hn[2] + hn[3] > 0) {
             const int gblocks = std::min(sms, hn[2] + hn[3]);
             DevBuf<uint32_t> gcnt((size_t)gblocks * nA, s);

@@ -37,8 +37,6 @@ constexpr int REPEAT_SLOTS = 4096;  // CtaHybrid repeat table
 constexpr int REPEAT_LIMIT = REPEAT_SLOTS / 2;
 constexpr int HEAD_MAX = 16384;     // dense 16-bit counters for keys < head
 constexpr int HEAD_SLICE = 2048;    // head of the key slices after the first
-constexpr int SLICE_WORDS = 45056;  // 16-bit counter words of a slice of the sliced tier
-constexpr int SLICE_KEYS = 2 * SLICE_WORDS;  // keys per slice of the sliced tier
 constexpr int SLICE_MIN_W = 49152;  // anchors with more wedges use the sliced tier
 constexpr int MAX_PROBE = 64;
 constexpr int WALK_UNROLL = 8;     // independent loads in flight per warp in cta_walk
@@ -347,38 +345,38 @@ inline size_t hybrid_bytes(int64_t keyspace, int32_t *head_cap_out = nullptr,
 // ------------------------------------------------------------------
 // Key k < hw sits in the low half of word k, key k >= hw in the high half of
 // word k - hw (hw = half the slice), so consecutive keys of a sorted list hit
-// different words. The first increment of a word appends it to a touched
-// list (one shared atomic per warp and step), so flushing and clearing cost
-// what the slice touched; past the list's capacity the sweep scans the slice.
-// Counts must stay below 2^16 (the caller routes anchors of degree >= 65535
-// elsewhere) unless the slice is set up with 32-bit counters. WORDS counter
-// words (at most 65,536: touched-list entries are 16-bit word indices).
+// different words. The first increment of a word sets its bit in a bitmap of
+// touched words, so flushing and clearing visit the words the slice touched
+// (one bitmap word per 32 counter words). Counts must stay below 2^16 (the
+// caller routes anchors of degree >= 65535 elsewhere) unless the slice is set
+// up with 32-bit counters. SCRATCH extra bytes after the bitmap are free for
+// the caller between passes.
 constexpr int DENSE_KEYS = 36864;               // keys per dense slice
 constexpr int DENSE_WORDS = DENSE_KEYS / 2;     // 18432 words (72 KB)
-constexpr int TOUCH_CAP = 8192;                 // touched-word list capacity
 
-template <int WORDS>
+template <int WORDS, int SCRATCH = 0>
 struct DenseSliceT {
-    static_assert(WORDS % 4 == 0 && WORDS <= 65536, "counter words");
+    static_assert(WORDS % 128 == 0, "counter words");
+    static constexpr int BM_WORDS = WORDS / 32;
     uint32_t *cnt;     // WORDS
-    uint16_t *tl;      // TOUCH_CAP
-    int *s_nt;         // shared scalar: touched words
+    uint32_t *tbm;     // BM_WORDS: touched counter words
     int32_t hw;        // half of the current slice width (<= WORDS)
     bool wide;         // 32-bit counters, one key per word (slices of WORDS keys)
 
-    static constexpr size_t bytes() { return (size_t)WORDS * 4 + (size_t)TOUCH_CAP * 2; }
-    __device__ unsigned char *bind(unsigned char *base, int *nt) {
+    static constexpr size_t bytes() {
+        return (size_t)WORDS * 4 + (size_t)BM_WORDS * 4 + (size_t)((SCRATCH + 15) & ~15);
+    }
+    __device__ unsigned char *bind(unsigned char *base, int * = nullptr) {
         cnt = (uint32_t *)base;
-        tl = (uint16_t *)(cnt + WORDS);
-        s_nt = nt;
+        tbm = cnt + WORDS;
         hw = WORDS;
         wide = false;
-        return (unsigned char *)(tl + TOUCH_CAP);
+        return (unsigned char *)base + bytes();
     }
+    __device__ void *scratch() const { return (void *)(tbm + BM_WORDS); }
     __device__ void clear_all() {
-        for (int i = threadIdx.x; i < WORDS / 4; i += blockDim.x)
+        for (int i = threadIdx.x; i < (WORDS + BM_WORDS) / 4; i += blockDim.x)
             ((uint4 *)cnt)[i] = make_uint4(0, 0, 0, 0);
-        if (threadIdx.x == 0) *s_nt = 0;
     }
     // Slice of w keys: 16-bit counters (w <= 2 * WORDS), or 32-bit counters
     // when counts may reach 2^16 (w <= WORDS).
@@ -390,19 +388,7 @@ struct DenseSliceT {
         const bool hi = !wide && k >= hw;
         const int32_t w = hi ? k - hw : k;
         const uint32_t old = atomicAdd(&cnt[w], hi ? 0x10000u : 1u);
-        const unsigned m = __activemask();
-        const unsigned b = __ballot_sync(m, old == 0);
-        if (b) {
-            const int lane = threadIdx.x & 31;
-            const int leader = __ffs(b) - 1;
-            int base = 0;
-            if (lane == leader) base = atomicAdd(s_nt, __popc(b));
-            base = __shfl_sync(m, base, leader);
-            if (old == 0) {
-                const int pos = base + __popc(b & lanemask_lt());
-                if (pos < TOUCH_CAP) tl[pos] = (uint16_t)w;
-            }
-        }
+        if (old == 0) atomicOr(&tbm[w >> 5], 1u << (w & 31));
     }
     __device__ __forceinline__ uint32_t count(int32_t k) const {
         if (wide) return cnt[k];
@@ -410,13 +396,17 @@ struct DenseSliceT {
         return (cnt[hi ? k - hw : k] >> (hi ? 16 : 0)) & 0xffffu;
     }
     // EMIT: emit(key, count) for every key with count >= 2; CLEAR: zero the
-    // touched words. The caller synchronises afterwards, then reset_scalars().
+    // touched words and their bits. The caller synchronises afterwards.
     template <bool EMIT, bool CLEAR, class Emit>
     __device__ void sweep(Emit &emit) {
-        const int nt = *(volatile int *)s_nt;
-        if (nt <= TOUCH_CAP) {
-            for (int i = threadIdx.x; i < nt; i += blockDim.x) {
-                const int w = tl[i];
+        const int nbw = (hw + 31) >> 5;
+        for (int b = threadIdx.x; b < nbw; b += blockDim.x) {
+            uint32_t m = tbm[b];
+            if (m == 0) continue;
+            if (CLEAR) tbm[b] = 0;
+            do {
+                const int w = (b << 5) + __ffs(m) - 1;
+                m &= m - 1;
                 const uint32_t v = cnt[w];
                 if (CLEAR) cnt[w] = 0;
                 if (EMIT) {
@@ -428,27 +418,10 @@ struct DenseSliceT {
                         if (c1 >= 2) emit(w + hw, c1);
                     }
                 }
-            }
-        } else {
-            for (int w = threadIdx.x; w < hw; w += blockDim.x) {
-                const uint32_t v = cnt[w];
-                if (v == 0) continue;
-                if (CLEAR) cnt[w] = 0;
-                if (EMIT) {
-                    if (wide) {
-                        if (v >= 2) emit(w, v);
-                        continue;
-                    }
-                    const uint32_t c0 = v & 0xffffu, c1 = v >> 16;
-                    if (c0 >= 2) emit(w, c0);
-                    if (c1 >= 2) emit(w + hw, c1);
-                }
-            }
+            } while (m);
         }
     }
-    __device__ void reset_scalars() {
-        if (threadIdx.x == 0) *s_nt = 0;
-    }
+    __device__ void reset_scalars() {}
 };
 
 using DenseSlice = DenseSliceT<DENSE_WORDS>;
@@ -494,7 +467,11 @@ struct Chunk {
     int32_t *len;    // MID_CHUNK: chunk-local mid index of compacted segment k
 };
 
-constexpr size_t CHUNK_BYTES = MID_CHUNK * 8 + (MID_CHUNK + 1) * 4 + 33 * 4 + MID_CHUNK * 4 + 16;
+// staging of up to T middle vertices (a CTA of T threads)
+__host__ __device__ constexpr size_t chunk_bytes(int T) {
+    return (size_t)T * 8 + (size_t)(T + 1) * 4 + 33 * 4 + (size_t)T * 4 + 16;
+}
+constexpr size_t CHUNK_BYTES = chunk_bytes(MID_CHUNK);
 
 __device__ __forceinline__ int32_t *chunk_len_ptr(int32_t *tmp) { return tmp + 36; }
 

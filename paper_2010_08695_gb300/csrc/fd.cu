@@ -33,7 +33,7 @@ constexpr int FD_THREADS = 512;
 // dense counters of the fine-grained step: 30,720 words (61,440 16-bit keys)
 constexpr int FD_WORDS = 30720;
 constexpr int FD_KEYS = 2 * FD_WORDS;
-using FdEngine = DenseSliceT<FD_WORDS>;
+using FdEngine = DenseSliceT<FD_WORDS, LOG_BUCKETS * 4>;  // scratch: the window histogram
 // walk-size flag: the vertex's degree is >= 65535 (counts may need 32 bits)
 constexpr unsigned long long WIDE_BIT = 1ull << 63;
 // heavy subsets: automatic threshold and levels enqueued per alive check
@@ -529,7 +529,7 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
                 // about `target` of them, become the window [.., T); a level
                 // then scans the window only, and members whose support
                 // falls below T during updates join it.
-                uint32_t *hist = (uint32_t *)H.tl;  // idle between passes
+                uint32_t *hist = (uint32_t *)H.scratch();  // idle between passes
                 for (int b = threadIdx.x; b < LOG_BUCKETS; b += blockDim.x) hist[b] = 0;
                 if (threadIdx.x == 0) {
                     s_pick = LOG_BUCKETS - 1;
@@ -751,6 +751,8 @@ struct FdhDev {
     unsigned long long level;    // mu of the last level
     unsigned long long wedges, levels;
     unsigned long long t0, t1;   // globaltimer at the start and at the end
+    unsigned long long cpeel;    // walk sizes of this level's peeled members with updates
+    unsigned long long rcnt;     // C_rcnt of the task's induced subgraph
     int32_t nalive, nkeep, nw, nb;
 };
 
@@ -780,6 +782,7 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 
 __global__ void k_fdh_reset(FdhDev *st, int32_t ni) {
     st->mn = st->mn_next = ~0ull;
+    st->cpeel = st->rcnt = 0;
     st->level = 0;
     st->wedges = st->levels = 0;
     st->t0 = globaltimer_ns();
@@ -808,7 +811,7 @@ __global__ void k_fdh_select(FdhArgs a) {
     const unsigned long long lv = a.st->level, mn = a.st->mn;
     const unsigned long long mu = mn > lv ? mn : lv;
     int32_t keep = 0;
-    unsigned long long kmin = ~0ull;
+    unsigned long long kmin = ~0ull, cpeel = 0;
     for (int32_t base = blockIdx.x * blockDim.x; base < a.ni; base += gridDim.x * blockDim.x) {
         const int32_t r = base + threadIdx.x;
         const bool al = r < a.ni && a.alive[r];
@@ -820,6 +823,7 @@ __global__ void k_fdh_select(FdhArgs a) {
         }
         const bool upd = peel && v > 0;
         const bool small = upd && a.wr[r] <= (unsigned long long)WARP_MAX_W;
+        if (upd) cpeel += a.wr[r] & ~WIDE_BIT;
         warp_append(small, r, &a.st->nw, a.Lw);
         warp_append(upd && !small, r, &a.st->nb, a.Lb);
         if (al && !peel) {
@@ -829,10 +833,58 @@ __global__ void k_fdh_select(FdhArgs a) {
     }
     keep = warp_sum(keep);
     kmin = warp_min(kmin);
+    cpeel = warp_sum(cpeel);
     if ((threadIdx.x & 31) == 0) {
         if (keep) atomicAdd(&a.st->nkeep, keep);
         if (kmin != ~0ull) atomicMin(&a.st->mn_next, kmin);
+        if (cpeel) atomicAdd(&a.st->cpeel, cpeel);
     }
+}
+
+// Hybrid update computation inside the fine-grained step (Sec. 4.1): a
+// member's support is the butterflies it shares with the vertices of higher
+// subsets (constant while its task is peeled: init minus its count inside
+// G_i) plus those it shares with the task's members still alive (its count
+// inside the alive part of G_i). A level of a heavy task may therefore
+// replace its updates by a recount of the alive part.
+//
+// C_rcnt of the task's induced subgraph: sum over its members' edges (x, y)
+// of min(d_x, d_y inside G_i).
+__global__ void k_fdh_rcnt(FdhArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long sum = 0;
+    for (int64_t r = w0; r < a.ni; r += nw) {
+        const int32_t x = a.mem[r];
+        const int64_t q0 = a.off_s[x], q1 = a.off_s[x + 1];
+        for (int64_t q = q0 + lane; q < q1; q += 32)
+            sum += (unsigned long long)imin64(q1 - q0, a.fd_len[q]);
+    }
+    sum = warp_sum(sum);
+    if (lane == 0 && sum) atomicAdd(&a.st->rcnt, sum);
+}
+
+// keep[mem[r]] = -1 for the task's members (alive ones only with alive_only),
+// the others of the side stay excluded (0).
+__global__ void k_fdh_keep(FdhArgs a, int32_t *__restrict__ keep, int alive_only) {
+    const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < a.ni && (!alive_only || a.alive[r])) keep[a.mem[r]] = -1;
+}
+
+// Supports of the alive members after a recount: init - (count inside G_i)
+// + (count inside the alive part of G_i); the next level's minimum follows.
+__global__ void k_fdh_apply(FdhArgs a, const unsigned long long *__restrict__ cnt0,
+                            const unsigned long long *__restrict__ cntr) {
+    const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long v = ~0ull;
+    if (r < a.ni && a.alive[r]) {
+        const int32_t x = a.mem[r];
+        v = a.init[x] - cnt0[x] + cntr[x];
+        a.fsup[r] = v;
+    }
+    v = warp_min(v);
+    if ((threadIdx.x & 31) == 0 && v != ~0ull) atomicMin(&a.st->mn_next, v);
 }
 
 __global__ void __launch_bounds__(256) k_fdh_warp(FdhArgs a) {
@@ -887,11 +939,74 @@ __global__ void k_fdh_next(FdhDev *st) {
     st->mn_next = ~0ull;
     st->nalive = st->nkeep;
     st->nkeep = st->nw = st->nb = 0;
+    st->cpeel = 0;
     st->levels++;
     if (st->nalive == 0) st->t1 = globaltimer_ns();
 }
 
 }  // namespace
+
+// Levels of one heavy task one at a time, each deciding on the host between
+// its updates and a recount of the task's alive members (hybrid update
+// computation, Sec. 4.1): with D.fd_huc == 1 every level with updates
+// recounts (test hook), otherwise a level whose peeled members' walks exceed
+// D.huc_factor * rcnt does. Exact either way.
+static void fdh_levels_with_recount(Decomp &D, const FdhArgs &ha, FdhDev *dst, FdhDev *hst_out,
+                             uint64_t rcnt, int grid_h, size_t smem_h, int gm, cudaStream_t s) {
+    const Side &S = *D.S;
+    const Side &O = *D.O;
+    const int32_t n = S.n;
+    const int sms = num_sms();
+    FdhDev *h = (FdhDev *)pinned_scratch(sizeof(FdhDev));
+    DevBuf<int32_t> keep, adjc, lenc;
+    DevBuf<unsigned long long> cnt0, cntr;
+    bool have0 = false;
+    // counts of the task's members (all, or the alive ones) inside G_i
+    auto count_members = [&](int alive_only, unsigned long long *out) {
+        if (!keep.get()) {
+            keep.alloc(n, s);
+            adjc.alloc(D.m, s);
+            lenc.alloc(O.n, s);
+        }
+        keep.zero();
+        k_fdh_keep<<<ceil_div(ha.ni, 256), 256, 0, s>>>(ha, keep.get(), alive_only);
+        RC_LAUNCH();
+        RC_CUDA(cudaMemcpyAsync(adjc.get(), O.adj, sizeof(int32_t) * D.m, cudaMemcpyDeviceToDevice, s));
+        list_lengths(O.off, O.n, lenc.get(), s);
+        compact_lists(O.off, lenc.get(), adjc.get(), O.n, keep.get(), s);
+        return recount_masked(S, O, D.s, D.m, keep.get(), out, lenc.get(), adjc.get(), s);
+    };
+    for (;;) {
+        k_fdh_select<<<gm, 256, 0, s>>>(ha);
+        RC_LAUNCH();
+        RC_CUDA(cudaMemcpyAsync(h, dst, sizeof(FdhDev), cudaMemcpyDeviceToHost, s));
+        RC_CUDA(cudaStreamSynchronize(s));
+        const bool updates = h->nw + h->nb > 0;
+        const bool recount =
+            updates && (D.fd_huc == 1 || (double)h->cpeel > D.huc_factor * (double)rcnt);
+        if (recount) {
+            if (!have0) {
+                cnt0.alloc(n, s);
+                cntr.alloc(n, s);
+                D.wedges_fd_recount += count_members(0, cnt0.get());
+                have0 = true;
+            }
+            D.wedges_fd_recount += count_members(1, cntr.get());
+            k_fdh_apply<<<ceil_div(ha.ni, 256), 256, 0, s>>>(ha, cnt0.get(), cntr.get());
+            RC_LAUNCH();
+            D.fd_recounts++;
+        } else {
+            k_fdh_warp<<<sms * 8, 256, 0, s>>>(ha);
+            RC_LAUNCH();
+            k_fdh_cta<<<grid_h, FD_THREADS, smem_h, s>>>(ha);
+            RC_LAUNCH();
+        }
+        k_fdh_next<<<1, 1, 0, s>>>(dst);
+        RC_LAUNCH();
+        if (h->nkeep == 0) break;
+    }
+    RC_CUDA(cudaMemcpyAsync(hst_out, dst, sizeof(FdhDev), cudaMemcpyDeviceToHost, s));
+}
 
 void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
     const int32_t n = D.n;
@@ -1112,6 +1227,22 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
             RC_LAUNCH();
             k_fdh_init<<<gi, 256, 0, s>>>(ha);
             RC_LAUNCH();
+            // Recount rule (Sec. 4.1) of this task: a level recounts when its
+            // peeled members' walks exceed factor * C_rcnt of the task; no
+            // level can when the task's whole walk weight does not.
+            bool may_recount = D.fd_huc == 1;
+            uint64_t rcnt = 0;
+            if (D.fd_huc == 0) {
+                k_fdh_rcnt<<<gi, 256, 0, s>>>(ha);
+                RC_LAUNCH();
+                RC_CUDA(cudaMemcpyAsync(&hh[h], hst.get(), sizeof(FdhDev), cudaMemcpyDeviceToHost, s));
+                RC_CUDA(cudaStreamSynchronize(s));
+                rcnt = hh[h].rcnt;
+                may_recount = rcnt > 0 && (double)tw[i] > D.huc_factor * (double)rcnt;
+            }
+            if (may_recount) {
+                fdh_levels_with_recount(D, ha, hst.get(), &hh[h], rcnt, grid_h, smem_h, gm, s);
+            } else
             // levels are enqueued in batches; the alive count of batch k is
             // checked while batch k + 1 runs (levels after the last change
             // nothing)

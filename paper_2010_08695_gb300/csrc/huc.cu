@@ -149,13 +149,16 @@ bool recount_fits(const Decomp &D) {
 
 uint64_t recount_remaining(const Decomp &D, const int32_t *len_w, const int32_t *adj_w,
                            cudaStream_t s) {
-    const Side &S = *D.S;
-    const Side &O = *D.O;
+    return recount_masked(*D.S, *D.O, D.s, D.m, D.sub, D.sup, len_w, adj_w, s);
+}
+
+uint64_t recount_masked(const Side &S, const Side &O, int side_s, int64_t m, const int32_t *sub,
+                        unsigned long long *sup, const int32_t *len_w, const int32_t *adj_w,
+                        cudaStream_t s) {
     const int32_t n = S.n, no = O.n;
-    const int64_t m = D.m;
     if (n == 0 || no == 0 || m == 0) return 0;
     DevBuf<int64_t> ls(n + 1, s), offs(n + 1, s), lo(no + 1, s), offo(no + 1, s);
-    k_len_remaining<<<ceil_div(n + 1, 256), 256, 0, s>>>(S.off, D.sub, n, ls.get());
+    k_len_remaining<<<ceil_div(n + 1, 256), 256, 0, s>>>(S.off, sub, n, ls.get());
     RC_LAUNCH();
     k_len_live<<<ceil_div(no + 1, 256), 256, 0, s>>>(len_w, no, lo.get());
     RC_LAUNCH();
@@ -173,7 +176,7 @@ uint64_t recount_remaining(const Decomp &D, const int32_t *len_w, const int32_t 
     lo.release();
     DevBuf<int32_t> adjs(mr, s), adjo(mr, s);
     if (mr > 0) {
-        k_gather_remaining<<<chunk_blocks(m), 256, 0, s>>>(S.off, n, S.adj, D.sub, m, offs.get(),
+        k_gather_remaining<<<chunk_blocks(m), 256, 0, s>>>(S.off, n, S.adj, sub, m, offs.get(),
                                                             adjs.get());
         RC_LAUNCH();
         k_gather_live<<<chunk_blocks(m), 256, 0, s>>>(O.off, no, adj_w, len_w, m, offo.get(),
@@ -181,14 +184,14 @@ uint64_t recount_remaining(const Decomp &D, const int32_t *len_w, const int32_t 
         RC_LAUNCH();
     }
     receipt_graph sg;
-    sg.side[D.s] = Side{n, offs.get(), adjs.get(), S.new2old, S.below, nullptr};
-    sg.side[1 - D.s] = Side{no, offo.get(), adjo.get(), O.new2old, O.below, nullptr};
+    sg.side[side_s] = Side{n, offs.get(), adjs.get(), S.new2old, S.below, nullptr};
+    sg.side[1 - side_s] = Side{no, offo.get(), adjo.get(), O.new2old, O.below, nullptr};
     sg.nu = sg.side[0].n;
     sg.nv = sg.side[1].n;
     sg.m = mr;
     DevBuf<unsigned long long> cu(sg.nu, s), cv(sg.nv, s);
     const uint64_t w = count_local(&sg, cu.get(), cv.get(), s);
-    k_apply_recount<<<ceil_div(n, 256), 256, 0, s>>>(n, D.sub, D.s ? cv.get() : cu.get(), D.sup);
+    k_apply_recount<<<ceil_div(n, 256), 256, 0, s>>>(n, sub, side_s ? cv.get() : cu.get(), sup);
     RC_LAUNCH();
     return w;
 }

@@ -10,8 +10,10 @@ receipt_graph *build_graph(const int32_t *d_eu, const int32_t *d_ev, int64_t m, 
 void destroy_graph(receipt_graph *g);
 
 // Butterfly counts of both sides by local id; returns wedges traversed.
+// points (optional, 4 entries) accumulates the start points per tier: warp,
+// CTA, global (by degree or key space), global after a repeat-table overflow.
 uint64_t count_local(const receipt_graph *g, unsigned long long *cnt_u, unsigned long long *cnt_v,
-                     cudaStream_t s);
+                     cudaStream_t s, int64_t *points = nullptr);
 void scatter_to_original(const unsigned long long *local, const int32_t *new2old, int32_t n,
                          unsigned long long *out, cudaStream_t s);
 // Counting with every temporary in a static device array (no allocation).
@@ -74,6 +76,15 @@ struct Decomp {
     // disjoint union (null otherwise)
     const std::vector<int64_t> *parts = nullptr;
     std::vector<receipt_subset> subsets;
+    int32_t fd_huc = 0;              // recount rule of the fine-grained step's heavy tasks
+    // factor of the recount rules (a range's first round of Algorithm 3, a
+    // heavy task's level of Algorithm 4, recounts when its walks exceed
+    // huc_factor * C_rcnt): per unit of the two cost measures the peel tiers
+    // run 4-10 times faster than the counting kernels (measured on Chung-Lu
+    // graphs of 10M and 100M edges), hence 8 by default
+    double huc_factor = 8.0;
+    int32_t fd_recounts = 0;         // levels of heavy tasks whose updates were a recount
+    uint64_t wedges_fd_recount = 0;  // wedges traversed by those recounts
     int32_t huc_recounts = 0;        // rounds whose updates were a recount (Sec. 4.1)
     uint64_t wedges_recount = 0;     // wedges traversed by those recounts
     uint64_t cost_recount = 0;       // C_rcnt = sum over edges of min(d_u, d_v)
@@ -94,6 +105,19 @@ bool recount_fits(const Decomp &D);
 // to remaining vertices. Returns the wedges traversed; synchronises s.
 uint64_t recount_remaining(const Decomp &D, const int32_t *len_w, const int32_t *adj_w,
                            cudaStream_t s);
+// The same for any kept set: counts, in the subgraph of the side-s vertices
+// x with sub[x] < 0 and all of the other side, of every kept vertex into
+// sup[x]. len_w/adj_w: the other side's lists (original offsets) already
+// compacted to kept vertices. Returns the wedges traversed; synchronises s.
+uint64_t recount_masked(const Side &S, const Side &O, int side_s, int64_t m, const int32_t *sub,
+                        unsigned long long *sup, const int32_t *len_w, const int32_t *adj_w,
+                        cudaStream_t s);
+// Drops from every list y of the other side (working copy adj_w with
+// lengths len_w, original offsets off_o) the entries x with sub[x] >= 0.
+void compact_lists(const int64_t *off_o, int32_t *len_w, int32_t *adj_w, int32_t n_o,
+                   const int32_t *sub, cudaStream_t s);
+// len[y] = off[y + 1] - off[y]
+void list_lengths(const int64_t *off, int32_t n, int32_t *len, cudaStream_t s);
 void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s);
 
 }  // namespace receipt

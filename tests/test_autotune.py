@@ -26,3 +26,18 @@ def test_shipped_table_is_valid():
         table = json.load(f)
     for key, rec in table.items():
         assert 0 < rec["warp_max_w"] <= 256 and rec["slice_min_w"] > 0
+
+
+def test_coordinate_search_picks_the_fastest_setting():
+    """The search visits every knob's candidates and keeps the fastest
+    combination (a synthetic cost with a known optimum, no GPU)."""
+    best = {"slice_ctas": 2, "warp_max_w": 128, "slice_min_w": 98304, "P": 300,
+            "range_max_n": -1, "dgm_frac_1024": 64}
+    calls = []
+
+    def cost(run, reps, **o):
+        calls.append(o)
+        return 1.0 + sum(o[k] != v for k, v in best.items())
+    rec, times = autotune.search(lambda **o: None, 1_000_000, time_fn=cost)
+    assert {k: rec[k] for k in best} == best and rec["ms"] == 1.0
+    assert len(times) == len(calls)

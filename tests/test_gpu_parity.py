@@ -47,10 +47,17 @@ def _check_graph(R, eu, ev, nu, nv, sides=(0, 1)):
     assert np.array_equal(gv, cv), "V counts differ"
     for side in sides:
         want, _ = oracle.bup(eu, ev, nu, nv, side)
-        got, _ = _gpu_tips(R, eu, ev, nu, nv, side)
+        got, g = _gpu_tips(R, eu, ev, nu, nv, side)
         bad = np.nonzero(got != want)[0]
         assert len(bad) == 0, f"side {side}: {len(bad)} tips differ, e.g. {bad[:5]} " \
                               f"got {got[bad[:5]]} want {want[bad[:5]]}"
+        # next activeSets from the support atomics' returned values, sliced
+        # tier at one CTA per SM, no vertex cap on the ranges
+        got = R.as_u64(g.tip_decompose(side, scan_frontier=-1, slice_ctas=1, range_max_n=-1))
+        assert np.array_equal(got, want), f"side {side}: crossings / slice_ctas=1 / no cap"
+        # a tight vertex cap on the ranges
+        got = R.as_u64(g.tip_decompose(side, range_max_n=max(1, (nu, nv)[side] // 500)))
+        assert np.array_equal(got, want), f"side {side}: range_max_n"
 
 
 def test_tiny_random_graphs(R):
@@ -97,6 +104,14 @@ def test_sliced_tier_over_several_key_slices(R):
         assert np.array_equal(t, want), f"slice_min_w={smw}"
         st = g.stats()
         assert st["peel_anchors"][3] > 0
+    # the tier's three shapes (1, 2 and 4 CTAs per SM over 2, 3 and 6 key
+    # slices here), with the next activeSet from crossings or from scans
+    for ctas in (1, 2, 4):
+        for scan in (-1, 1):
+            t = R.as_u64(g.tip_decompose(0, slice_min_w=2000, slice_ctas=ctas,
+                                         scan_frontier=scan, timing=True))
+            assert np.array_equal(t, want), f"slice_ctas={ctas} scan={scan}"
+            assert g.stats()["peel_anchors"][3] > 0
     t = R.as_u64(g.tip_decompose(0, warp_max_w=32))
     assert np.array_equal(t, want)
     # one subset of 150k ranks: the fine-grained step aggregates rank slices
@@ -303,6 +318,36 @@ def test_recount_rounds_give_same_tips(R):
     for i, (o, w) in enumerate(zip(outs, wants)):
         assert np.array_equal(R.as_u64(o), w), f"batch graph {i}"
     assert graphs[0].stats()["huc_recounts"] >= 1
+
+
+def test_fd_recount_levels_give_same_tips(R):
+    """Hybrid update computation inside the fine-grained step (Sec. 4.1):
+    heavy tasks (all tasks forced heavy) whose levels recount the task's
+    alive members instead of applying updates -- at every level, or by the
+    cost rule with a tiny factor -- give the oracle's tips on both sides,
+    for one subset and for several, and in a batch."""
+    nu, nv = 3000, 800
+    eu, ev = synth.chung_lu(nu, nv, 20000, 2.3, 2.2, seed=36)
+    g = R.Graph(eu, ev, nu, nv)
+    for side in (0, 1):
+        want, _ = oracle.bup(eu, ev, nu, nv, side)
+        for P in (1, 3, 12):
+            t = R.as_u64(g.tip_decompose(side, P=P, fd_heavy_w=1, fd_huc=1))
+            assert np.array_equal(t, want), f"side {side} P={P} forced"
+            st = g.stats()
+            assert st["fd_heavy_subsets"] > 0 and st["fd_recounts"] > 0
+            t = R.as_u64(g.tip_decompose(side, P=P, fd_heavy_w=1, fd_huc=0, huc_factor_1024=1))
+            assert np.array_equal(t, want), f"side {side} P={P} rule"
+            assert g.stats()["fd_recounts"] > 0
+    # never: no recount
+    t = R.as_u64(g.tip_decompose(0, P=3, fd_heavy_w=1, fd_huc=-1))
+    assert g.stats()["fd_recounts"] == 0
+    # a batch: tasks are packed graphs' parts of a subset
+    parts = [synth.chung_lu(400 + 50 * k, 120, 2500, 2.3, 2.2, seed=60 + k) for k in range(5)]
+    built = [R.Graph(a, b, 400 + 50 * k, 120) for k, (a, b) in enumerate(parts)]
+    outs = R.receipt_decompose_batch(built, [0] * 5, P=4, fd_heavy_w=1, fd_huc=1)
+    for k, ((a, b), o) in enumerate(zip(parts, outs)):
+        assert np.array_equal(R.as_u64(o), oracle.bup(a, b, 400 + 50 * k, 120, 0)[0]), f"graph {k}"
 
 
 def test_batch_equals_alone(R):
