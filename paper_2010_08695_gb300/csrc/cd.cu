@@ -348,6 +348,32 @@ struct CdEmit {
             atomicAdd(&sup[k], 0ull - d);
         }
     }
+    // N pairs at once (k < 0: none): the `sub` loads, then the support
+    // atomics, then the crossing checks, so their latencies overlap.
+    template <int N>
+    __device__ __forceinline__ void many(const int32_t (&k)[N], const uint32_t (&c)[N]) {
+        bool live[N];
+#pragma unroll
+        for (int u = 0; u < N; u++) live[u] = k[u] >= 0 && sub[k[u]] < 0;
+        unsigned long long old[N], d[N];
+#pragma unroll
+        for (int u = 0; u < N; u++) {
+            d[u] = choose2(c[u]);
+            old[u] = 0;
+            if (live[u]) {
+                pairs++;
+                if (next)
+                    old[u] = atomicAdd(&sup[k[u]], 0ull - d[u]);
+                else
+                    atomicAdd(&sup[k[u]], 0ull - d[u]);
+            }
+        }
+        if (next) {
+#pragma unroll
+            for (int u = 0; u < N; u++)
+                if (live[u] && old[u] >= hi && old[u] - d[u] < hi) next[atomicAdd(n_next, 1)] = k[u];
+        }
+    }
 };
 
 // Adds the support atomics of every thread of the calling warp to tier t's
@@ -416,6 +442,13 @@ struct SliceEmit {
     CdEmit *e;
     int32_t base;
     __device__ __forceinline__ void operator()(int32_t k, uint32_t c) { (*e)(k + base, c); }
+    template <int N>
+    __device__ __forceinline__ void many(const int32_t (&k)[N], const uint32_t (&c)[N]) {
+        int32_t kk[N];
+#pragma unroll
+        for (int u = 0; u < N; u++) kk[u] = k[u] >= 0 ? k[u] + base : -1;
+        e->template many<N>(kk, c);
+    }
 };
 
 struct PeelArgs {

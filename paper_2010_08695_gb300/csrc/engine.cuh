@@ -82,6 +82,71 @@ __device__ __forceinline__ void visit_many(V &v, const int (&kk)[N], const int32
     visit_many_impl<N>(v, kk, key, 0);
 }
 
+// Emits of up to N (key, count) pairs (key < 0: none). An emitter with a
+// many<N>() member gets them together (to overlap their memory operations);
+// others get one call per pair.
+template <int N, class E>
+__device__ __forceinline__ auto emit_many_impl(E &e, const int32_t (&k)[N], const uint32_t (&c)[N],
+                                               int) -> decltype(e.template many<N>(k, c), void()) {
+    e.template many<N>(k, c);
+}
+template <int N, class E>
+__device__ __forceinline__ void emit_many_impl(E &e, const int32_t (&k)[N], const uint32_t (&c)[N],
+                                               long) {
+#pragma unroll
+    for (int u = 0; u < N; u++)
+        if (k[u] >= 0) e(k[u], c[u]);
+}
+template <int N, class E>
+__device__ __forceinline__ void emit_many(E &e, const int32_t (&k)[N], const uint32_t (&c)[N]) {
+    emit_many_impl<N>(e, k, c, 0);
+}
+
+// Walks the segments of the middle vertices q in [q0, q1) with one warp, 32
+// middle vertices at a time: lane i fetches segment i, a warp scan of the
+// lengths numbers their wedges, and each lane takes wedges lane, lane + 32,
+// ..., finding its segment by a binary search over the lanes' starts, so all
+// key loads of a step are independent (U per lane in flight). visit(key).
+template <int U, class Mids, class Visit>
+__device__ __forceinline__ void warp_walk(const Mids &M, int64_t q0, int64_t q1,
+                                          const int32_t *__restrict__ keys, Visit &visit) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t qb = q0; qb < q1; qb += 32) {
+        int64_t beg = 0;
+        int32_t len = 0;
+        if (qb + lane < q1) M.seg(qb + lane, beg, len);
+        int32_t inc = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const int32_t total = __shfl_sync(0xffffffffu, inc, 31);
+        const int32_t ex = inc - len;
+        for (int32_t j0 = 0; j0 < total; j0 += 32 * U) {
+            int32_t key[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int32_t j = j0 + u * 32 + lane;
+                // last lane whose segment starts at or before j (all lanes
+                // take part in the shuffles)
+                int lo = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int32_t e = __shfl_sync(0xffffffffu, ex, lo + step);
+                    if (e <= j) lo += step;
+                }
+                const int64_t b = __shfl_sync(0xffffffffu, beg, lo);
+                const int32_t e0 = __shfl_sync(0xffffffffu, ex, lo);
+                key[u] = j < total ? __ldg(keys + b + (j - e0)) : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++)
+                if (key[u] >= 0) visit(key[u]);
+        }
+    }
+}
+
 // ------------------------------------------------------------------
 // Warp-private table
 // ------------------------------------------------------------------
@@ -114,6 +179,28 @@ struct WarpHash {
             h = (h + 1) & (WARP_SLOTS - 1);
         }
         return false;
+    }
+    // emit(key, count) for every key with count >= 2, 8 slots per lane at a
+    // time (emits overlapped), and clears the table. One warp.
+    template <class Emit>
+    __device__ __forceinline__ void flush_clear(Emit &emit, int lane) {
+        for (int s0 = 0; s0 < WARP_SLOTS; s0 += 32 * 8) {
+            int32_t kk[8];
+            uint32_t cc[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int sl = s0 + u * 32 + lane;
+                const int32_t k = key[sl];
+                const uint32_t c = val[sl];
+                kk[u] = (k != EMPTY_KEY && c >= 2) ? k : -1;
+                cc[u] = c;
+                if (k != EMPTY_KEY) {
+                    key[sl] = EMPTY_KEY;
+                    val[sl] = 0;
+                }
+            }
+            emit_many<8>(emit, kk, cc);
+        }
     }
     __device__ uint32_t lookup(int32_t k) const {
         uint32_t h = hash_key(k) & (WARP_SLOTS - 1);
@@ -397,6 +484,8 @@ struct DenseSliceT {
     }
     // EMIT: emit(key, count) for every key with count >= 2; CLEAR: zero the
     // touched words and their bits. The caller synchronises afterwards.
+    // Words are taken 4 at a time from a bitmap word, so up to 8 emits of a
+    // thread are issued together.
     template <bool EMIT, bool CLEAR, class Emit>
     __device__ void sweep(Emit &emit) {
         const int nbw = (hw + 31) >> 5;
@@ -405,19 +494,31 @@ struct DenseSliceT {
             if (m == 0) continue;
             if (CLEAR) tbm[b] = 0;
             do {
-                const int w = (b << 5) + __ffs(m) - 1;
-                m &= m - 1;
-                const uint32_t v = cnt[w];
-                if (CLEAR) cnt[w] = 0;
-                if (EMIT) {
+                int32_t kk[8];
+                uint32_t cc[8];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    int w = -1;
+                    if (m) {
+                        w = (b << 5) + __ffs(m) - 1;
+                        m &= m - 1;
+                    }
+                    const uint32_t v = w >= 0 ? cnt[w] : 0u;
+                    if (CLEAR && w >= 0) cnt[w] = 0;
                     if (wide) {
-                        if (v >= 2) emit(w, v);
+                        kk[2 * u] = v >= 2 ? w : -1;
+                        cc[2 * u] = v;
+                        kk[2 * u + 1] = -1;
+                        cc[2 * u + 1] = 0;
                     } else {
                         const uint32_t c0 = v & 0xffffu, c1 = v >> 16;
-                        if (c0 >= 2) emit(w, c0);
-                        if (c1 >= 2) emit(w + hw, c1);
+                        kk[2 * u] = c0 >= 2 ? w : -1;
+                        cc[2 * u] = c0;
+                        kk[2 * u + 1] = c1 >= 2 ? w + hw : -1;
+                        cc[2 * u + 1] = c1;
                     }
                 }
+                if (EMIT) emit_many<8>(emit, kk, cc);
             } while (m);
         }
     }

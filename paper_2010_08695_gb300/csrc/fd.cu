@@ -267,6 +267,29 @@ struct FdEmit {
             }
         }
     }
+    // N pairs at once (k < 0: none): all `alive` loads, then all support
+    // atomics, then the bookkeeping, so their latencies overlap.
+    template <int N>
+    __device__ __forceinline__ void many(const int32_t (&k)[N], const uint32_t (&c)[N]) {
+        bool al[N];
+#pragma unroll
+        for (int u = 0; u < N; u++) al[u] = k[u] >= 0 && alive[k[u]];
+        unsigned long long old[N], d[N];
+#pragma unroll
+        for (int u = 0; u < N; u++) {
+            d[u] = choose2(c[u]);
+            old[u] = al[u] ? atomicAdd(&fsup[k[u]], 0ull - d[u]) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < N; u++) {
+            if (!al[u]) continue;
+            const unsigned long long nv = old[u] - d[u];
+            if (nv < T) {
+                atomicMin(mn, nv);
+                if (old[u] >= T) cand[atomicAdd(n_cand, 1)] = k[u];
+            }
+        }
+    }
 };
 
 // Ranks of one slice [base, end) of the subset's rank space: the run of a
@@ -302,6 +325,13 @@ struct FdSliceEmit {
     FdEmit *e;
     int32_t base;
     __device__ __forceinline__ void operator()(int32_t k, uint32_t c) { (*e)(k + base, c); }
+    template <int N>
+    __device__ __forceinline__ void many(const int32_t (&k)[N], const uint32_t (&c)[N]) {
+        int32_t kk[N];
+#pragma unroll
+        for (int u = 0; u < N; u++) kk[u] = k[u] >= 0 ? k[u] + base : -1;
+        e->template many<N>(kk, c);
+    }
 };
 
 // Several anchors of one level aggregated in one pass: anchor slot a of the
@@ -353,6 +383,13 @@ struct FdBatchEmit {
     FdEmit *e;
     int32_t ni;
     __device__ __forceinline__ void operator()(int32_t w, uint32_t c) { (*e)(w % ni, c); }
+    template <int N>
+    __device__ __forceinline__ void many(const int32_t (&k)[N], const uint32_t (&c)[N]) {
+        int32_t kk[N];
+#pragma unroll
+        for (int u = 0; u < N; u++) kk[u] = k[u] >= 0 ? k[u] % ni : -1;
+        e->template many<N>(kk, c);
+    }
 };
 
 // Update of one peeled member r (anchor x, edges [q0, q1) of side s) whose
@@ -361,31 +398,13 @@ __device__ __forceinline__ void fd_update_warp(WarpHash &WH, const FdMids &M,
                                                const int32_t *__restrict__ fd_adj, int64_t q0,
                                                int64_t q1, int32_t r, int32_t kb, int lane,
                                                FdEmit &emit) {
-    for (int64_t qb = q0; qb < q1; qb += 32) {
-        const int64_t q = qb + lane;
-        int64_t beg = 0;
-        int32_t len = 0;
-        if (q < q1) M.seg(q, beg, len);
-        const int cnt = (int)imin64(32, q1 - qb);
-        for (int t2 = 0; t2 < cnt; t2++) {
-            const int64_t b = __shfl_sync(0xffffffffu, beg, t2);
-            const int32_t l = __shfl_sync(0xffffffffu, len, t2);
-            for (int p = lane; p < l; p += 32) {
-                const int32_t k = fd_adj[b + p] - kb;
-                if (k != r) WH.add(k);
-            }
-        }
-    }
+    auto add = [&](int32_t key) {
+        const int32_t k = key - kb;
+        if (k != r) WH.add(k);
+    };
+    warp_walk<4>(M, q0, q1, fd_adj, add);
     __syncwarp();
-    for (int sl = lane; sl < WARP_SLOTS; sl += 32) {
-        const int32_t k = WH.key[sl];
-        if (k != EMPTY_KEY) {
-            const uint32_t c = WH.val[sl];
-            if (c >= 2) emit(k, c);
-            WH.key[sl] = EMPTY_KEY;
-            WH.val[sl] = 0;
-        }
-    }
+    WH.flush_clear(emit, lane);
     __syncwarp();
 }
 
@@ -612,36 +631,44 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
             // peel every window member with support <= mu; the rest go to
             // the other window buffer (ballot compaction, order irrelevant)
             int peeled = 0;
-            for (int base = 0; base < ncand; base += blockDim.x) {
-                const int j = base + threadIdx.x;
-                int32_t r = -1;
-                unsigned long long v = 0;
-                if (j < ncand) {
-                    r = clist[j];
-                    v = fsup[r];
+            constexpr int SCAN_U = 4;  // window entries per thread with their loads in flight
+            for (int base0 = 0; base0 < ncand; base0 += SCAN_U * blockDim.x) {
+                int32_t rr[SCAN_U];
+                unsigned long long vv[SCAN_U];
+#pragma unroll
+                for (int u = 0; u < SCAN_U; u++) {
+                    const int j = base0 + u * blockDim.x + threadIdx.x;
+                    rr[u] = j < ncand ? clist[j] : -1;
                 }
-                const bool keep = r >= 0 && v > mu;
-                const bool peel = r >= 0 && !keep;
-                unsigned long long w = 0;
-                if (peel) {
-                    alive[r] = 0;
-                    a.tip[a.new2old[mem[r]]] = mu;
-                    w = wr[r];
-                    peeled++;
+#pragma unroll
+                for (int u = 0; u < SCAN_U; u++) vv[u] = rr[u] >= 0 ? fsup[rr[u]] : 0ull;
+#pragma unroll
+                for (int u = 0; u < SCAN_U; u++) {
+                    const int32_t r = rr[u];
+                    const unsigned long long v = vv[u];
+                    const bool keep = r >= 0 && v > mu;
+                    const bool peel = r >= 0 && !keep;
+                    unsigned long long w = 0;
+                    if (peel) {
+                        alive[r] = 0;
+                        a.tip[a.new2old[mem[r]]] = mu;
+                        w = wr[r];
+                        peeled++;
+                    }
+                    // updates: small walks -> one warp each; bigger ones -> the
+                    // batched pass; degree >= 65535 (32-bit counts) or a subset
+                    // too large to batch -> one anchor per pass (end of blist)
+                    const bool upd = peel && v > 0;
+                    const bool small = upd && w <= (unsigned long long)WARP_MAX_W;
+                    const bool single = upd && !small && ((w & WIDE_BIT) || bk == 1);
+                    warp_append(keep, r, &s_nk, clist_next);
+                    warp_append(small, r, &s_np, plist);
+                    warp_append(upd && !small && !single, r, &s_nbig, blist);
+                    if (single) blist[ni - 1 - atomicAdd(&s_nwide, 1)] = r;
+                    // minimum of the survivors before this level's updates
+                    const unsigned long long kv = warp_min(keep ? v : ~0ull);
+                    if (lane == 0 && kv != ~0ull) atomicMin(&s_mn, kv);
                 }
-                // updates: small walks -> one warp each; bigger ones -> the
-                // batched pass; degree >= 65535 (32-bit counts) or a subset
-                // too large to batch -> one anchor per pass (end of blist)
-                const bool upd = peel && v > 0;
-                const bool small = upd && w <= (unsigned long long)WARP_MAX_W;
-                const bool single = upd && !small && ((w & WIDE_BIT) || bk == 1);
-                warp_append(keep, r, &s_nk, clist_next);
-                warp_append(small, r, &s_np, plist);
-                warp_append(upd && !small && !single, r, &s_nbig, blist);
-                if (single) blist[ni - 1 - atomicAdd(&s_nwide, 1)] = r;
-                // minimum of the survivors before this level's updates
-                const unsigned long long kv = warp_min(keep ? v : ~0ull);
-                if (lane == 0 && kv != ~0ull) atomicMin(&s_mn, kv);
             }
             peeled = warp_sum(peeled);
             if (lane == 0 && peeled) atomicAdd(&s_peel, peeled);
