@@ -209,10 +209,10 @@ typedef struct {
      * support changes). */
     uint64_t peel_pairs[5];
     /* Start points of Algorithm 1 per aggregation tier, both sides: warp
-     * table, shared-memory hybrid, global counters (degree >= 65535 or a key
-     * space beyond shared memory), global counters after the hybrid's repeat
-     * table overflowed. */
-    int64_t count_points[4];
+     * table, shared hash table (at most 2,048 wedges), shared-memory hybrid,
+     * global counters (degree >= 65535 or a key space beyond shared memory),
+     * global counters after the hybrid's repeat table overflowed. */
+    int64_t count_points[5];
     /* Levels of the fine-grained step's heavy tasks whose updates were a
      * recount (see receipt_options.fd_huc), and the wedges those recounts
      * traversed. */

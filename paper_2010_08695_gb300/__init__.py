@@ -69,7 +69,7 @@ class Stats(ctypes.Structure):
                 ("huc_recounts", ctypes.c_int32), ("wedges_recount", ctypes.c_uint64),
                 ("cost_recount", ctypes.c_uint64), ("ms_recount", ctypes.c_float),
                 ("reserved3", ctypes.c_int32), ("peel_pairs", ctypes.c_uint64 * 5),
-                ("count_points", ctypes.c_int64 * 4), ("fd_recounts", ctypes.c_int64),
+                ("count_points", ctypes.c_int64 * 5), ("fd_recounts", ctypes.c_int64),
                 ("wedges_fd_recount", ctypes.c_uint64)]
 
 

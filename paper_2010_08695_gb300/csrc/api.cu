@@ -250,7 +250,7 @@ void tip_decompose_impl(receipt_graph *g, int side, uint64_t *d_tip, const recei
     }
     unsigned long long h_wbup = 0;
     RC_CUDA(cudaMemcpyAsync(&h_wbup, wbup.get(), 8, cudaMemcpyDeviceToHost, s));
-    int64_t cpoints[4] = {0, 0, 0, 0};
+    int64_t cpoints[5] = {0, 0, 0, 0, 0};
     uint64_t wc = count_local(g, cu.get(), cv.get(), s, cpoints);
     T.mark();
     D.sup = side ? cv.get() : cu.get();
@@ -274,7 +274,7 @@ void tip_decompose_impl(receipt_graph *g, int side, uint64_t *d_tip, const recei
     receipt_stats &st = g->stats;
     st = receipt_stats{};
     st.wedges_count = wc;
-    for (int t = 0; t < 4; t++) st.count_points[t] = cpoints[t];
+    for (int t = 0; t < 5; t++) st.count_points[t] = cpoints[t];
     st.wedges_bup = h_wbup;
     st.wedges_cd = D.wedges_cd;
     st.wedges_fd = D.wedges_fd;
@@ -558,7 +558,7 @@ receipt_status receipt_count_butterflies(receipt_graph *g, uint64_t *d_cnt_u, ui
         check_count_bound(g);
         cudaStream_t s = (cudaStream_t)stream;
         DevBuf<unsigned long long> cu(g->nu, s), cv(g->nv, s);
-        int64_t cpoints[4] = {0, 0, 0, 0};
+        int64_t cpoints[5] = {0, 0, 0, 0, 0};
         uint64_t w = count_local(g, cu.get(), cv.get(), s, cpoints);
         if (d_cnt_u)
             scatter_to_original(cu.get(), g->side[0].new2old, g->nu, (unsigned long long *)d_cnt_u, s);
@@ -566,7 +566,7 @@ receipt_status receipt_count_butterflies(receipt_graph *g, uint64_t *d_cnt_u, ui
             scatter_to_original(cv.get(), g->side[1].new2old, g->nv, (unsigned long long *)d_cnt_v, s);
         g->stats = receipt_stats{};
         g->stats.wedges_count = w;
-        for (int t = 0; t < 4; t++) g->stats.count_points[t] = cpoints[t];
+        for (int t = 0; t < 5; t++) g->stats.count_points[t] = cpoints[t];
     });
 }
 

@@ -667,37 +667,60 @@ __global__ void __launch_bounds__(Shape::threads, 1024 / Shape::threads)
     k_cd_update_slice(PeelArgs a, int32_t n) {
     using Engine = typename Shape::Engine;
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ long long s_idx;
-    __shared__ int s_nt;
+    __shared__ long long s_items[32];
+    __shared__ int s_nitems, s_pos;
     if (a.st->nLs == 0) return;
     Engine H;
-    unsigned char *p = H.bind(smem, &s_nt);
+    unsigned char *p = H.bind(smem);
     Chunk ch;
     ch.beg = (int64_t *)p;
     ch.pre = (int32_t *)(ch.beg + Shape::threads);
     ch.tmp = ch.pre + Shape::threads + 1;
     ch.len = chunk_len_ptr(ch.tmp);
     H.clear_all();
+    if (threadIdx.x == 0) s_nitems = s_pos = 0;
     __syncthreads();
     CdEmit emit{a.sup, a.sub, a.st->hi, a.scan ? nullptr : a.next, &a.st->nNext, 0};
     unsigned long long cw = 0, cm = 0, ca = 0;
     const int64_t items = (int64_t)a.st->nLs * a.C;
+    const int lane = threadIdx.x & 31;
     for (;;) {
-        // next (anchor, slice) item whose slice meets the anchor's window
-        if (threadIdx.x == 0) {
-            int64_t it;
-            for (;;) {
-                it = atomicAdd((unsigned long long *)&a.st->work64, 1ull);
-                if (it >= items) break;
-                const int64_t ai = it / a.C;
-                const int32_t jj = (int32_t)(it % a.C);
-                if (jj >= a.Ls_lo[ai] && jj <= a.Ls_hi[ai]) break;
+        // warp 0 refills the CTA's batch of (anchor, slice) items whose slice
+        // meets the anchor's window: 32 consecutive item numbers per atomic,
+        // checked by the 32 lanes at once
+        if (threadIdx.x < 32) {
+            __syncwarp();
+            if (s_pos >= s_nitems) {
+                int nvalid = 0;
+                bool done = false;
+                while (nvalid == 0 && !done) {
+                    unsigned long long b = 0;
+                    if (lane == 0) b = atomicAdd((unsigned long long *)&a.st->work64, 32ull);
+                    b = __shfl_sync(0xffffffffu, b, 0);
+                    const int64_t it = (int64_t)b + lane;
+                    bool ok = false;
+                    if (it < items) {
+                        const int64_t ai = it / a.C;
+                        const int32_t jj = (int32_t)(it % a.C);
+                        ok = jj >= a.Ls_lo[ai] && jj <= a.Ls_hi[ai];
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, ok);
+                    if (ok) s_items[__popc(bal & lanemask_lt())] = it;
+                    nvalid = __popc(bal);
+                    done = (int64_t)b + 32 >= items;
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    s_nitems = nvalid;
+                    s_pos = 0;
+                }
             }
-            s_idx = it < items ? it : -1;
         }
         __syncthreads();
-        const int64_t idx = s_idx;
-        if (idx < 0) break;
+        if (s_pos >= s_nitems) break;  // no item left
+        const int64_t idx = s_items[s_pos];
+        __syncthreads();
+        if (threadIdx.x == 0) s_pos++;
         const int64_t ai = idx / a.C;
         const int32_t x = a.Ls[ai];
         const int32_t j = (int32_t)(idx % a.C);

@@ -52,12 +52,20 @@ __global__ void k_plen_i64(const int32_t *__restrict__ plen, int64_t m, int64_t 
     if (q < m) out[q] = plen[q];
 }
 
-// Splits start points into tiers by their exact wedge count.
+// Start points with at most HASH_W wedges (and more than WARP_MAX_W) take the
+// shared hash tier: small CTAs, any key space, any degree.
+constexpr int HASH_SLOTS = 4096;
+constexpr int HASH_W = HASH_SLOTS / 2;
+constexpr int HASH_THREADS = 256;
+using CountHash = CtaHashT<HASH_SLOTS>;
+
+// Splits start points into tiers by their exact wedge count (lh: the hash
+// tier, null to leave it out).
 __global__ void k_count_tiers(const int64_t *__restrict__ offA, const int64_t *__restrict__ pscan,
                               int32_t nA, int64_t m, int64_t cta_keyspace_max,
                               int32_t *__restrict__ lw, int32_t *__restrict__ lc,
-                              int32_t *__restrict__ lg, int32_t *__restrict__ nl,
-                              unsigned long long *wedges) {
+                              int32_t *__restrict__ lg, int32_t *__restrict__ lh,
+                              int32_t *__restrict__ nl, unsigned long long *wedges) {
     int32_t sp = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long wsum = 0;
     if (sp < nA) {
@@ -70,6 +78,8 @@ __global__ void k_count_tiers(const int64_t *__restrict__ offA, const int64_t *_
             int64_t deg = e - b;
             if (W <= WARP_MAX_W)
                 lw[atomicAdd(&nl[0], 1)] = sp;
+            else if (lh && W <= HASH_W)
+                lh[atomicAdd(&nl[8], 1)] = sp;
             else if (deg < 65535 && sp <= cta_keyspace_max)
                 lc[atomicAdd(&nl[1], 1)] = sp;
             else
@@ -335,6 +345,50 @@ __global__ void __maxnreg__(64) k_count_global(CountArgs a, const int32_t *over_
     }
 }
 
+// Start points with at most HASH_W wedges: one 256-thread CTA each (several
+// per SM) with a shared hash table; the same two walks as the CTA tier.
+__global__ void __launch_bounds__(HASH_THREADS, 4) k_count_hash(CountArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_idx, s_nt;
+    __shared__ unsigned long long s_red[32];
+    CountHash H;
+    unsigned char *p = H.bind(smem, &s_nt);
+    Chunk ch;
+    ch.beg = (int64_t *)p;
+    unsigned long long *sacc = (unsigned long long *)(ch.beg + HASH_THREADS);
+    ch.pre = (int32_t *)(sacc + HASH_THREADS);
+    ch.tmp = ch.pre + HASH_THREADS + 1;
+    ch.len = chunk_len_ptr(ch.tmp);
+    H.clear_all();
+    for (int i = threadIdx.x; i < HASH_THREADS; i += blockDim.x) sacc[i] = 0;
+    __syncthreads();
+    const int32_t n = *a.nlist;
+    CountMids M{a.adjA, a.offB, a.plen};
+    NoEmit ne;
+    for (;;) {
+        if (threadIdx.x == 0) s_idx = atomicAdd(a.work, 1);
+        __syncthreads();
+        const int idx = s_idx;
+        if (idx >= n) break;
+        const int32_t sp = a.list[idx];
+        const int64_t q0 = a.offA[sp], q1 = a.offA[sp + 1];
+        AddVisit<CountHash> add{&H};
+        cta_walk(M, q0, q1, a.adjB, ch, add);
+        CountSameEmit<CountHash> em{a.cntA, 0};
+        H.sweep<true, false>(em);
+        const unsigned long long tot = block_sum_u64(em.acc, s_red);
+        if (threadIdx.x == 0 && tot) atomicAdd(&a.cntA[sp], tot);
+        CountOppVisit<CountHash> ov{&H, sacc};
+        CountOppHook hook{a.adjA, a.cntB, sacc};
+        cta_walk(M, q0, q1, a.adjB, ch, ov, &hook);
+        H.sweep<false, true>(ne);
+        __syncthreads();
+        H.reset_scalars();
+    }
+}
+
+size_t count_hash_smem() { return CountHash::bytes() + HASH_THREADS * 8 + chunk_bytes(HASH_THREADS); }
+
 __global__ void k_scatter_counts(const unsigned long long *__restrict__ cnt,
                                  const int32_t *__restrict__ new2old, int32_t n,
                                  unsigned long long *__restrict__ out) {
@@ -381,10 +435,11 @@ uint64_t count_local(const receipt_graph *g, unsigned long long *cnt_u,
         const int64_t cta_ks_max = max_cta_keyspace(nA, MID_CHUNK * 8 + CHUNK_BYTES);
         int32_t headn = 0, bmw = 0;
         size_t smem = cta_ks_max > 0 ? count_cta_smem(cta_ks_max, &headn, &bmw) : 0;
-        DevBuf<int32_t> lw(nA, s), lc(nA, s), lg(nA, s), lo(nA, s);
-        int32_t *nl = ctr.get();  // [0] warp [1] cta [2] global [3] overflow, [4..7] work
+        DevBuf<int32_t> lw(nA, s), lc(nA, s), lg(nA, s), lo(nA, s), lh(nA, s);
+        // [0] warp [1] cta [2] global [3] overflow, [4..7] work, [8] hash, [9] its work
+        int32_t *nl = ctr.get();
         k_count_tiers<<<ceil_div(nA, 256), 256, 0, s>>>(SA.off, pscan.get(), nA, m, cta_ks_max,
-                                                       lw.get(), lc.get(), lg.get(), nl,
+                                                       lw.get(), lc.get(), lg.get(), lh.get(), nl,
                                                        wedges.get());
         RC_LAUNCH();
         unsigned long long *cA = A ? cnt_v : cnt_u;
@@ -392,6 +447,19 @@ uint64_t count_local(const receipt_graph *g, unsigned long long *cnt_u,
         CountArgs a{SA.off, SA.adj, SB.off, SB.adj, plen.get(), cA, cB, lw.get(), nl + 0, nl + 4};
         k_count_warp<<<sms * 8, 256, 0, s>>>(a);
         RC_LAUNCH();
+        {
+            const size_t hsm = count_hash_smem();
+            allow_max_smem((const void *)k_count_hash);
+            int occ = 1;
+            RC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_count_hash, HASH_THREADS,
+                                                                  hsm));
+            CountArgs c = a;
+            c.list = lh.get();
+            c.nlist = nl + 8;
+            c.work = nl + 9;
+            k_count_hash<<<sms * std::max(1, occ), HASH_THREADS, hsm, s>>>(c);
+            RC_LAUNCH();
+        }
         if (cta_ks_max > 0) {
             allow_max_smem((const void *)k_count_cta);
             CountArgs c = a;
@@ -402,11 +470,16 @@ uint64_t count_local(const receipt_graph *g, unsigned long long *cnt_u,
             RC_LAUNCH();
         }
         // global tier: hubs + overflowed anchors; key space [0, nA)
-        int32_t hn[4];
+        int32_t hn[10];
         RC_CUDA(cudaMemcpyAsync(hn, nl, sizeof(hn), cudaMemcpyDeviceToHost, s));
         RC_CUDA(cudaStreamSynchronize(s));
-        if (points)
-            for (int t = 0; t < 4; t++) points[t] += hn[t];
+        if (points) {
+            points[0] += hn[0];
+            points[1] += hn[8];
+            points[2] += hn[1];
+            points[3] += hn[2];
+            points[4] += hn[3];
+        }
         if (hn[2] + hn[3] > 0) {
             const int gblocks = std::min(sms, hn[2] + hn[3]);
             DevBuf<uint32_t> gcnt((size_t)gblocks * nA, s);

@@ -215,6 +215,90 @@ struct WarpHash {
 };
 
 // ------------------------------------------------------------------
+// CTA hash: open addressing over any key space, for anchors with few wedges
+// ------------------------------------------------------------------
+// SLOTS (key, count) pairs at load <= 1/2: an anchor with at most SLOTS / 2
+// wedges always finds room (it cannot touch more distinct keys). Every slot
+// taken is listed, so flushing and clearing cost what the anchor touched.
+template <int SLOTS>
+struct CtaHashT {
+    static_assert((SLOTS & (SLOTS - 1)) == 0 && SLOTS <= 65536, "slots");
+    int32_t *key;   // SLOTS
+    uint32_t *val;  // SLOTS
+    uint16_t *tl;   // SLOTS / 2: slots taken
+    int *s_nt;      // shared scalar: slots taken
+
+    static constexpr size_t bytes() { return (size_t)SLOTS * 8 + (size_t)SLOTS; }
+    __device__ unsigned char *bind(unsigned char *base, int *nt) {
+        key = (int32_t *)base;
+        val = (uint32_t *)(key + SLOTS);
+        tl = (uint16_t *)(val + SLOTS);
+        s_nt = nt;
+        return base + bytes();
+    }
+    __device__ void clear_all() {
+        for (int i = threadIdx.x; i < SLOTS; i += blockDim.x) {
+            key[i] = EMPTY_KEY;
+            val[i] = 0;
+        }
+        if (threadIdx.x == 0) *s_nt = 0;
+    }
+    __device__ __forceinline__ void add(int32_t k) {
+        uint32_t h = hash_key(k) & (SLOTS - 1);
+        for (int p = 0; p < SLOTS; p++) {
+            const int32_t cur = ((volatile int32_t *)key)[h];
+            if (cur == k) {
+                atomicAdd(&val[h], 1u);
+                return;
+            }
+            if (cur == EMPTY_KEY) {
+                const int32_t prev = atomicCAS(&key[h], EMPTY_KEY, k);
+                if (prev == EMPTY_KEY) {
+                    atomicAdd(&val[h], 1u);
+                    tl[atomicAdd(s_nt, 1)] = (uint16_t)h;
+                    return;
+                }
+                if (prev == k) {
+                    atomicAdd(&val[h], 1u);
+                    return;
+                }
+            }
+            h = (h + 1) & (SLOTS - 1);
+        }
+    }
+    __device__ __forceinline__ uint32_t count(int32_t k) const {
+        uint32_t h = hash_key(k) & (SLOTS - 1);
+        for (int p = 0; p < SLOTS; p++) {
+            const int32_t cur = key[h];
+            if (cur == k) return val[h];
+            if (cur == EMPTY_KEY) return 0;
+            h = (h + 1) & (SLOTS - 1);
+        }
+        return 0;
+    }
+    // EMIT: emit(key, count) for every key with count >= 2; CLEAR: empty the
+    // slots taken. The caller synchronises afterwards, then reset_scalars().
+    template <bool EMIT, bool CLEAR, class Emit>
+    __device__ void sweep(Emit &emit) {
+        const int nt = *(volatile int *)s_nt;
+        for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+            const int h = tl[i];
+            if (EMIT) {
+                const uint32_t c = val[h];
+                if (c >= 2) emit(key[h], c);
+            }
+            if (CLEAR) {
+                key[h] = EMPTY_KEY;
+                val[h] = 0;
+            }
+        }
+    }
+    __device__ void reset_scalars() {
+        if (threadIdx.x == 0) *s_nt = 0;
+    }
+};
+
+// ------------------------------------------------------------------
 // CTA hybrid: dense head counters + tail bitmap + repeat table
 // ------------------------------------------------------------------
 // Keys below `headn` (low labels = high degree, where repeated end points
@@ -471,11 +555,18 @@ struct DenseSliceT {
         wide = wide_counts;
         hw = wide ? w : (w + 1) >> 1;
     }
+    // The lanes that touch a word first set its bit; lanes whose words share
+    // a bitmap word (consecutive keys) combine their bits into one atomic.
     __device__ __forceinline__ void add(int32_t k) {
         const bool hi = !wide && k >= hw;
         const int32_t w = hi ? k - hw : k;
         const uint32_t old = atomicAdd(&cnt[w], hi ? 0x10000u : 1u);
-        if (old == 0) atomicOr(&tbm[w >> 5], 1u << (w & 31));
+        const unsigned first = __ballot_sync(__activemask(), old == 0);
+        if (old == 0) {
+            const unsigned grp = __match_any_sync(first, w >> 5);
+            const unsigned bits = __reduce_or_sync(grp, 1u << (w & 31));
+            if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicOr(&tbm[w >> 5], bits);
+        }
     }
     __device__ __forceinline__ uint32_t count(int32_t k) const {
         if (wide) return cnt[k];

@@ -10,8 +10,9 @@ receipt_graph *build_graph(const int32_t *d_eu, const int32_t *d_ev, int64_t m, 
 void destroy_graph(receipt_graph *g);
 
 // Butterfly counts of both sides by local id; returns wedges traversed.
-// points (optional, 4 entries) accumulates the start points per tier: warp,
-// CTA, global (by degree or key space), global after a repeat-table overflow.
+// points (optional, 5 entries) accumulates the start points per tier: warp,
+// shared hash, CTA hybrid, global (by degree or key space), global after a
+// repeat-table overflow.
 uint64_t count_local(const receipt_graph *g, unsigned long long *cnt_u, unsigned long long *cnt_v,
                      cudaStream_t s, int64_t *points = nullptr);
 void scatter_to_original(const unsigned long long *local, const int32_t *new2old, int32_t n,
