@@ -342,7 +342,7 @@ def measure_graph(R, name, args, dist=None, world=1, local=0, clocks=True, e2e=T
         # end to end through the C ABI with host buffers: H2D of the edges,
         # build, decomposition, D2H of the tips, with the step's options
         e2e_opt = {k: tuned.get(k, 0) for k in ("warp_max_w", "slice_min_w", "dgm_frac_1024",
-                                                 "slice_ctas", "range_max_n")}
+                                                 "slice_ctas", "range_max_n", "slice_fetch")}
         e2e_opt.update(huc=args.huc, huc_factor_1024=args.huc_factor_1024,
                        round_graphs=args.round_graphs)
         eu_h = torch.from_numpy(eu).pin_memory().numpy()

@@ -153,6 +153,9 @@ typedef struct {
      * many vertices with small walks holds few wedges but as many levels of
      * Algorithm 4 as distinct supports. Speed only (Theorem 2). */
     int32_t range_max_n;
+    /* Key-sliced tier: (anchor, slice) items a CTA takes per work-counter
+     * atomic, consecutive slices of one anchor (1..32; 0 = 1). Speed only. */
+    int32_t slice_fetch;
 } receipt_options;
 
 /* Counters of the last call on a graph (Sec. 5: wedges and rounds). */

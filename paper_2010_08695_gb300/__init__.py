@@ -50,7 +50,8 @@ class Options(ctypes.Structure):
                 ("fd_heavy_w", ctypes.c_int64), ("round_graphs", ctypes.c_int32),
                 ("huc", ctypes.c_int32), ("huc_factor_1024", ctypes.c_int32),
                 ("slice_ctas", ctypes.c_int32), ("scan_frontier", ctypes.c_int32),
-                ("fd_huc", ctypes.c_int32), ("range_max_n", ctypes.c_int32)]
+                ("fd_huc", ctypes.c_int32), ("range_max_n", ctypes.c_int32),
+                ("slice_fetch", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -185,10 +186,11 @@ def _dptr(t):
 def _options(P=150, bounds=None, subset=None, bounds_out=None, p_eff=None, timing=False,
              warp_max_w=0, slice_min_w=0, dgm=True, dgm_frac_1024=0, fd_heavy_w=0,
              round_graphs=False, huc=0, huc_factor_1024=0, slice_ctas=0, scan_frontier=0,
-             fd_huc=0, range_max_n=0):
+             fd_huc=0, range_max_n=0, slice_fetch=0):
     o = Options()
     load().receipt_options_default(ctypes.byref(o))
     o.P = int(P)
+    o.slice_fetch = int(slice_fetch)
     o.fd_huc = int(fd_huc)
     o.range_max_n = int(range_max_n)
     o.slice_ctas = int(slice_ctas)
@@ -350,7 +352,7 @@ class Graph:
                       timing=False, out=None, stream=None, warp_max_w=0, slice_min_w=0, dgm=True,
                       dgm_frac_1024=0, fd_heavy_w=0, round_graphs=False, huc=0,
                       huc_factor_1024=0, slice_ctas=0, scan_frontier=None, fd_huc=0,
-                      range_max_n=None):
+                      range_max_n=None, slice_fetch=0):
         """Tip numbers of ``side`` (Algorithms 3 and 4). P = 0 takes the tuned
         value for this graph's shape class, else 150. With ``subsets=True``
         returns ``(tips, subset_of_vertex, range_bounds)``. ``huc``: 0 = the
@@ -372,6 +374,7 @@ class Graph:
                 scan_frontier = tuned.get("scan_frontier", 0)
             if range_max_n is None:
                 range_max_n = tuned.get("range_max_n", 0)
+            slice_fetch = slice_fetch or tuned.get("slice_fetch", 0)
         P = P or 150
         tip = out if out is not None else torch.empty(n, dtype=torch.int64, device=self.device)
         sub = torch.empty(n, dtype=torch.int32, device=self.device) if subsets else None
@@ -380,7 +383,8 @@ class Graph:
         peff = ctypes.c_int32(0)
         o, keep = _options(P, bounds, sub, bout, peff, timing, warp_max_w, slice_min_w, dgm,
                            dgm_frac_1024, fd_heavy_w, round_graphs, huc, huc_factor_1024,
-                           slice_ctas, int(scan_frontier or 0), fd_huc, int(range_max_n or 0))
+                           slice_ctas, int(scan_frontier or 0), fd_huc, int(range_max_n or 0),
+                           slice_fetch)
         receipt_tip_decompose(self._h, side, tip, o, stream)
         if subsets:
             return tip, sub, bout[: peff.value + 1]
@@ -406,7 +410,8 @@ def receipt_decompose_batch(graphs, sides, outs=None, P: int = 0, stream=None, t
     if tuned and n > 0:
         from . import autotune
         rec = autotune.lookup(autotune.batch_shape_class(graphs, sides)) or {}
-        for k in ("warp_max_w", "slice_min_w", "dgm_frac_1024", "slice_ctas", "range_max_n"):
+        for k in ("warp_max_w", "slice_min_w", "dgm_frac_1024", "slice_ctas", "range_max_n",
+                  "slice_fetch"):
             if k in rec and not options.get(k):
                 options[k] = rec[k]
         P = P or rec.get("P", 0)

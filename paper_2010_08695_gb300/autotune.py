@@ -77,11 +77,12 @@ def _time(run, reps, **kw):
 
 def knobs(n: int):
     """Candidate values of every tuned option, in search order: the sliced
-    tier's shape, the tier thresholds (which anchors, by walk size, take the
+    tier's shape and its items per fetch, the tier thresholds (which anchors, by walk size, take the
     warp table, the shared-memory hybrid or the key slices), P, the vertex
     cap of a range (absolute; -1 none, 0 = 2 n / P) and the compaction
     trigger of dynamic graph maintenance."""
     return [("slice_ctas", (4, 2, 1)),
+            ("slice_fetch", (1, 2, 4)),
             ("warp_max_w", WARP_MAX_W),
             ("slice_min_w", SLICE_MIN_W),
             ("P", P_CANDIDATES),
@@ -95,8 +96,8 @@ def search(run, n: int, reps: int = 1, time_fn=None):
     `time_fn(run, reps, **options)` times it (default: CUDA events, best of
     `reps`). Returns (best options with their time in ms, all timings)."""
     _time_fn = time_fn or _time
-    cur = {"slice_ctas": 4, "warp_max_w": 256, "slice_min_w": SLICE_MIN_W[0], "P": 150,
-           "range_max_n": 0, "dgm_frac_1024": 128}
+    cur = {"slice_ctas": 4, "slice_fetch": 1, "warp_max_w": 256, "slice_min_w": SLICE_MIN_W[0],
+           "P": 150, "range_max_n": 0, "dgm_frac_1024": 128}
     run(**cur)  # warm-up
     times = {}
 

@@ -475,6 +475,7 @@ struct PeelArgs {
     int32_t SW;            // keys per slice
     int32_t n_keys;        // keys of the side
     int32_t scan;          // next activeSet by a scan after the round (no crossing detection)
+    int32_t fetch;         // sliced tier: candidate items per work-counter atomic (1..32)
 };
 
 __global__ void __launch_bounds__(256) k_cd_update_warp(PeelArgs a) {
@@ -655,19 +656,21 @@ template <int THREADS, int WORDS>
 struct SliceShape {
     static constexpr int threads = THREADS;
     static constexpr int keys = 2 * WORDS;
-    using Engine = DenseSliceT<WORDS>;
+    using Engine = DenseSliceT<WORDS, TOUCH_BITMAP>;
     static constexpr size_t smem() { return Engine::bytes() + chunk_bytes(THREADS); }
 };
 using Slice1 = SliceShape<SLICE_THREADS, 51200>;
 using Slice2 = SliceShape<512, 25600>;
 using Slice4 = SliceShape<256, 12672>;
 
+constexpr int SLICE_FETCH_MAX = 32;  // candidate items per work-counter atomic, at most
+
 template <class Shape>
 __global__ void __launch_bounds__(Shape::threads, 1024 / Shape::threads)
     k_cd_update_slice(PeelArgs a, int32_t n) {
     using Engine = typename Shape::Engine;
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ long long s_items[32];
+    __shared__ long long s_items[SLICE_FETCH_MAX];
     __shared__ int s_nitems, s_pos;
     if (a.st->nLs == 0) return;
     Engine H;
@@ -686,20 +689,24 @@ __global__ void __launch_bounds__(Shape::threads, 1024 / Shape::threads)
     const int lane = threadIdx.x & 31;
     for (;;) {
         // warp 0 refills the CTA's batch of (anchor, slice) items whose slice
-        // meets the anchor's window: 32 consecutive item numbers per atomic,
-        // checked by the 32 lanes at once
+        // meets the anchor's window: a.fetch consecutive item numbers per
+        // atomic, checked by as many lanes at once. Items are numbered anchor
+        // by anchor (item = anchor * C + j): consecutive slices of one anchor
+        // share its middle vertices' table rows and list positions.
         if (threadIdx.x < 32) {
             __syncwarp();
             if (s_pos >= s_nitems) {
+                const int fetch = a.fetch;
                 int nvalid = 0;
                 bool done = false;
                 while (nvalid == 0 && !done) {
                     unsigned long long b = 0;
-                    if (lane == 0) b = atomicAdd((unsigned long long *)&a.st->work64, 32ull);
+                    if (lane == 0)
+                        b = atomicAdd((unsigned long long *)&a.st->work64, (unsigned long long)fetch);
                     b = __shfl_sync(0xffffffffu, b, 0);
                     const int64_t it = (int64_t)b + lane;
                     bool ok = false;
-                    if (it < items) {
+                    if (lane < fetch && it < items) {
                         const int64_t ai = it / a.C;
                         const int32_t jj = (int32_t)(it % a.C);
                         ok = jj >= a.Ls_lo[ai] && jj <= a.Ls_hi[ai];
@@ -707,7 +714,7 @@ __global__ void __launch_bounds__(Shape::threads, 1024 / Shape::threads)
                     const unsigned bal = __ballot_sync(0xffffffffu, ok);
                     if (ok) s_items[__popc(bal & lanemask_lt())] = it;
                     nvalid = __popc(bal);
-                    done = (int64_t)b + 32 >= items;
+                    done = (int64_t)b + fetch >= items;
                 }
                 __syncwarp();
                 if (lane == 0) {
@@ -1040,6 +1047,7 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
                               : slice_ctas == 2 ? Slice2::smem() : Slice1::smem();
     const int32_t SW = slice_ctas == 4 ? Slice4::keys : slice_ctas == 2 ? Slice2::keys : Slice1::keys;
     const bool scan_next = opt.scan_frontier >= 0;
+    const int32_t slice_fetch = opt.slice_fetch > 0 ? std::min(opt.slice_fetch, SLICE_FETCH_MAX) : 1;
     // vertices per range: at most range_max_n (0: 2 n / P, -1: no bound)
     const int32_t range_cap =
         opt.range_max_n < 0 ? 0
@@ -1160,7 +1168,8 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
         PeelArgs a{S.off,     S.adj,      O.off,       len_w.get(), adj_w.get(), D.sup, D.sub,
                    st.get(),  Lw.get(),   Lc.get(),    Lg.get(),    Ls.get(), nxt,
                    Lc_k.get(), Lc_w.get(), Ls_lo.get(), Ls_hi.get(), Ld.get(), Ld_k.get(),
-                   Ld_w.get(), table ? soff.get() : nullptr, C, SW, n, scan_next ? 1 : 0};
+                   Ld_w.get(), table ? soff.get() : nullptr, C, SW, n, scan_next ? 1 : 0,
+                   slice_fetch};
         mark(0);
         k_cd_update_warp<<<sms * 8, 256, 0, q>>>(a);
         RC_LAUNCH();

@@ -516,38 +516,54 @@ inline size_t hybrid_bytes(int64_t keyspace, int32_t *head_cap_out = nullptr,
 // ------------------------------------------------------------------
 // Key k < hw sits in the low half of word k, key k >= hw in the high half of
 // word k - hw (hw = half the slice), so consecutive keys of a sorted list hit
-// different words. The first increment of a word sets its bit in a bitmap of
-// touched words, so flushing and clearing visit the words the slice touched
-// (one bitmap word per 32 counter words). Counts must stay below 2^16 (the
-// caller routes anchors of degree >= 65535 elsewhere) unless the slice is set
-// up with 32-bit counters. SCRATCH extra bytes after the bitmap are free for
-// the caller between passes.
+// different words. Flushing and clearing visit only the words the slice
+// touched, found one of two ways (TRACK):
+//  * TOUCH_LIST -- the first increment of a word appends it to a list (one
+//    shared atomic per warp and step); past the list's capacity (TCAP) the
+//    sweep scans the slice. Suits narrow key ranges (consecutive keys).
+//  * TOUCH_BITMAP -- the first increment of a word sets its bit in a bitmap
+//    (one bit per counter word, no capacity). Suits wide slices where a
+//    warp's keys are far apart (its bitmap words differ).
+// Counts must stay below 2^16 (the caller routes anchors of degree >= 65535
+// elsewhere) unless the slice is set up with 32-bit counters. SCRATCH extra
+// bytes after the tracking structure are free for the caller between passes.
 constexpr int DENSE_KEYS = 36864;               // keys per dense slice
 constexpr int DENSE_WORDS = DENSE_KEYS / 2;     // 18432 words (72 KB)
+constexpr int TOUCH_CAP = 8192;                 // touched-word list capacity
+enum { TOUCH_LIST = 0, TOUCH_BITMAP = 1 };
 
-template <int WORDS, int SCRATCH = 0>
+template <int WORDS, int TRACK = TOUCH_LIST, int SCRATCH = 0>
 struct DenseSliceT {
-    static_assert(WORDS % 128 == 0, "counter words");
+    static_assert(WORDS % 128 == 0 && WORDS <= 65536, "counter words");
     static constexpr int BM_WORDS = WORDS / 32;
+    static constexpr int TCAP = TOUCH_CAP;
+    static constexpr size_t track_bytes() {
+        return TRACK == TOUCH_BITMAP ? (size_t)BM_WORDS * 4 : (size_t)TCAP * 2;
+    }
     uint32_t *cnt;     // WORDS
-    uint32_t *tbm;     // BM_WORDS: touched counter words
+    uint32_t *tbm;     // BM_WORDS: touched counter words (bitmap tracking)
+    uint16_t *tl;      // TCAP: touched counter words (list tracking)
+    int *s_nt;         // shared scalar: list entries (list tracking)
     int32_t hw;        // half of the current slice width (<= WORDS)
     bool wide;         // 32-bit counters, one key per word (slices of WORDS keys)
 
     static constexpr size_t bytes() {
-        return (size_t)WORDS * 4 + (size_t)BM_WORDS * 4 + (size_t)((SCRATCH + 15) & ~15);
+        return (size_t)WORDS * 4 + track_bytes() + (size_t)((SCRATCH + 15) & ~15);
     }
-    __device__ unsigned char *bind(unsigned char *base, int * = nullptr) {
+    __device__ unsigned char *bind(unsigned char *base, int *nt = nullptr) {
         cnt = (uint32_t *)base;
         tbm = cnt + WORDS;
+        tl = (uint16_t *)(cnt + WORDS);
+        s_nt = nt;
         hw = WORDS;
         wide = false;
         return (unsigned char *)base + bytes();
     }
-    __device__ void *scratch() const { return (void *)(tbm + BM_WORDS); }
+    __device__ void *scratch() const { return (void *)((unsigned char *)(cnt + WORDS) + track_bytes()); }
     __device__ void clear_all() {
-        for (int i = threadIdx.x; i < (WORDS + BM_WORDS) / 4; i += blockDim.x)
-            ((uint4 *)cnt)[i] = make_uint4(0, 0, 0, 0);
+        const int n4 = TRACK == TOUCH_BITMAP ? (WORDS + BM_WORDS) / 4 : WORDS / 4;
+        for (int i = threadIdx.x; i < n4; i += blockDim.x) ((uint4 *)cnt)[i] = make_uint4(0, 0, 0, 0);
+        if (TRACK == TOUCH_LIST && threadIdx.x == 0) *s_nt = 0;
     }
     // Slice of w keys: 16-bit counters (w <= 2 * WORDS), or 32-bit counters
     // when counts may reach 2^16 (w <= WORDS).
@@ -555,17 +571,26 @@ struct DenseSliceT {
         wide = wide_counts;
         hw = wide ? w : (w + 1) >> 1;
     }
-    // The lanes that touch a word first set its bit; lanes whose words share
-    // a bitmap word (consecutive keys) combine their bits into one atomic.
     __device__ __forceinline__ void add(int32_t k) {
         const bool hi = !wide && k >= hw;
         const int32_t w = hi ? k - hw : k;
         const uint32_t old = atomicAdd(&cnt[w], hi ? 0x10000u : 1u);
-        const unsigned first = __ballot_sync(__activemask(), old == 0);
-        if (old == 0) {
-            const unsigned grp = __match_any_sync(first, w >> 5);
-            const unsigned bits = __reduce_or_sync(grp, 1u << (w & 31));
-            if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicOr(&tbm[w >> 5], bits);
+        if (TRACK == TOUCH_BITMAP) {
+            if (old == 0) atomicOr(&tbm[w >> 5], 1u << (w & 31));
+        } else {
+            const unsigned m = __activemask();
+            const unsigned b = __ballot_sync(m, old == 0);
+            if (b) {
+                const int lane = threadIdx.x & 31;
+                const int leader = __ffs(b) - 1;
+                int base = 0;
+                if (lane == leader) base = atomicAdd(s_nt, __popc(b));
+                base = __shfl_sync(m, base, leader);
+                if (old == 0) {
+                    const int pos = base + __popc(b & lanemask_lt());
+                    if (pos < TCAP) tl[pos] = (uint16_t)w;
+                }
+            }
         }
     }
     __device__ __forceinline__ uint32_t count(int32_t k) const {
@@ -573,47 +598,77 @@ struct DenseSliceT {
         const bool hi = k >= hw;
         return (cnt[hi ? k - hw : k] >> (hi ? 16 : 0)) & 0xffffu;
     }
-    // EMIT: emit(key, count) for every key with count >= 2; CLEAR: zero the
-    // touched words and their bits. The caller synchronises afterwards.
-    // Words are taken 4 at a time from a bitmap word, so up to 8 emits of a
-    // thread are issued together.
-    template <bool EMIT, bool CLEAR, class Emit>
-    __device__ void sweep(Emit &emit) {
-        const int nbw = (hw + 31) >> 5;
-        for (int b = threadIdx.x; b < nbw; b += blockDim.x) {
-            uint32_t m = tbm[b];
-            if (m == 0) continue;
-            if (CLEAR) tbm[b] = 0;
-            do {
-                int32_t kk[8];
-                uint32_t cc[8];
+    // (key, count) pairs of up to four counter words, for emit_many.
+    __device__ __forceinline__ void pairs4(const int (&w)[4], const uint32_t (&v)[4], int32_t (&kk)[8],
+                                           uint32_t (&cc)[8]) const {
 #pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    int w = -1;
-                    if (m) {
-                        w = (b << 5) + __ffs(m) - 1;
-                        m &= m - 1;
-                    }
-                    const uint32_t v = w >= 0 ? cnt[w] : 0u;
-                    if (CLEAR && w >= 0) cnt[w] = 0;
-                    if (wide) {
-                        kk[2 * u] = v >= 2 ? w : -1;
-                        cc[2 * u] = v;
-                        kk[2 * u + 1] = -1;
-                        cc[2 * u + 1] = 0;
-                    } else {
-                        const uint32_t c0 = v & 0xffffu, c1 = v >> 16;
-                        kk[2 * u] = c0 >= 2 ? w : -1;
-                        cc[2 * u] = c0;
-                        kk[2 * u + 1] = c1 >= 2 ? w + hw : -1;
-                        cc[2 * u + 1] = c1;
-                    }
-                }
-                if (EMIT) emit_many<8>(emit, kk, cc);
-            } while (m);
+        for (int u = 0; u < 4; u++) {
+            if (wide) {
+                kk[2 * u] = w[u] >= 0 && v[u] >= 2 ? w[u] : -1;
+                cc[2 * u] = v[u];
+                kk[2 * u + 1] = -1;
+                cc[2 * u + 1] = 0;
+            } else {
+                const uint32_t c0 = v[u] & 0xffffu, c1 = v[u] >> 16;
+                kk[2 * u] = w[u] >= 0 && c0 >= 2 ? w[u] : -1;
+                cc[2 * u] = c0;
+                kk[2 * u + 1] = w[u] >= 0 && c1 >= 2 ? w[u] + hw : -1;
+                cc[2 * u + 1] = c1;
+            }
         }
     }
-    __device__ void reset_scalars() {}
+    // EMIT: emit(key, count) for every key with count >= 2; CLEAR: zero the
+    // touched words (and their bits). Four words at a time per thread, so up
+    // to 8 emits are issued together. The caller synchronises afterwards,
+    // then reset_scalars().
+    template <bool EMIT, bool CLEAR, class Emit>
+    __device__ void sweep(Emit &emit) {
+        int32_t kk[8];
+        uint32_t cc[8];
+        int w[4];
+        uint32_t v[4];
+        if (TRACK == TOUCH_BITMAP) {
+            const int nbw = (hw + 31) >> 5;
+            for (int b = threadIdx.x; b < nbw; b += blockDim.x) {
+                uint32_t m = tbm[b];
+                if (m == 0) continue;
+                if (CLEAR) tbm[b] = 0;
+                do {
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        w[u] = -1;
+                        if (m) {
+                            w[u] = (b << 5) + __ffs(m) - 1;
+                            m &= m - 1;
+                        }
+                        v[u] = w[u] >= 0 ? cnt[w[u]] : 0u;
+                        if (CLEAR && w[u] >= 0) cnt[w[u]] = 0;
+                    }
+                    pairs4(w, v, kk, cc);
+                    if (EMIT) emit_many<8>(emit, kk, cc);
+                } while (m);
+            }
+            return;
+        }
+        const int nt = *(volatile int *)s_nt;
+        const bool listed = nt <= TCAP;
+        const int n = listed ? nt : hw;  // list entries, or every word of the slice
+        for (int i0 = threadIdx.x; i0 < n; i0 += 4 * blockDim.x) {
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int i = i0 + u * blockDim.x;
+                w[u] = i < n ? (listed ? (int)tl[i] : i) : -1;
+                v[u] = w[u] >= 0 ? cnt[w[u]] : 0u;
+                if (v[u] == 0) w[u] = -1;
+                if (CLEAR && w[u] >= 0) cnt[w[u]] = 0;
+            }
+            pairs4(w, v, kk, cc);
+            if (EMIT) emit_many<8>(emit, kk, cc);
+        }
+    }
+    __device__ void reset_scalars() {
+        if (TRACK == TOUCH_LIST && threadIdx.x == 0) *s_nt = 0;
+    }
 };
 
 using DenseSlice = DenseSliceT<DENSE_WORDS>;

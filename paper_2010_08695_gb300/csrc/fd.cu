@@ -33,7 +33,9 @@ constexpr int FD_THREADS = 512;
 // dense counters of the fine-grained step: 30,720 words (61,440 16-bit keys)
 constexpr int FD_WORDS = 30720;
 constexpr int FD_KEYS = 2 * FD_WORDS;
-using FdEngine = DenseSliceT<FD_WORDS, LOG_BUCKETS * 4>;  // scratch: the window histogram
+// the touched-word list doubles as the window histogram between passes
+using FdEngine = DenseSliceT<FD_WORDS, TOUCH_LIST>;
+static_assert(TOUCH_CAP * 2 >= LOG_BUCKETS * 4, "histogram in the touched-word list");
 // walk-size flag: the vertex's degree is >= 65535 (counts may need 32 bits)
 constexpr unsigned long long WIDE_BIT = 1ull << 63;
 // heavy subsets: automatic threshold and levels enqueued per alive check
@@ -42,6 +44,10 @@ constexpr unsigned long long HEAVY_SHARE = 8;
 constexpr int HEAVY_LEVELS_PER_CHECK = 4;
 // parts of one subset are merged into tasks of at least this many members
 constexpr int32_t TASK_MIN = 8192;
+// LPT weight of one member of a task in wedges: a level of the one-CTA peel
+// costs ~20-40 us (measured on Chung-Lu graphs of 10M-100M edges), the time
+// a CTA needs for ~2^15 wedges of updates
+constexpr unsigned long long LEVEL_WEDGES = 1ull << 15;
 
 __global__ void k_sub_keys(const int32_t *__restrict__ sub, int32_t n, uint64_t *__restrict__ key,
                            uint32_t *__restrict__ val, int32_t *__restrict__ cnt) {
@@ -548,7 +554,7 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
                 // about `target` of them, become the window [.., T); a level
                 // then scans the window only, and members whose support
                 // falls below T during updates join it.
-                uint32_t *hist = (uint32_t *)H.scratch();  // idle between passes
+                uint32_t *hist = (uint32_t *)H.tl;  // idle between passes
                 for (int b = threadIdx.x; b < LOG_BUCKETS; b += blockDim.x) hist[b] = 0;
                 if (threadIdx.x == 0) {
                     s_pick = LOG_BUCKETS - 1;
@@ -1168,12 +1174,14 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
         RC_CUDA(cudaMemcpyAsync(tw.data(), dtw.get(), 8 * (size_t)T, cudaMemcpyDeviceToHost, s));
         RC_CUDA(cudaStreamSynchronize(s));
     }
-    // LPT order (ties by task id)
+    // LPT order (ties by task id). A task's time is its walks plus its
+    // levels, each level a chain of dependent steps inside one CTA; levels
+    // are at most its members, so a member counts as LEVEL_WEDGES wedges.
     std::vector<int32_t> hq(T);
     for (int k = 0; k < T; k++) hq[k] = k;
     std::stable_sort(hq.begin(), hq.end(), [&](int32_t x, int32_t y) {
-        const unsigned long long kx = tw[x] + (unsigned long long)tlen[x];
-        const unsigned long long ky = tw[y] + (unsigned long long)tlen[y];
+        const unsigned long long kx = tw[x] + LEVEL_WEDGES * (unsigned long long)tlen[x];
+        const unsigned long long ky = tw[y] + LEVEL_WEDGES * (unsigned long long)tlen[y];
         return kx > ky;
     });
     const size_t warp_tables = (size_t)(FD_THREADS / 32) * WARP_SLOTS * 8 + 16;

@@ -31,8 +31,8 @@ def test_shipped_table_is_valid():
 def test_coordinate_search_picks_the_fastest_setting():
     """The search visits every knob's candidates and keeps the fastest
     combination (a synthetic cost with a known optimum, no GPU)."""
-    best = {"slice_ctas": 2, "warp_max_w": 128, "slice_min_w": 98304, "P": 300,
-            "range_max_n": -1, "dgm_frac_1024": 64}
+    best = {"slice_ctas": 2, "slice_fetch": 4, "warp_max_w": 128, "slice_min_w": 98304,
+            "P": 300, "range_max_n": -1, "dgm_frac_1024": 64}
     calls = []
 
     def cost(run, reps, **o):
