@@ -88,22 +88,32 @@ void *pinned_scratch(size_t bytes) {
 }
 
 namespace {
+// per device: [0] the capture stream, [1..NUM_TIER_STREAMS] the tier streams
 struct CaptureTLS {
-    cudaStream_t s[64] = {};
+    cudaStream_t s[64][1 + NUM_TIER_STREAMS] = {};
     ~CaptureTLS() {
-        for (auto &x : s)
-            if (x) cudaStreamDestroy(x);
+        for (auto &d : s)
+            for (auto &x : d)
+                if (x) cudaStreamDestroy(x);
     }
 };
 thread_local CaptureTLS g_capture;
-}  // namespace
 
-cudaStream_t aux_stream() {
+cudaStream_t device_stream(int k) {
     int d = 0;
     RC_CUDA(cudaGetDevice(&d));
     if (d < 0 || d >= 64) fail(RECEIPT_ERR_INTERNAL, "device index out of range");
-    if (!g_capture.s[d]) RC_CUDA(cudaStreamCreateWithFlags(&g_capture.s[d], cudaStreamNonBlocking));
-    return g_capture.s[d];
+    if (!g_capture.s[d][k])
+        RC_CUDA(cudaStreamCreateWithFlags(&g_capture.s[d][k], cudaStreamNonBlocking));
+    return g_capture.s[d][k];
+}
+}  // namespace
+
+cudaStream_t aux_stream() { return device_stream(0); }
+
+cudaStream_t tier_stream(int k) {
+    if (k < 0 || k >= NUM_TIER_STREAMS) fail(RECEIPT_ERR_INTERNAL, "tier stream index");
+    return device_stream(1 + k);
 }
 
 int num_sms() { return dev_info().sms; }

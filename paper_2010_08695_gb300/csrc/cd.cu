@@ -1113,6 +1113,17 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
     const size_t hdr = offsetof(CdDev, hist_w);
     unsigned long long prev_w[NTIER] = {}, prev_a[NTIER] = {};
 
+    // fork/join of the tier streams (no timing)
+    cudaEvent_t fork_ev[1 + NUM_TIER_STREAMS] = {};
+    struct ForkGuard {
+        cudaEvent_t *e;
+        ~ForkGuard() {
+            for (int i = 0; i < 1 + NUM_TIER_STREAMS; i++)
+                if (e[i]) cudaEventDestroy(e[i]);
+        }
+    } fg{fork_ev};
+    for (int i = 0; i < 1 + NUM_TIER_STREAMS; i++)
+        RC_CUDA(cudaEventCreateWithFlags(&fork_ev[i], cudaEventDisableTiming));
     // ev[0..NTIER]: peel tiers; ev[NTIER + 1..NTIER + 2]: a recount
     cudaEvent_t ev[NTIER + 3] = {};
     struct EvGuard {
@@ -1170,11 +1181,25 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
                    Lc_k.get(), Lc_w.get(), Ls_lo.get(), Ls_hi.get(), Ld.get(), Ld_k.get(),
                    Ld_w.get(), table ? soff.get() : nullptr, C, SW, n, scan_next ? 1 : 0,
                    slice_fetch};
+        // The tiers' anchors are disjoint and their support decrements are
+        // atomic, so without per-tier timing the warp, dense-window and
+        // global tiers run on their own streams beside the hybrid and sliced
+        // tiers (the sliced tier takes the hybrid's overflows: same stream),
+        // and the tiers a round leaves empty cost no serial launch gaps.
+        const bool fork = !D.timing;
+        cudaStream_t qs[NUM_TIER_STREAMS] = {q, q, q};
+        if (fork) {
+            RC_CUDA(cudaEventRecord(fork_ev[0], q));
+            for (int k = 0; k < NUM_TIER_STREAMS; k++) {
+                qs[k] = tier_stream(k);
+                RC_CUDA(cudaStreamWaitEvent(qs[k], fork_ev[0], 0));
+            }
+        }
         mark(0);
-        k_cd_update_warp<<<sms * 8, 256, 0, q>>>(a);
+        k_cd_update_warp<<<sms * 8, 256, 0, qs[0]>>>(a);
         RC_LAUNCH();
         mark(1);
-        k_cd_update_dense<<<dblocks, DENSE_THREADS, DenseSlice::bytes() + CHUNK_BYTES, q>>>(a);
+        k_cd_update_dense<<<dblocks, DENSE_THREADS, DenseSlice::bytes() + CHUNK_BYTES, qs[1]>>>(a);
         RC_LAUNCH();
         mark(2);
         if (cta_ok) {
@@ -1183,8 +1208,8 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
         }
         mark(3);
         if (hubs) {
-            k_cd_update_global<<<gblocks, CTA_THREADS, smem_glob, q>>>(a, gcnt.get(), gtouch.get(),
-                                                                      n);
+            k_cd_update_global<<<gblocks, CTA_THREADS, smem_glob, qs[2]>>>(a, gcnt.get(),
+                                                                          gtouch.get(), n);
             RC_LAUNCH();
         }
         mark(4);
@@ -1195,6 +1220,11 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
             RC_LAUNCH();
         }
         mark(5);
+        if (fork)
+            for (int k = 0; k < NUM_TIER_STREAMS; k++) {
+                RC_CUDA(cudaEventRecord(fork_ev[1 + k], qs[k]));
+                RC_CUDA(cudaStreamWaitEvent(q, fork_ev[1 + k], 0));
+            }
         if (scan_next) {
             // next activeSet: remaining vertices whose support is now below hi
             k_cd_frontier<<<nb, 512, 0, q>>>(n, D.sub, D.sup, D.wfull, st.get(), &st.get()->nNext,

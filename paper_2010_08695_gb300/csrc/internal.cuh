@@ -28,6 +28,10 @@ void *pinned_scratch(size_t bytes);
 // Non-blocking auxiliary stream of the calling thread on the current device:
 // CUDA graphs are captured on it, and counting runs its second pass on it.
 cudaStream_t aux_stream();
+// Non-blocking streams of the calling thread on the current device on which
+// the independent peel tiers of one round run side by side.
+constexpr int NUM_TIER_STREAMS = 3;
+cudaStream_t tier_stream(int k);
 
 // Largest key space whose CtaHybrid engine plus `extra` bytes fits in the
 // opt-in shared memory of one CTA (capped at `want`); 0 if none.
