@@ -752,23 +752,53 @@ __device__ int64_t cta_walk(const Mids &M, int64_t q0, int64_t q1, const int32_t
     const unsigned lanes_le = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
     for (int64_t c0 = q0; c0 < q1; c0 += blockDim.x) {
         const int nm = (int)imin64(blockDim.x, q1 - c0);
-        int64_t beg = 0;
-        int32_t len = 0;
-        if ((int)threadIdx.x < nm) M.seg(c0 + threadIdx.x, beg, len);
         long long tot2;
-        const long long packed = (long long)len | (len > 0 ? (1ll << 40) : 0ll);
-        const long long ex2 = block_exclusive_scan<long long, false>(packed, s_scan, &tot2);
-        const int32_t ex = (int32_t)(ex2 & ((1ll << 40) - 1));
-        const int32_t slot = (int32_t)(ex2 >> 40);
+        if (nm <= 32) {
+            // at most 32 middle vertices: warp 0 stages them with a warp scan
+            // (one barrier instead of the block scan's three)
+            if (warp == 0) {
+                int64_t beg = 0;
+                int32_t len = 0;
+                if (lane < nm) M.seg(c0 + lane, beg, len);
+                const long long packed = (long long)len | (len > 0 ? (1ll << 40) : 0ll);
+                long long inc = packed;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const long long y = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += y;
+                }
+                const long long ex2 = inc - packed;
+                if (len > 0) {
+                    const int32_t slot = (int32_t)(ex2 >> 40);
+                    ch.beg[slot] = beg;
+                    ch.pre[slot] = (int32_t)(ex2 & ((1ll << 40) - 1));
+                    ch.len[slot] = lane;
+                }
+                if (lane == 31) {
+                    s_scan[32] = inc;
+                    ch.pre[inc >> 40] = (int32_t)(inc & ((1ll << 40) - 1));
+                }
+            }
+            __syncthreads();
+            tot2 = s_scan[32];
+        } else {
+            int64_t beg = 0;
+            int32_t len = 0;
+            if ((int)threadIdx.x < nm) M.seg(c0 + threadIdx.x, beg, len);
+            const long long packed = (long long)len | (len > 0 ? (1ll << 40) : 0ll);
+            const long long ex2 = block_exclusive_scan<long long, false>(packed, s_scan, &tot2);
+            const int32_t ex = (int32_t)(ex2 & ((1ll << 40) - 1));
+            const int32_t slot = (int32_t)(ex2 >> 40);
+            if (len > 0) {
+                ch.beg[slot] = beg;
+                ch.pre[slot] = ex;
+                ch.len[slot] = threadIdx.x;
+            }
+            if (threadIdx.x == 0) ch.pre[tot2 >> 40] = (int32_t)(tot2 & ((1ll << 40) - 1));
+            __syncthreads();
+        }
         const int32_t total = (int32_t)(tot2 & ((1ll << 40) - 1));
         const int32_t nnz = (int32_t)(tot2 >> 40);
-        if (len > 0) {
-            ch.beg[slot] = beg;
-            ch.pre[slot] = ex;
-            ch.len[slot] = threadIdx.x;
-        }
-        if (threadIdx.x == 0) ch.pre[nnz] = total;
-        __syncthreads();
         const int32_t groups = (total + 31) >> 5;
         const int32_t g_lo = BALANCED ? (int32_t)(((int64_t)groups * warp) / nwarps) : warp * WALK_UNROLL;
         const int32_t g_hi = BALANCED ? (int32_t)(((int64_t)groups * (warp + 1)) / nwarps) : groups;
