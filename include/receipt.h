@@ -104,8 +104,7 @@ typedef struct {
      * are peeled by all CTAs level by level instead of by one CTA of the
      * persistent queue. 0 = automatic (8 times the total weight divided by
      * the smaller of the CTA count and the task count, or by the CTA count
-     * when there are at most half as many tasks as CTAs; at least 2^23; and
-     * every task of at least 2^23 wedges averaging 2^18 or more per member),
+     * when there are at most half as many tasks as CTAs; at least 2^23),
      * -1 = never. Speed only. */
     int64_t fd_heavy_w;
     /* Non-zero: every synchronisation round of Algorithm 3 runs as one

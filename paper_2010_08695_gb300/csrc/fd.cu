@@ -41,7 +41,6 @@ constexpr unsigned long long WIDE_BIT = 1ull << 63;
 // heavy subsets: automatic threshold and levels enqueued per alive check
 constexpr unsigned long long HEAVY_MIN_W = 1ull << 23;
 constexpr unsigned long long HEAVY_SHARE = 8;
-constexpr unsigned long long HEAVY_PER_MEMBER = 1ull << 18;
 constexpr int HEAVY_LEVELS_PER_CHECK = 4;
 // parts of one subset are merged into tasks of at least this many members
 constexpr int32_t TASK_MIN = 8192;
@@ -1206,18 +1205,10 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
             thr = std::max<unsigned long long>(HEAVY_MIN_W,
                                                tot / (unsigned long long)div * HEAVY_SHARE);
         }
-        // also heavy: a task whose walks average HEAVY_PER_MEMBER wedges or
-        // more per member. It has few, long levels (on the 100M-edge graph
-        // two tasks of 134 and 196 members walked 2.4M and 1.0M wedges per
-        // member, 254 and 161 ms on one CTA, while the other tasks walked
-        // 2-8k per member at ~20 us per level); all CTAs take a level's
-        // walks together.
         std::vector<int32_t> front, back;
         for (int k = 0; k < T; k++) {
             const int32_t t = hq[k];
-            const bool long_walks = D.fd_heavy_w == 0 && tw[t] >= HEAVY_MIN_W &&
-                                    tw[t] >= HEAVY_PER_MEMBER * (unsigned long long)tlen[t];
-            ((tw[t] >= thr || long_walks) && tlen[t] > 0 ? front : back).push_back(t);
+            (tw[t] >= thr && tlen[t] > 0 ? front : back).push_back(t);
         }
         nheavy = (int)front.size();
         int pos = 0;
