@@ -471,6 +471,16 @@ def batch_leg(R, args):
         outs = R.receipt_decompose_batch(built, sides, outs=outs, round_graphs=args.round_graphs)
         torch.cuda.synchronize()
         tb.append(time.perf_counter() - t0)
+    # the same with every coarse-grained round as one CUDA graph launch
+    tg = []
+    outs_g = R.receipt_decompose_batch(built, sides, round_graphs=True)
+    torch.cuda.synchronize()
+    for _ in range(3):
+        t0 = time.perf_counter()
+        outs_g = R.receipt_decompose_batch(built, sides, outs=outs_g, round_graphs=True)
+        torch.cuda.synchronize()
+        tg.append(time.perf_counter() - t0)
+    same_g = all(torch.equal(a, b) for a, b in zip(outs, outs_g))
     R.receipt_decompose_batch(built, sides, outs=outs, timing=True, round_graphs=args.round_graphs)
     bs = built[0].stats()
     alone = [torch.empty_like(o) for o in outs]
@@ -489,7 +499,9 @@ def batch_leg(R, args):
             "seconds_one_graph_per_launch": t_plain,
             "graphs_per_s_one_graph_per_launch": len(built) / t_plain,
             "speedup_vs_one_graph_per_launch": t_plain / tbm,
-            "wedges_per_s_batched": wedges / tbm, "rounds_cd": bs["rounds_cd"],
+            "wedges_per_s_batched": wedges / tbm,
+            "graphs_per_s_rounds_as_cuda_graphs": len(built) / statistics.median(tg),
+            "rounds_as_cuda_graphs_equal": same_g, "rounds_cd": bs["rounds_cd"],
             "subsets": bs["p_eff"], "fd_tasks": bs["fd_tasks"],
             "phase_ms": {"count": bs["ms_count"], "cd": bs["ms_cd"], "fd": bs["ms_fd"],
                          "peel_tiers": bs["ms_peel"]},

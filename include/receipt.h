@@ -127,9 +127,9 @@ typedef struct {
     int32_t huc_factor_1024;
     /* Shape of the key-sliced tier of the peel update (anchors with many
      * wedges, aggregated one key slice at a time): 1 = one 1,024-thread CTA
-     * per SM over 102,400-key slices, 2 = two 512-thread CTAs per SM over
-     * 51,200-key slices, 4 (or 0) = four 256-thread CTAs per SM over
-     * 25,344-key slices. Speed only. */
+     * per SM over 98,304-key slices, 2 = two 512-thread CTAs per SM over
+     * 49,152-key slices, 4 (or 0) = four 256-thread CTAs per SM over
+     * 22,016-key slices. Speed only. */
     int32_t slice_ctas;
     /* How the activeSet of a range's later rounds is found: >= 0 (default)
      * by a scan of the remaining vertices after each round (support <

@@ -255,8 +255,7 @@ __global__ void k_cd_prepare(const int32_t *__restrict__ F, CdDev *st,
 // hybrid; otherwise -> key slices that meet the window.
 __global__ void k_cd_route(CdDev *st, const int32_t *__restrict__ Lb,
                            const int64_t *__restrict__ off_s, const int32_t *__restrict__ adj_s,
-                           const int64_t *__restrict__ off_o, const int32_t *__restrict__ len_o,
-                           const int32_t *__restrict__ adj_o,
+                           const int2 *__restrict__ kwin,
                            const unsigned long long *__restrict__ wfull, int64_t cta_keys,
                            int32_t slice_min_w, int32_t SW, int32_t *__restrict__ Lc,
                            int32_t *__restrict__ Lc_k, int32_t *__restrict__ Lc_w,
@@ -273,7 +272,8 @@ __global__ void k_cd_route(CdDev *st, const int32_t *__restrict__ Lb,
         const int32_t x = Lb[i];
         const int64_t q0 = off_s[x], q1 = off_s[x + 1];
         int32_t kmin = INT32_MAX, kmax = -1;
-        // four middle vertices per lane and step, loads independent
+        // four middle vertices per lane and step, loads independent; the
+        // first and last key of every list are kept in kwin
         for (int64_t qb = q0; qb < q1; qb += 128) {
             int32_t y[4];
 #pragma unroll
@@ -281,18 +281,12 @@ __global__ void k_cd_route(CdDev *st, const int32_t *__restrict__ Lb,
                 const int64_t q = qb + 32 * u + lane;
                 y[u] = q < q1 ? adj_s[q] : -1;
             }
-            int64_t b[4];
-            int32_t l[4];
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                b[u] = y[u] >= 0 ? off_o[y[u]] : 0;
-                l[u] = y[u] >= 0 ? len_o[y[u]] : 0;
-            }
 #pragma unroll
             for (int u = 0; u < 4; u++)
-                if (l[u] > 0) {
-                    kmin = min(kmin, adj_o[b[u]]);
-                    kmax = max(kmax, adj_o[b[u] + l[u] - 1]);
+                if (y[u] >= 0) {
+                    const int2 w = kwin[y[u]];
+                    kmin = min(kmin, w.x);
+                    kmax = max(kmax, w.y);
                 }
         }
 #pragma unroll
@@ -647,21 +641,23 @@ __global__ void __maxnreg__(64) k_cd_update_global(PeelArgs a, uint32_t *gcnt,
 // Anchors with many wedges: the key space is cut into C slices of SW keys and
 // every (anchor, slice) pair is one work item, so the slices of a heavy
 // anchor run on different CTAs. Each item aggregates its slice with dense
-// 16-bit counters in shared memory. Three shapes: one 1,024-thread CTA per
-// SM with 102,400-key slices, or two 512-thread (51,200 keys) or four
-// 256-thread (25,344 keys) CTAs per SM, whose items' barrier-separated
-// phases (staging, walk, sweep) overlap on the SM. Each shape's counters,
-// touched-word bitmap and staging fill the SM's shared memory.
+// 16-bit counters in shared memory, listing the keys whose count reaches 2
+// (most keys of a wide slice are touched once and emit nothing). Three
+// shapes: one 1,024-thread CTA per SM with 98,304-key slices, or two
+// 512-thread (49,152 keys) or four 256-thread (22,016 keys) CTAs per SM,
+// whose items' barrier-separated phases (staging, walk, sweep) overlap on the
+// SM. Each shape's counters, key list and staging fill the SM's shared
+// memory.
 template <int THREADS, int WORDS>
 struct SliceShape {
     static constexpr int threads = THREADS;
     static constexpr int keys = 2 * WORDS;
-    using Engine = DenseSliceT<WORDS, TOUCH_BITMAP>;
+    using Engine = DenseSliceT<WORDS, TOUCH_PAIRS>;
     static constexpr size_t smem() { return Engine::bytes() + chunk_bytes(THREADS); }
 };
-using Slice1 = SliceShape<SLICE_THREADS, 51200>;
-using Slice2 = SliceShape<512, 25600>;
-using Slice4 = SliceShape<256, 12672>;
+using Slice1 = SliceShape<SLICE_THREADS, 49152>;
+using Slice2 = SliceShape<512, 24576>;
+using Slice4 = SliceShape<256, 11008>;
 
 constexpr int SLICE_FETCH_MAX = 32;  // candidate items per work-counter atomic, at most
 
@@ -671,10 +667,10 @@ __global__ void __launch_bounds__(Shape::threads, 1024 / Shape::threads)
     using Engine = typename Shape::Engine;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_items[SLICE_FETCH_MAX];
-    __shared__ int s_nitems, s_pos;
+    __shared__ int s_nitems, s_pos, s_nt;
     if (a.st->nLs == 0) return;
     Engine H;
-    unsigned char *p = H.bind(smem);
+    unsigned char *p = H.bind(smem, &s_nt);
     Chunk ch;
     ch.beg = (int64_t *)p;
     ch.pre = (int32_t *)(ch.beg + Shape::threads);
@@ -951,6 +947,16 @@ __global__ void k_list_lengths(const int64_t *__restrict__ off, int32_t n, int32
     if (y < n) len[y] = (int32_t)(off[y + 1] - off[y]);
 }
 
+// kwin[y] = (first, last) key of the working list y ((INT32_MAX, -1) when
+// empty): the window the route of an anchor takes over its middle vertices.
+__global__ void k_list_window(const int64_t *__restrict__ off, const int32_t *__restrict__ len,
+                              const int32_t *__restrict__ adj, int32_t n, int2 *__restrict__ kwin) {
+    int32_t y = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y >= n) return;
+    const int32_t l = len[y];
+    kwin[y] = l > 0 ? make_int2(adj[off[y]], adj[off[y] + l - 1]) : make_int2(INT32_MAX, -1);
+}
+
 // soff[y * (C + 1) + j] = number of entries of N_y below j * SW (j = 0..C).
 __global__ void k_slice_table(const int64_t *__restrict__ off_o, const int32_t *__restrict__ len_o,
                               const int32_t *__restrict__ adj_o, int32_t n_o, int32_t C, int32_t SW,
@@ -1059,6 +1065,7 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
     DevBuf<int32_t> soff(table ? (size_t)O.n * (C + 1) : 1, s);
     // working copy of the other side's lists, compacted between ranges
     DevBuf<int32_t> adj_w(D.m, s), len_w(O.n, s);
+    DevBuf<int2> kwin(O.n, s);
     if (D.m > 0)
         RC_CUDA(cudaMemcpyAsync(adj_w.get(), O.adj, sizeof(int32_t) * D.m, cudaMemcpyDeviceToDevice, s));
     const bool dgm = !opt.no_dgm;
@@ -1074,6 +1081,9 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
         rcost.zero();
     if (O.n > 0) {
         k_list_lengths<<<ceil_div(O.n, 256), 256, 0, s>>>(O.off, O.n, len_w.get());
+        RC_LAUNCH();
+        k_list_window<<<ceil_div(O.n, 256), 256, 0, s>>>(O.off, len_w.get(), adj_w.get(), O.n,
+                                                        kwin.get());
         RC_LAUNCH();
         if (table) {
             k_slice_table<<<ceil_div((int64_t)O.n * (C + 1), 256), 256, 0, s>>>(
@@ -1170,8 +1180,8 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
         k_cd_prepare<<<nb, 512, 0, q>>>(cur, st.get(), D.sub, D.sup, D.wfull, S.off, Lw.get(),
                                         Lb.get(), warp_max_w);
         RC_LAUNCH();
-        k_cd_route<<<sms * 8, 256, 0, q>>>(st.get(), Lb.get(), S.off, S.adj, O.off, len_w.get(),
-                                           adj_w.get(), D.wfull, cta_ok ? cta_keys : 0, slice_min_w,
+        k_cd_route<<<sms * 8, 256, 0, q>>>(st.get(), Lb.get(), S.off, S.adj, kwin.get(),
+                                           D.wfull, cta_ok ? cta_keys : 0, slice_min_w,
                                            SW, Lc.get(), Lc_k.get(), Lc_w.get(), Ld.get(),
                                            Ld_k.get(), Ld_w.get(), Lg.get(), Ls.get(), Ls_lo.get(),
                                            Ls_hi.get());
@@ -1262,6 +1272,11 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
             k_dgm_compact<<<std::min(ceil_div((int64_t)O.n * 32, 256), sms * 32), 256, 0, s>>>(
                 O.off, ll, la, O.n, D.sub);
             RC_LAUNCH();
+            if (dgm) {
+                k_list_window<<<ceil_div(O.n, 256), 256, 0, s>>>(O.off, len_w.get(), adj_w.get(),
+                                                                O.n, kwin.get());
+                RC_LAUNCH();
+            }
             if (dgm && table) {
                 k_slice_table<<<ceil_div((int64_t)O.n * (C + 1), 256), 256, 0, s>>>(
                     O.off, len_w.get(), adj_w.get(), O.n, C, SW, soff.get());
@@ -1390,6 +1405,9 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
             (double)(peeled_now - peeled_at_dgm) >= dgm_frac * (double)(D.m - peeled_at_dgm)) {
             k_dgm_compact<<<std::min(ceil_div((int64_t)O.n * 32, 256), sms * 32), 256, 0, s>>>(
                 O.off, len_w.get(), adj_w.get(), O.n, D.sub);
+            RC_LAUNCH();
+            k_list_window<<<ceil_div(O.n, 256), 256, 0, s>>>(O.off, len_w.get(), adj_w.get(), O.n,
+                                                            kwin.get());
             RC_LAUNCH();
             if (table) {
                 k_slice_table<<<ceil_div((int64_t)O.n * (C + 1), 256), 256, 0, s>>>(

@@ -524,25 +524,35 @@ inline size_t hybrid_bytes(int64_t keyspace, int32_t *head_cap_out = nullptr,
 //  * TOUCH_BITMAP -- the first increment of a word sets its bit in a bitmap
 //    (one bit per counter word, no capacity). Suits wide slices where a
 //    warp's keys are far apart (its bitmap words differ).
+//  * TOUCH_PAIRS -- only a key whose count goes from 1 to 2 is listed (the
+//    keys that will emit); the sweep visits the list and the slice is
+//    cleared whole with 16-byte stores; past the list's capacity (PCAP) the
+//    sweep scans the slice. Suits wide slices where most keys are touched
+//    once (no emit): the sweep costs the emitting keys, not the touched ones.
 // Counts must stay below 2^16 (the caller routes anchors of degree >= 65535
 // elsewhere) unless the slice is set up with 32-bit counters. SCRATCH extra
 // bytes after the tracking structure are free for the caller between passes.
 constexpr int DENSE_KEYS = 36864;               // keys per dense slice
 constexpr int DENSE_WORDS = DENSE_KEYS / 2;     // 18432 words (72 KB)
 constexpr int TOUCH_CAP = 8192;                 // touched-word list capacity
-enum { TOUCH_LIST = 0, TOUCH_BITMAP = 1 };
+enum { TOUCH_LIST = 0, TOUCH_BITMAP = 1, TOUCH_PAIRS = 2 };
 
-template <int WORDS, int TRACK = TOUCH_LIST, int SCRATCH = 0>
+template <int WORDS, int TRACK = TOUCH_LIST, int SCRATCH = 0, int PAIRS_CAP = 4096>
 struct DenseSliceT {
     static_assert(WORDS % 128 == 0 && WORDS <= 65536, "counter words");
     static constexpr int BM_WORDS = WORDS / 32;
     static constexpr int TCAP = TOUCH_CAP;
+    // listed keys fit 16 bits while a slice has at most 65,536 keys
+    static constexpr bool P16 = 2 * WORDS <= 65536;
     static constexpr size_t track_bytes() {
-        return TRACK == TOUCH_BITMAP ? (size_t)BM_WORDS * 4 : (size_t)TCAP * 2;
+        return TRACK == TOUCH_BITMAP  ? (size_t)BM_WORDS * 4
+               : TRACK == TOUCH_PAIRS ? (size_t)PAIRS_CAP * (P16 ? 2 : 4)
+                                      : (size_t)TCAP * 2;
     }
     uint32_t *cnt;     // WORDS
     uint32_t *tbm;     // BM_WORDS: touched counter words (bitmap tracking)
     uint16_t *tl;      // TCAP: touched counter words (list tracking)
+    uint32_t *pl;      // PAIRS_CAP: keys that reached count 2 (pairs tracking)
     int *s_nt;         // shared scalar: list entries (list tracking)
     int32_t hw;        // half of the current slice width (<= WORDS)
     bool wide;         // 32-bit counters, one key per word (slices of WORDS keys)
@@ -554,6 +564,7 @@ struct DenseSliceT {
         cnt = (uint32_t *)base;
         tbm = cnt + WORDS;
         tl = (uint16_t *)(cnt + WORDS);
+        pl = cnt + WORDS;
         s_nt = nt;
         hw = WORDS;
         wide = false;
@@ -563,7 +574,7 @@ struct DenseSliceT {
     __device__ void clear_all() {
         const int n4 = TRACK == TOUCH_BITMAP ? (WORDS + BM_WORDS) / 4 : WORDS / 4;
         for (int i = threadIdx.x; i < n4; i += blockDim.x) ((uint4 *)cnt)[i] = make_uint4(0, 0, 0, 0);
-        if (TRACK == TOUCH_LIST && threadIdx.x == 0) *s_nt = 0;
+        if (TRACK != TOUCH_BITMAP && threadIdx.x == 0) *s_nt = 0;
     }
     // Slice of w keys: 16-bit counters (w <= 2 * WORDS), or 32-bit counters
     // when counts may reach 2^16 (w <= WORDS).
@@ -577,6 +588,26 @@ struct DenseSliceT {
         const uint32_t old = atomicAdd(&cnt[w], hi ? 0x10000u : 1u);
         if (TRACK == TOUCH_BITMAP) {
             if (old == 0) atomicOr(&tbm[w >> 5], 1u << (w & 31));
+        } else if (TRACK == TOUCH_PAIRS) {
+            const uint32_t prev = wide ? old : (hi ? old >> 16 : old & 0xffffu);
+            const unsigned m = __activemask();
+            const unsigned b = __ballot_sync(m, prev == 1);
+            if (b) {
+                const int lane = threadIdx.x & 31;
+                const int leader = __ffs(b) - 1;
+                int base = 0;
+                if (lane == leader) base = atomicAdd(s_nt, __popc(b));
+                base = __shfl_sync(m, base, leader);
+                if (prev == 1) {
+                    const int pos = base + __popc(b & lanemask_lt());
+                    if (pos < PAIRS_CAP) {
+                        if (P16)
+                            tl[pos] = (uint16_t)k;
+                        else
+                            pl[pos] = (uint32_t)k;
+                    }
+                }
+            }
         } else {
             const unsigned m = __activemask();
             const unsigned b = __ballot_sync(m, old == 0);
@@ -650,6 +681,40 @@ struct DenseSliceT {
             }
             return;
         }
+        if (TRACK == TOUCH_PAIRS) {
+            const int np = *(volatile int *)s_nt;
+            if (np <= PAIRS_CAP) {
+                // the listed keys, 8 per thread at a time
+                for (int i0 = threadIdx.x; i0 < np; i0 += 8 * blockDim.x) {
+#pragma unroll
+                    for (int u = 0; u < 8; u++) {
+                        const int i = i0 + u * blockDim.x;
+                        kk[u] = i < np ? (int32_t)(P16 ? (uint32_t)tl[i] : pl[i]) : -1;
+                        cc[u] = kk[u] >= 0 ? count(kk[u]) : 0u;
+                    }
+                    if (EMIT) emit_many<8>(emit, kk, cc);
+                }
+            } else {
+                // too many to list: every word of the slice
+                for (int i0 = threadIdx.x; i0 < hw; i0 += 4 * blockDim.x) {
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        const int i = i0 + u * blockDim.x;
+                        w[u] = i < hw ? i : -1;
+                        v[u] = w[u] >= 0 ? cnt[w[u]] : 0u;
+                        if (v[u] == 0) w[u] = -1;
+                    }
+                    pairs4(w, v, kk, cc);
+                    if (EMIT) emit_many<8>(emit, kk, cc);
+                }
+            }
+            if (CLEAR) {
+                __syncthreads();  // every count read before the slice is cleared
+                for (int i = threadIdx.x; i < (hw + 3) / 4; i += blockDim.x)
+                    ((uint4 *)cnt)[i] = make_uint4(0, 0, 0, 0);
+            }
+            return;
+        }
         const int nt = *(volatile int *)s_nt;
         const bool listed = nt <= TCAP;
         const int n = listed ? nt : hw;  // list entries, or every word of the slice
@@ -667,7 +732,7 @@ struct DenseSliceT {
         }
     }
     __device__ void reset_scalars() {
-        if (TRACK == TOUCH_LIST && threadIdx.x == 0) *s_nt = 0;
+        if (TRACK != TOUCH_BITMAP && threadIdx.x == 0) *s_nt = 0;
     }
 };
 

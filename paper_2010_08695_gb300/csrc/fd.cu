@@ -493,8 +493,12 @@ __device__ __forceinline__ unsigned char *fd_bind_smem(unsigned char *smem, int 
 
 __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_t, s_dn, s_np, s_nk, s_nbig, s_nwide, s_nf, s_pick, s_peel;
-    __shared__ unsigned long long s_mn;  // minimum support of the window's members
+    __shared__ int s_t, s_dn, s_np, s_nbig, s_nwide, s_nf, s_pick, s_peel, s_rk;
+    // window list count and next level's minimum, by level parity: level L
+    // fills set L & 1 while stragglers of level L - 1 may still read the other
+    __shared__ int s_nk[2];
+    __shared__ unsigned long long s_mn[2];
+    __shared__ unsigned long long s_rmn;  // minimum of a refilled window
     __shared__ unsigned long long s_T;   // window bound
     __shared__ int32_t s_scan[33];
     __shared__ int64_t s_bq0[FD_BATCH];
@@ -544,7 +548,8 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
             flist[r] = r;
         }
         int32_t nalive = ni, nfar = ni, ncand = 0;
-        unsigned long long level = 0;
+        unsigned long long level = 0, mn = ~0ull;
+        int par = 0;
         // anchors aggregated per pass of the batched update
         const int32_t bk = ni <= FD_KEYS / 2 ? min(FD_BATCH, FD_KEYS / ni) : 1;
         __syncthreads();
@@ -559,8 +564,8 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
                 if (threadIdx.x == 0) {
                     s_pick = LOG_BUCKETS - 1;
                     s_nf = 0;
-                    s_nk = 0;
-                    s_mn = ~0ull;
+                    s_rk = 0;
+                    s_rmn = ~0ull;
                 }
                 __syncthreads();
                 for (int j = threadIdx.x; j < nfar; j += blockDim.x) {
@@ -604,14 +609,15 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
                             r = -1;
                     }
                     const bool in = r >= 0 && v < T;
-                    warp_append(in, r, &s_nk, clist);
+                    warp_append(in, r, &s_rk, clist);
                     warp_append(r >= 0 && !in, r, &s_nf, flist_next);
                     const unsigned long long kv = warp_min(in ? v : ~0ull);
-                    if (lane == 0 && kv != ~0ull) atomicMin(&s_mn, kv);
+                    if (lane == 0 && kv != ~0ull) atomicMin(&s_rmn, kv);
                 }
                 __syncthreads();
-                ncand = s_nk;
+                ncand = s_rk;
                 nfar = s_nf;
+                mn = s_rmn;
                 {
                     int32_t *tmp = flist;
                     flist = flist_next;
@@ -619,19 +625,19 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
                 }
                 if (ncand == 0) break;  // cannot happen while members are alive
             }
-            // mu from the minimum left by the previous level (or the refill)
-            const unsigned long long mu = s_mn > level ? s_mn : level;
+            // mu from the minimum left by the previous level (or the refill);
+            // this level's counters: the per-level ones and set `par`
+            const unsigned long long mu = mn > level ? mn : level;
             const unsigned long long T = s_T;
             level = mu;
             levels++;
-            __syncthreads();
             if (threadIdx.x == 0) {
                 s_np = 0;
-                s_nk = 0;
+                s_nk[par] = 0;
                 s_nbig = 0;
                 s_nwide = 0;
                 s_peel = 0;
-                s_mn = ~0ull;
+                s_mn[par] = ~0ull;
             }
             __syncthreads();
             // peel every window member with support <= mu; the rest go to
@@ -667,13 +673,13 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
                     const bool upd = peel && v > 0;
                     const bool small = upd && w <= (unsigned long long)WARP_MAX_W;
                     const bool single = upd && !small && ((w & WIDE_BIT) || bk == 1);
-                    warp_append(keep, r, &s_nk, clist_next);
+                    warp_append(keep, r, &s_nk[par], clist_next);
                     warp_append(small, r, &s_np, plist);
                     warp_append(upd && !small && !single, r, &s_nbig, blist);
                     if (single) blist[ni - 1 - atomicAdd(&s_nwide, 1)] = r;
                     // minimum of the survivors before this level's updates
                     const unsigned long long kv = warp_min(keep ? v : ~0ull);
-                    if (lane == 0 && kv != ~0ull) atomicMin(&s_mn, kv);
+                    if (lane == 0 && kv != ~0ull) atomicMin(&s_mn[par], kv);
                 }
             }
             peeled = warp_sum(peeled);
@@ -687,25 +693,25 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
             }
             int np = s_np;
             // a level with few updates makes them all in one batched pass
-            // (one pass costs less than a warp phase followed by a pass)
-            if (bk > 1 && np > 0 && np + s_nbig <= bk) {
-                const int nb0 = s_nbig;
-                for (int pi = threadIdx.x; pi < np; pi += blockDim.x) blist[nb0 + pi] = plist[pi];
-                __syncthreads();
-                if (threadIdx.x == 0) s_nbig = nb0 + np;
+            // (one pass costs less than a warp phase followed by a pass): the
+            // pass takes blist's nbig0 anchors, then plist's np
+            const int nbig0 = s_nbig;
+            int nmerged = 0;
+            if (bk > 1 && np > 0 && np + nbig0 <= bk) {
+                nmerged = np;
                 np = 0;
             }
             // updates of the peeled vertices inside G_i. Phase A: one warp per
             // peeled vertex whose update walks at most WARP_MAX_W wedges.
-            FdEmit emit{fsup, alive, &s_mn, T, clist, &s_nk};
+            FdEmit emit{fsup, alive, &s_mn[par], T, clist, &s_nk[par]};
             for (int pi = warp; pi < np; pi += nwarps) {
                 const int32_t r = plist[pi];
                 const int32_t x = mem[r];
                 fd_update_warp(WH, M, a.fd_adj, a.off_s[x], a.off_s[x + 1], r, kb, lane, emit);
                 if (lane == 0) wedges += wr[r];
             }
-            __syncthreads();
-            const int nbig = s_nbig, nwide = s_nwide;
+            if (np > 0) __syncthreads();
+            const int nbig = nbig0 + nmerged, nwide = s_nwide;
             // Phase B: bk anchors per pass of the whole CTA over one dense key
             // space of bk * ni keys
             for (int p0 = 0; p0 < nbig; p0 += bk) {
@@ -713,7 +719,8 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
                 if (warp == 0) {
                     int32_t deg = 0;
                     if (lane < nb) {
-                        const int32_t r = blist[p0 + lane];
+                        const int i = p0 + lane;
+                        const int32_t r = i < nbig0 ? blist[i] : plist[i - nbig0];
                         const int32_t x = mem[r];
                         const int64_t q0 = a.off_s[x];
                         deg = (int32_t)(a.off_s[x + 1] - q0);
@@ -739,9 +746,10 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
                     FdBatchEmit em{&emit, ni};
                     H.sweep<true, true>(em);
                     __syncthreads();
+                    // the next use of the touched-word count is after the next
+                    // pass's set-up barrier (or the level's last barrier)
                     H.reset_scalars();
                 }
-                __syncthreads();
             }
             // one anchor at a time: degree >= 65535, or a subset too large
             // to batch (rank slices)
@@ -754,7 +762,9 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fd_peel(FdArgs a) {
             }
             __syncthreads();
             // window survivors plus the members that fell below T
-            ncand = s_nk;
+            ncand = s_nk[par];
+            mn = s_mn[par];
+            par ^= 1;
         }
         __syncthreads();
         if (threadIdx.x == 0) {

@@ -104,7 +104,7 @@ def test_sliced_tier_over_several_key_slices(R):
         assert np.array_equal(t, want), f"slice_min_w={smw}"
         st = g.stats()
         assert st["peel_anchors"][3] > 0
-    # the tier's three shapes (1, 2 and 4 CTAs per SM over 2, 3 and 6 key
+    # the tier's three shapes (1, 2 and 4 CTAs per SM over 2, 4 and 7 key
     # slices here), with the next activeSet from crossings or from scans
     for ctas in (1, 2, 4):
         for scan in (-1, 1):
