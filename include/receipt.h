@@ -102,15 +102,26 @@ typedef struct {
     /* Fine-grained step (Algorithm 4): subsets whose wedge count (the LPT key
      * of Sec. 3.2.1, sum of L(L-1) over the runs L of G_i) is at least this
      * are peeled by all CTAs level by level instead of by one CTA of the
-     * persistent queue. 0 = automatic (8 times the total weight divided by
+     * persistent queue. 0 = automatic: 8 times the total weight divided by
      * the smaller of the CTA count and the task count, or by the CTA count
-     * when there are at most half as many tasks as CTAs; at least 2^23),
-     * -1 = never. Speed only. */
+     * when there are at most half as many tasks as CTAs; at least 2^23; and
+     * also every task whose weight plus 2^15 per member exceeds the CTA
+     * count's share of the total of those sums while its wedges are at
+     * least 4 x 2^15 per member (walk-bound). A level of such a task with at
+     * most 8 members with big walks spreads each one's middle vertices over
+     * the CTAs. -1 = never. Speed only. */
     int64_t fd_heavy_w;
-    /* Non-zero: every synchronisation round of Algorithm 3 runs as one
-     * launch of a CUDA graph captured once per call (the round's kernels,
-     * the copy of its counters to the host and the advance to the next
-     * activeSet) instead of separate launches. Speed only. */
+    /* How the synchronisation rounds of Algorithm 3 are launched.
+     * 0 (default): device-driven; the rounds of a range run inside one
+     * launch of a CUDA graph whose while-node repeats the round body until
+     * a round leaves no next activeSet (at most 64 rounds a launch), each
+     * round's counters going to a device record that the host reads after
+     * the launch; with timing on or the activeSet found by crossings the
+     * rounds run as with -1. 1: every round is one launch of a CUDA graph
+     * captured once per call (the round's kernels, the copy of its counters
+     * to the host and the advance), with a host round trip per round.
+     * -1: every round's kernels are launched separately, with a host round
+     * trip per round. Speed only. */
     int32_t round_graphs;
     /* Hybrid update computation (Sec. 4.1). When the first activeSet of a
      * range of Algorithm 3 carries C_peel wedges (sum over its vertices x
@@ -172,7 +183,9 @@ typedef struct {
     int64_t levels_fd;       /* peeling levels summed over all subsets       */
     int32_t p_eff;           /* subsets actually created                     */
     int32_t reserved;
-    float ms_csr, ms_count, ms_cd, ms_fd, ms_total; /* only if timing != 0   */
+    /* Phase device times (CUDA events around each phase, recorded on every
+     * call; ms_csr is not measured here and stays 0). */
+    float ms_csr, ms_count, ms_cd, ms_fd, ms_total;
     /* Batched peel update of the coarse-grained step, per aggregation tier
      * (0 = warp table, 1 = shared-memory hybrid over the anchor's key window,
      * 2 = global dense counters for hubs, 3 = dense counters over key slices,
@@ -205,7 +218,9 @@ typedef struct {
     uint64_t wedges_recount;
     uint64_t cost_recount;
     float ms_recount;
-    int32_t reserved3;
+    /* Levels of heavy tasks whose big-walk members were each spread over
+     * the CTAs (see fd_heavy_w). */
+    int32_t fd_split_levels;
     /* Support atomics of the coarse-grained peel update per tier (the same
      * tiers as peel_wedges): one per pair (x, x') of a peeled vertex x and a
      * remaining vertex x' that share at least two neighbours (the pairs whose

@@ -69,7 +69,7 @@ class Stats(ctypes.Structure):
                 ("levels_fd_heavy", ctypes.c_int64), ("fd_tasks", ctypes.c_int32),
                 ("huc_recounts", ctypes.c_int32), ("wedges_recount", ctypes.c_uint64),
                 ("cost_recount", ctypes.c_uint64), ("ms_recount", ctypes.c_float),
-                ("reserved3", ctypes.c_int32), ("peel_pairs", ctypes.c_uint64 * 5),
+                ("fd_split_levels", ctypes.c_int32), ("peel_pairs", ctypes.c_uint64 * 5),
                 ("count_points", ctypes.c_int64 * 5), ("fd_recounts", ctypes.c_int64),
                 ("wedges_fd_recount", ctypes.c_uint64)]
 
@@ -198,7 +198,9 @@ def _options(P=150, bounds=None, subset=None, bounds_out=None, p_eff=None, timin
     o.huc = int(huc)
     o.huc_factor_1024 = int(huc_factor_1024)
     o.fd_heavy_w = int(fd_heavy_w)
-    o.round_graphs = 1 if round_graphs else 0
+    # True: one graph launch per round; False: device-driven rounds; -1:
+    # separate launches per round
+    o.round_graphs = -1 if round_graphs == -1 else (1 if round_graphs else 0)
     o.dgm_frac_1024 = int(dgm_frac_1024)
     o.no_dgm = 0 if dgm else 1
     o.warp_max_w = int(warp_max_w)
@@ -373,7 +375,7 @@ class Graph:
             if scan_frontier is None:
                 scan_frontier = tuned.get("scan_frontier", 0)
             if range_max_n is None:
-                range_max_n = tuned.get("range_max_n", 0)
+                range_max_n = _tuned_cap(tuned, P)
             slice_fetch = slice_fetch or tuned.get("slice_fetch", 0)
         P = P or 150
         tip = out if out is not None else torch.empty(n, dtype=torch.int64, device=self.device)
@@ -400,6 +402,18 @@ class Graph:
         return receipt_get_subsets(self._h)
 
 
+def _tuned_cap(rec, P):
+    """The tuned vertex cap of a range for a run with P ranges: the table's
+    cap was tuned with its own P, so the cap keeps cap * P (the vertices the
+    capped ranges can hold together) when P differs; -1 (no cap) and 0
+    (2 n / P) stay."""
+    cap = int(rec.get("range_max_n", 0))
+    tp = int(rec.get("P", 0))
+    if cap > 0 and tp > 0 and P > 0 and P != tp:
+        return max(1, (cap * tp + P // 2) // P)
+    return cap
+
+
 def receipt_decompose_batch(graphs, sides, outs=None, P: int = 0, stream=None, timing=False,
                             round_graphs=False, huc=0, huc_factor_1024=0, tuned=True, **options):
     """Tip numbers of many graphs in one pass (disjoint-union packing). With
@@ -410,11 +424,12 @@ def receipt_decompose_batch(graphs, sides, outs=None, P: int = 0, stream=None, t
     if tuned and n > 0:
         from . import autotune
         rec = autotune.lookup(autotune.batch_shape_class(graphs, sides)) or {}
-        for k in ("warp_max_w", "slice_min_w", "dgm_frac_1024", "slice_ctas", "range_max_n",
-                  "slice_fetch"):
+        for k in ("warp_max_w", "slice_min_w", "dgm_frac_1024", "slice_ctas", "slice_fetch"):
             if k in rec and not options.get(k):
                 options[k] = rec[k]
         P = P or rec.get("P", 0)
+        if rec and not options.get("range_max_n"):
+            options["range_max_n"] = _tuned_cap(rec, P or 150)
     P = P or 150
     hs = (ctypes.c_void_p * n)(*[g.handle for g in graphs])
     ss = (ctypes.c_int * n)(*[int(s) for s in sides])

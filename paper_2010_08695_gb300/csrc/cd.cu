@@ -42,7 +42,10 @@ __device__ __forceinline__ unsigned long long bucket_top(int b) { return log_buc
 
 struct CdDev {
     unsigned long long hi;
-    int32_t nF, nNext, nLw, nLc, nLg, nLo, nLs, nLb, nLd, pad2;
+    int32_t nF, nNext, nLw, nLc, nLg, nLo, nLs, nLb, nLd;
+    int32_t par;      // device-driven rounds: which of two buffers holds the activeSet
+    int32_t burst_k;  // device-driven rounds: rounds run by the current graph launch
+    int32_t pad2;
     int32_t work[6];
     unsigned long long work64;  // item counter of the sliced tier
     unsigned long long peeled_edges;  // adjacency entries of assigned vertices (for DGM)
@@ -188,10 +191,18 @@ __global__ void k_set_hi(CdDev *st, unsigned long long hi) {
 // recount): remaining vertices with sup < hi, compacted with a warp ballot
 // and one atomic per warp on *count; their wedge total (the C_peel of
 // Sec. 4.1) is added to st->front_w.
+// With F1 != nullptr (device-driven rounds) the round's activeSet is in
+// {F, F1}[st->par], the next one goes to the other buffer, and a round with
+// an empty activeSet changed nothing, so its scan is skipped.
 __global__ void k_cd_frontier(int32_t n, const int32_t *__restrict__ sub,
                               const unsigned long long *__restrict__ sup,
                               const unsigned long long *__restrict__ wfull, CdDev *st,
-                              int32_t *count, int32_t *__restrict__ F) {
+                              int32_t *count, int32_t *__restrict__ F,
+                              int32_t *__restrict__ F1 = nullptr) {
+    if (F1 != nullptr) {
+        if (st->nF == 0) return;
+        if (st->par == 0) F = F1;
+    }
     const unsigned long long hi = st->hi;
     const int lane = threadIdx.x & 31;
     unsigned long long wsum = 0;
@@ -213,11 +224,14 @@ __global__ void k_cd_frontier(int32_t n, const int32_t *__restrict__ sub,
 
 // Assigns the activeSet to subset `range` and splits the vertices that have
 // updates to make into the three engine tiers.
+// With F1 != nullptr (device-driven rounds) the activeSet is {F, F1}[st->par].
 __global__ void k_cd_prepare(const int32_t *__restrict__ F, CdDev *st,
                              int32_t *__restrict__ sub, const unsigned long long *__restrict__ sup,
                              const unsigned long long *__restrict__ wfull,
                              const int64_t *__restrict__ off_s, int32_t *__restrict__ Lw,
-                             int32_t *__restrict__ Lb, int32_t warp_max_w) {
+                             int32_t *__restrict__ Lb, int32_t warp_max_w,
+                             const int32_t *__restrict__ F1 = nullptr) {
+    if (F1 != nullptr && st->par != 0) F = F1;
     const int32_t nF = st->nF;
     const int32_t range = st->range;
     unsigned long long wsum = 0, esum = 0;
@@ -978,6 +992,35 @@ __global__ void k_cd_advance(CdDev *st) {
     st->work64 = 0;
 }
 
+// Device-driven rounds: the end of a round. The round's header (everything
+// before the histogram, as the host loop copies it) goes to record
+// st->burst_k, the activeSet advances (the next one is in the other buffer),
+// and the graph's while-condition stays set while there is a next activeSet
+// and fewer than `burst` rounds ran in this launch.
+__global__ void k_cd_round_end(CdDev *st, unsigned long long *__restrict__ rec, int32_t words,
+                               int32_t burst, cudaGraphConditionalHandle cond) {
+    const int32_t k = st->burst_k;
+    const unsigned long long *src = reinterpret_cast<const unsigned long long *>(st);
+    for (int i = threadIdx.x; i < words; i += blockDim.x) rec[(size_t)k * words + i] = src[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int32_t nn = st->nNext;
+        if (nn > 0) st->par ^= 1;
+        st->nF = nn;
+        st->nNext = 0;
+        st->nLw = st->nLc = st->nLg = st->nLo = st->nLs = st->nLb = st->nLd = 0;
+        for (int i = 0; i < 6; i++) st->work[i] = 0;
+        st->work64 = 0;
+        st->burst_k = k + 1;
+        cudaGraphSetConditional(cond, (nn > 0 && k + 1 < burst) ? 1u : 0u);
+    }
+}
+
+__global__ void k_cd_burst_begin(CdDev *st, int32_t par) {
+    st->par = par;
+    st->burst_k = 0;
+}
+
 __global__ void k_cd_new_range(CdDev *st, int32_t range) {
     if (threadIdx.x == 0) {
         st->range = range;
@@ -1118,9 +1161,13 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
     gcnt.zero();
     const size_t smem_glob = chunk_extra;
     allow_max_smem((const void *)k_cd_update_global);
-    unsigned long long *hpin = (unsigned long long *)pinned_scratch(64 + sizeof(CdDev));
-    CdDev *hst = reinterpret_cast<CdDev *>(hpin + 8);
     const size_t hdr = offsetof(CdDev, hist_w);
+    // pinned: C_rcnt, the state's header, the device-driven rounds' records
+    constexpr int ROUND_BURST = 64;
+    unsigned long long *hpin =
+        (unsigned long long *)pinned_scratch(64 + sizeof(CdDev) + ROUND_BURST * hdr);
+    CdDev *hst = reinterpret_cast<CdDev *>(hpin + 8);
+    unsigned long long *hrec = hpin + 8 + (sizeof(CdDev) + 7) / 8;
     unsigned long long prev_w[NTIER] = {}, prev_a[NTIER] = {};
 
     // fork/join of the tier streams (no timing)
@@ -1166,10 +1213,21 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
         }
     } gg{round_graph, round_exec};
     uint64_t round_kernels = 0;
+    // Device-driven rounds: one graph whose while-node repeats the round
+    // body until a round leaves no next activeSet or ROUND_BURST rounds ran;
+    // the rounds' headers go to device records that the host reads after the
+    // launch, so a range's rounds need no host round trip between them.
+    const bool dloop = opt.round_graphs == 0 && scan_next && !D.timing;
+    const int32_t hdr_words = (int32_t)(offsetof(CdDev, hist_w) / 8);
+    DevBuf<unsigned long long> rec(dloop ? (size_t)ROUND_BURST * hdr_words : 1, s);
+    cudaGraphConditionalHandle loop_cond = 0;
     // The round body on stream `q`: split the activeSet `cur` into tiers,
     // route, apply the updates of every tier (their crossings form the next
     // activeSet in `nxt`), copy the round's header to the host, advance.
-    auto round_body = [&](cudaStream_t q, int32_t *cur, int32_t *nxt, bool external_events) {
+    // With `loop` the activeSet buffer is chosen on the device ({cur,
+    // nxt}[st->par]) and the header goes to the device records instead.
+    auto round_body = [&](cudaStream_t q, int32_t *cur, int32_t *nxt, bool external_events,
+                          bool loop) {
         auto mark = [&](int i) {
             if (!D.timing) return;
             if (external_events)
@@ -1178,7 +1236,7 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
                 RC_CUDA(cudaEventRecord(ev[i], q));
         };
         k_cd_prepare<<<nb, 512, 0, q>>>(cur, st.get(), D.sub, D.sup, D.wfull, S.off, Lw.get(),
-                                        Lb.get(), warp_max_w);
+                                        Lb.get(), warp_max_w, loop ? nxt : nullptr);
         RC_LAUNCH();
         k_cd_route<<<sms * 8, 256, 0, q>>>(st.get(), Lb.get(), S.off, S.adj, kwin.get(),
                                            D.wfull, cta_ok ? cta_keys : 0, slice_min_w,
@@ -1237,9 +1295,19 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
             }
         if (scan_next) {
             // next activeSet: remaining vertices whose support is now below hi
-            k_cd_frontier<<<nb, 512, 0, q>>>(n, D.sub, D.sup, D.wfull, st.get(), &st.get()->nNext,
-                                             nxt);
+            if (loop)
+                k_cd_frontier<<<nb, 512, 0, q>>>(n, D.sub, D.sup, D.wfull, st.get(),
+                                                 &st.get()->nNext, cur, nxt);
+            else
+                k_cd_frontier<<<nb, 512, 0, q>>>(n, D.sub, D.sup, D.wfull, st.get(),
+                                                 &st.get()->nNext, nxt);
             RC_LAUNCH();
+        }
+        if (loop) {
+            k_cd_round_end<<<1, 64, 0, q>>>(st.get(), rec.get(), hdr_words, ROUND_BURST,
+                                            loop_cond);
+            RC_LAUNCH();
+            return;
         }
         RC_CUDA(cudaMemcpyAsync(hst, st.get(), hdr, cudaMemcpyDeviceToHost, q));
         k_cd_advance<<<1, 1, 0, q>>>(st.get());
@@ -1298,12 +1366,54 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
     // With round_graphs the body is captured once per activeSet parity (on a
     // private stream: the caller's may be the legacy default stream, which
     // cannot capture) and each round is one graph launch.
-    const bool graphs = opt.round_graphs != 0;
+    const bool graphs = opt.round_graphs > 0;
+    cudaGraph_t loop_graph = nullptr;
+    cudaGraphExec_t loop_exec = nullptr;
+    struct LoopGuard {
+        cudaGraph_t *g;
+        cudaGraphExec_t *e;
+        ~LoopGuard() {
+            if (*e) cudaGraphExecDestroy(*e);
+            if (*g) cudaGraphDestroy(*g);
+        }
+    } lg{&loop_graph, &loop_exec};
+    if (dloop) {
+        // while-node (condition 1 at launch) around the round body, captured
+        // into the node's body graph on a private stream
+        RC_CUDA(cudaGraphCreate(&loop_graph, 0));
+        RC_CUDA(cudaGraphConditionalHandleCreate(&loop_cond, loop_graph, 1,
+                                                 cudaGraphCondAssignDefault));
+        cudaGraphNodeParams np{};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = loop_cond;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t wnode;
+        RC_CUDA(cudaGraphAddNode(&wnode, loop_graph, nullptr, nullptr, 0, &np));
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        cudaStream_t cs = aux_stream();
+        RC_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal));
+        round_body(cs, abuf[0], abuf[1], false, true);
+        RC_CUDA(cudaStreamEndCapture(cs, &body));
+        RC_CUDA(cudaGraphInstantiate(&loop_exec, loop_graph, 0));
+        size_t nn = 0;
+        RC_CUDA(cudaGraphGetNodes(body, nullptr, &nn));
+        std::vector<cudaGraphNode_t> nodes(nn);
+        RC_CUDA(cudaGraphGetNodes(body, nodes.data(), &nn));
+        round_kernels = 0;
+        for (size_t k = 0; k < nn; k++) {
+            cudaGraphNodeType t;
+            RC_CUDA(cudaGraphNodeGetType(nodes[k], &t));
+            if (t == cudaGraphNodeTypeKernel) round_kernels++;
+        }
+        uncount_launches(round_kernels);
+    }
     if (graphs) {
         cudaStream_t cs = aux_stream();
         for (int par = 0; par < 2; par++) {
             RC_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-            round_body(cs, abuf[par], abuf[par ^ 1], true);
+            round_body(cs, abuf[par], abuf[par ^ 1], true, false);
             RC_CUDA(cudaStreamEndCapture(cs, &round_graph[par]));
             RC_CUDA(cudaGraphInstantiate(&round_exec[par], round_graph[par], 0));
             // the captured launches are counted per graph launch instead
@@ -1350,32 +1460,24 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
         bool recount = huc == 1 || (huc == 0 && crcnt > 0 &&
                                     (double)hst->front_w > huc_factor * (double)crcnt &&
                                     recount_fits(D));
-        for (;;) {
-            if (recount) {
-                huc_round(abuf[parity], abuf[parity ^ 1]);
-            } else if (graphs) {
-                RC_CUDA(cudaGraphLaunch(round_exec[parity], s));
-                count_launches(round_kernels);
-            } else {
-                round_body(s, abuf[parity], abuf[parity ^ 1], false);
-            }
-            RC_CUDA(cudaStreamSynchronize(s));
-            if (!recount)
+        // one trace record per round from a copy of the state's header
+        auto record_round = [&](const CdDev *h, bool rc) {
+            if (!rc)
                 for (int t = 0; t < NTIER; t++) D.tier_launches[t]++;
             D.rounds++;
             receipt_round rr{};
             rr.range = range;
-            rr.frontier = hst->nF;
+            rr.frontier = h->nF;
             rr.hi = hi;
-            rr.recount = recount ? 1 : 0;
+            rr.recount = rc ? 1 : 0;
             for (int t = 0; t < NTIER; t++) {
-                rr.anchors[t] = hst->tier_a[t] - prev_a[t];
-                rr.wedges[t] = hst->tier_w[t] - prev_w[t];
-                prev_a[t] = hst->tier_a[t];
-                prev_w[t] = hst->tier_w[t];
+                rr.anchors[t] = h->tier_a[t] - prev_a[t];
+                rr.wedges[t] = h->tier_w[t] - prev_w[t];
+                prev_a[t] = h->tier_a[t];
+                prev_w[t] = h->tier_w[t];
             }
-            if (recount) {
-                if (dgm) peeled_at_dgm = hst->peeled_edges;  // the lists were just compacted
+            if (rc) {
+                if (dgm) peeled_at_dgm = h->peeled_edges;  // the lists were just compacted
                 if (D.timing) {
                     float ms = 0;
                     RC_CUDA(cudaEventElapsedTime(&ms, ev[NTIER + 1], ev[NTIER + 2]));
@@ -1392,6 +1494,38 @@ void cd_run(Decomp &D, const receipt_options &opt, cudaStream_t s) {
                 }
             }
             D.trace.push_back(rr);
+        };
+        for (;;) {
+            if (!recount && dloop) {
+                // a burst of up to ROUND_BURST rounds in one graph launch
+                k_cd_burst_begin<<<1, 1, 0, s>>>(st.get(), parity);
+                RC_LAUNCH();
+                RC_CUDA(cudaGraphLaunch(loop_exec, s));
+                RC_CUDA(cudaMemcpyAsync(hrec, rec.get(), (size_t)ROUND_BURST * hdr,
+                                        cudaMemcpyDeviceToHost, s));
+                RC_CUDA(cudaMemcpyAsync(hst, st.get(), hdr, cudaMemcpyDeviceToHost, s));
+                RC_CUDA(cudaStreamSynchronize(s));
+                const int32_t kk = hst->burst_k;
+                if (kk < 1 || kk > ROUND_BURST)
+                    fail(RECEIPT_ERR_INTERNAL, "device-driven rounds: bad round count");
+                count_launches((uint64_t)kk * round_kernels);
+                for (int32_t r = 0; r < kk; r++)
+                    record_round(reinterpret_cast<const CdDev *>(hrec + (size_t)r * hdr_words),
+                                 false);
+                parity = hst->par;
+                if (hst->nF == 0) break;  // the last round left no next activeSet
+                continue;
+            }
+            if (recount) {
+                huc_round(abuf[parity], abuf[parity ^ 1]);
+            } else if (graphs) {
+                RC_CUDA(cudaGraphLaunch(round_exec[parity], s));
+                count_launches(round_kernels);
+            } else {
+                round_body(s, abuf[parity], abuf[parity ^ 1], false, false);
+            }
+            RC_CUDA(cudaStreamSynchronize(s));
+            record_round(hst, recount);
             if (hst->nNext == 0) break;
             parity ^= 1;  // the next round reads the activeSet this one wrote
             recount = false;

@@ -212,6 +212,45 @@ def test_any_P_and_injected_ranges_give_same_tips(R):
         assert np.array_equal(R.as_u64(t), want), f"bounds {b}"
 
 
+def _round_records(tr):
+    return [(r["range"], r["frontier"], r["hi"], r["recount"], tuple(r["anchors"]),
+             tuple(r["wedges"])) for r in tr]
+
+
+def test_round_launch_modes_give_same_rounds(R):
+    # device-driven rounds (default: while-node graph launches of up to 64
+    # rounds), one graph launch per round, separate launches per round: same
+    # tip numbers and the same per-round records
+    eu, ev = synth.chung_lu(20000, 4000, 120000, 2.4, 2.2, seed=31)
+    g = R.Graph(eu, ev, 20000, 4000)
+    for side in (0, 1):
+        want, _ = oracle.bup(eu, ev, 20000, 4000, side)
+        for P, huc in ((1, 0), (7, 0), (150, 0), (40, 1)):
+            recs = []
+            for mode in (0, True, -1):
+                t = R.as_u64(g.tip_decompose(side, P=P, huc=huc, round_graphs=mode))
+                assert np.array_equal(t, want), f"side {side} P={P} huc={huc} mode {mode}"
+                recs.append(_round_records(g.trace()))
+                assert g.stats()["rounds_cd"] == len(recs[-1])
+            assert recs[0] == recs[1] == recs[2], f"side {side} P={P} huc={huc}"
+    # a ladder: u_i shares one butterfly with u_{i-1} and one with u_{i+1},
+    # so below the bound 2 the peel cascades in from both ends, two vertices
+    # a round: one range of ~k/2 rounds, several launches of the while-node
+    k = 400
+    i = np.arange(k, dtype=np.int32)
+    eu = np.repeat(i, 4)
+    ev = np.stack([i, i + 1, k + 1 + i, k + 2 + i], axis=1).reshape(-1).astype(np.int32)
+    g = R.Graph(eu, ev, k, 2 * (k + 1))
+    want, _ = oracle.bup(eu, ev, k, 2 * (k + 1), 0)
+    recs = []
+    for mode in (0, True, -1):
+        t = R.as_u64(g.tip_decompose(0, P=1, bounds=np.array([2], np.uint64), round_graphs=mode))
+        assert np.array_equal(t, want), f"ladder mode {mode}"
+        recs.append(_round_records(g.trace()))
+    assert recs[0] == recs[1] == recs[2]
+    assert len(recs[0]) >= 3 * 64
+
+
 def test_heavy_subset_path_gives_same_tips(R):
     """Subsets peeled by all CTAs level by level (forced for every subset,
     or never) give the one-CTA result; the per-subset records add up."""
@@ -229,6 +268,10 @@ def test_heavy_subset_path_gives_same_tips(R):
             assert len(heavy) == st["fd_heavy_subsets"]
             if hw == 1:
                 assert len(heavy) == sum(1 for s in subs if s["n"] > 0 and s["wedges_est"] >= 1)
+                if P == 1:  # levels with few big walks spread them over the CTAs
+                    assert 0 < st["fd_split_levels"] <= st["levels_fd_heavy"]
+            if hw == -1:
+                assert st["fd_split_levels"] == 0
             if hw == -1:
                 assert not heavy
             assert sum(s["levels"] for s in subs) == st["levels_fd"]
