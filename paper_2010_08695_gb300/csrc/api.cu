@@ -235,7 +235,7 @@ void tip_decompose_impl(receipt_graph *g, int side, uint64_t *d_tip, const recei
     const int32_t n = S.n;
     if (n > 0 && !d_tip) fail(RECEIPT_ERR_INVALID, "null d_tip");
     check_count_bound(g);
-    Timer T(opt.timing != 0, s);
+    Timer T(true, s);  // phase times on every call (four events)
     T.mark();
     Decomp D;
     D.s = side;
@@ -298,6 +298,7 @@ void tip_decompose_impl(receipt_graph *g, int side, uint64_t *d_tip, const recei
     st.fd_heavy_subsets = D.fd_heavy;
     st.ms_fd_heavy = D.fd_heavy_ms;
     st.levels_fd_heavy = D.fd_heavy_levels;
+    st.fd_split_levels = (int32_t)std::min<int64_t>(D.fd_split_levels, INT32_MAX);
     st.fd_tasks = D.fd_tasks;
     st.huc_recounts = D.huc_recounts;
     st.fd_recounts = D.fd_recounts;
@@ -314,12 +315,10 @@ void tip_decompose_impl(receipt_graph *g, int side, uint64_t *d_tip, const recei
         st.peel_launches[t] = D.tier_launches[t];
         st.ms_peel[t] = D.tier_ms[t];
     }
-    if (opt.timing) {
-        st.ms_count = T.ms(0, 1);
-        st.ms_cd = T.ms(1, 2);
-        st.ms_fd = T.ms(2, 3);
-        st.ms_total = T.ms(0, 3);
-    }
+    st.ms_count = T.ms(0, 1);
+    st.ms_cd = T.ms(1, 2);
+    st.ms_fd = T.ms(2, 3);
+    st.ms_total = T.ms(0, 3);
 }
 
 // ---------------------------------------------------------------------

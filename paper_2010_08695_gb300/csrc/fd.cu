@@ -42,6 +42,13 @@ constexpr unsigned long long WIDE_BIT = 1ull << 63;
 constexpr unsigned long long HEAVY_MIN_W = 1ull << 23;
 constexpr unsigned long long HEAVY_SHARE = 8;
 constexpr int HEAVY_LEVELS_PER_CHECK = 4;
+// a level of a heavy task with at most this many members with big walks
+// splits each one's middle vertices over the CTAs (partial counts summed in
+// global counters) instead of giving each member one CTA
+constexpr int FDH_SPLIT_NB = 8;
+// a task whose walk wedges reach this many times LEVEL_WEDGES per member is
+// walk-bound (see the heavy rule)
+constexpr unsigned long long HEAVY_WALK_LEVELS = 4;
 // parts of one subset are merged into tasks of at least this many members
 constexpr int32_t TASK_MIN = 8192;
 // LPT weight of one member of a task in wedges: a level of the one-CTA peel
@@ -418,10 +425,50 @@ __device__ __forceinline__ void fd_update_warp(WarpHash &WH, const FdMids &M,
 // slice by slice of the subset's rank space (ni ranks) with dense counters,
 // 32-bit ones when the anchor's degree lets a count reach 2^16. Returns the
 // wedges walked (the same value in every thread). All threads must call it.
+// What a CTA does with one aggregated slice: apply the member's updates
+// (count c of a key -> support decrement C(c, 2)) ...
+struct FdSweepOut {
+    FdEmit *emit;
+    __device__ __forceinline__ void slice(FdEngine &H, int32_t base) {
+        FdSliceEmit em{emit, base};
+        H.sweep<true, true>(em);
+    }
+};
+
+// ... or add its partial counts (the walk of part of the member's middle
+// vertices) to global counters over the task's ranks, listing each key the
+// first time its counter leaves 0; the slice is cleared either way.
+struct FdPartialOut {
+    uint32_t *gcnt;  // ni counters of this member
+    int32_t *gtl;    // keys with a non-zero counter
+    int32_t *gnt;    // their number
+    __device__ __forceinline__ void add(int32_t z, uint32_t c) {
+        if (atomicAdd(&gcnt[z], c) == 0u) gtl[atomicAdd(gnt, 1)] = z;
+    }
+    __device__ __forceinline__ void slice(FdEngine &H, int32_t base) {
+        const int nt = *(volatile int *)H.s_nt;
+        const bool listed = nt <= FdEngine::TCAP;
+        const int n = listed ? nt : H.hw;  // touched words, or every word of the slice
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int w = listed ? (int)H.tl[i] : i;
+            const uint32_t v = H.cnt[w];
+            if (v == 0u) continue;
+            H.cnt[w] = 0u;
+            if (H.wide) {
+                add(base + w, v);
+            } else {
+                if (v & 0xffffu) add(base + w, v & 0xffffu);
+                if (v >> 16) add(base + w + H.hw, v >> 16);
+            }
+        }
+    }
+};
+
+template <class Out>
 __device__ int64_t fd_update_cta(FdEngine &H, Chunk &ch, const int64_t *__restrict__ fd_beg,
                                  const int32_t *__restrict__ fd_len,
                                  const int32_t *__restrict__ fd_adj, int64_t q0, int64_t q1,
-                                 int32_t r, int32_t ni, int32_t kb, FdEmit &emit) {
+                                 int32_t r, int32_t ni, int32_t kb, Out &out) {
     const bool wide = q1 - q0 >= 65535;
     const int32_t SWk = wide ? FD_WORDS : FD_KEYS;
     const int32_t C = (ni + SWk - 1) / SWk;
@@ -473,12 +520,21 @@ __device__ int64_t fd_update_cta(FdEngine &H, Chunk &ch, const int64_t *__restri
         }
         wedges += walked;
         if (walked == 0) continue;
-        FdSliceEmit em{&emit, base};
-        H.sweep<true, true>(em);
+        out.slice(H, base);
         __syncthreads();
         H.reset_scalars();
     }
     return wedges;
+}
+
+__device__ __forceinline__ int64_t fd_update_cta(FdEngine &H, Chunk &ch,
+                                                 const int64_t *__restrict__ fd_beg,
+                                                 const int32_t *__restrict__ fd_len,
+                                                 const int32_t *__restrict__ fd_adj, int64_t q0,
+                                                 int64_t q1, int32_t r, int32_t ni, int32_t kb,
+                                                 FdEmit &emit) {
+    FdSweepOut o{&emit};
+    return fd_update_cta(H, ch, fd_beg, fd_len, fd_adj, q0, q1, r, ni, kb, o);
 }
 
 __device__ __forceinline__ unsigned char *fd_bind_smem(unsigned char *smem, int *s_dn, FdEngine &H,
@@ -797,6 +853,8 @@ struct FdhDev {
     unsigned long long cpeel;    // walk sizes of this level's peeled members with updates
     unsigned long long rcnt;     // C_rcnt of the task's induced subgraph
     int32_t nalive, nkeep, nw, nb;
+    int32_t gnt[FDH_SPLIT_NB];   // split levels: keys listed per member
+    unsigned long long splits;   // split levels so far
 };
 
 struct FdhArgs {
@@ -815,7 +873,15 @@ struct FdhArgs {
     int32_t *Lw, *Lb;          // peeled members with small / big walks
     unsigned long long *tip;   // output, original ids
     FdhDev *st;
+    uint32_t *gcnt;            // split levels: FDH_SPLIT_NB x ni counters, zero between levels
+    int32_t *gtl;              // split levels: FDH_SPLIT_NB x ni listed keys
 };
+
+// A level splits its big-walk members' middle vertices over the CTAs when it
+// has few of them (the same test in the update and the sweep kernel).
+__device__ __forceinline__ bool fdh_split(int32_t nb, int32_t grid) {
+    return nb > 0 && nb <= FDH_SPLIT_NB && grid >= 2 * nb;
+}
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;
@@ -832,6 +898,8 @@ __global__ void k_fdh_reset(FdhDev *st, int32_t ni) {
     st->t1 = 0;
     st->nalive = ni;
     st->nkeep = st->nw = st->nb = 0;
+    for (int i = 0; i < FDH_SPLIT_NB; i++) st->gnt[i] = 0;
+    st->splits = 0;
 }
 
 __global__ void k_fdh_init(FdhArgs a) {
@@ -963,18 +1031,60 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fdh_cta(FdhArgs a) {
     FdEmit emit{a.fsup, a.alive, &a.st->mn_next, ~0ull, nullptr, nullptr};
     const int32_t nb = a.st->nb;
     unsigned long long wedges = 0;
-    for (int32_t i = blockIdx.x; i < nb; i += gridDim.x) {
-        const int32_t r = a.Lb[i];
-        const int32_t x = a.mem[r];
-        wedges += (unsigned long long)fd_update_cta(H, ch, a.fd_beg, a.fd_len, a.fd_adj, a.off_s[x],
-                                                    a.off_s[x + 1], r, a.ni, a.kb, emit);
+    if (fdh_split(nb, gridDim.x)) {
+        // K CTAs per member, each over an equal share of its middle
+        // vertices; k_fdh_sweep applies the summed counts
+        const int32_t K = gridDim.x / nb;
+        for (int32_t it = blockIdx.x; it < nb * K; it += gridDim.x) {
+            const int32_t i = it / K, k = it % K;
+            const int32_t r = a.Lb[i];
+            const int32_t x = a.mem[r];
+            const int64_t q0 = a.off_s[x], nm = a.off_s[x + 1] - q0;
+            const int64_t qa = q0 + nm * k / K, qb = q0 + nm * (k + 1) / K;
+            if (qa == qb) continue;
+            FdPartialOut o{a.gcnt + (size_t)i * a.ni, a.gtl + (size_t)i * a.ni, &a.st->gnt[i]};
+            wedges += (unsigned long long)fd_update_cta(H, ch, a.fd_beg, a.fd_len, a.fd_adj, qa,
+                                                        qb, r, a.ni, a.kb, o);
+        }
+    } else {
+        for (int32_t i = blockIdx.x; i < nb; i += gridDim.x) {
+            const int32_t r = a.Lb[i];
+            const int32_t x = a.mem[r];
+            wedges += (unsigned long long)fd_update_cta(H, ch, a.fd_beg, a.fd_len, a.fd_adj,
+                                                        a.off_s[x], a.off_s[x + 1], r, a.ni, a.kb,
+                                                        emit);
+        }
     }
     if (threadIdx.x == 0 && wedges) atomicAdd(&a.st->wedges, wedges);
+}
+
+// Split levels: the summed count c of every listed key becomes the support
+// decrement C(c, 2) of that member (alive ones only), and the counters return
+// to zero. `grid` is the update kernel's grid.
+__global__ void k_fdh_sweep(FdhArgs a, int32_t grid) {
+    const int32_t nb = a.st->nb;
+    if (!fdh_split(nb, grid)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.st->splits++;
+    FdEmit emit{a.fsup, a.alive, &a.st->mn_next, ~0ull, nullptr, nullptr};
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+    for (int32_t i = 0; i < nb; i++) {
+        uint32_t *gc = a.gcnt + (size_t)i * a.ni;
+        const int32_t *gl = a.gtl + (size_t)i * a.ni;
+        const int32_t n = a.st->gnt[i];
+        for (int64_t t = t0; t < n; t += nt) {
+            const int32_t z = gl[t];
+            const uint32_t c = gc[z];
+            gc[z] = 0u;
+            if (c >= 2u) emit(z, c);
+        }
+    }
 }
 
 // Closes a level. Launched again after the subset is empty, it changes
 // nothing that is read later (the host enqueues levels ahead of its check).
 __global__ void k_fdh_next(FdhDev *st) {
+    for (int i = 0; i < FDH_SPLIT_NB; i++) st->gnt[i] = 0;
     if (st->nalive == 0) return;
     const unsigned long long mu = st->mn > st->level ? st->mn : st->level;
     st->level = mu;
@@ -1042,6 +1152,8 @@ static void fdh_levels_with_recount(Decomp &D, const FdhArgs &ha, FdhDev *dst, F
             k_fdh_warp<<<sms * 8, 256, 0, s>>>(ha);
             RC_LAUNCH();
             k_fdh_cta<<<grid_h, FD_THREADS, smem_h, s>>>(ha);
+            RC_LAUNCH();
+            k_fdh_sweep<<<sms * 4, 256, 0, s>>>(ha, grid_h);
             RC_LAUNCH();
         }
         k_fdh_next<<<1, 1, 0, s>>>(dst);
@@ -1215,10 +1327,22 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
             thr = std::max<unsigned long long>(HEAVY_MIN_W,
                                                tot / (unsigned long long)div * HEAVY_SHARE);
         }
+        // Automatic rule, second part: a task above one CTA's share of the
+        // LPT weight whose walks outweigh its levels several times over (its
+        // one-CTA peel is walk-bound, and split levels spread the walks over
+        // every CTA)
+        unsigned long long share = ~0ull;
+        if (D.fd_heavy_w == 0) {
+            unsigned long long totk = 0;
+            for (int k = 0; k < T; k++) totk += tw[k] + LEVEL_WEDGES * (unsigned long long)tlen[k];
+            share = totk / (unsigned long long)grid_all;
+        }
         std::vector<int32_t> front, back;
         for (int k = 0; k < T; k++) {
             const int32_t t = hq[k];
-            (tw[t] >= thr && tlen[t] > 0 ? front : back).push_back(t);
+            const unsigned long long lw = LEVEL_WEDGES * (unsigned long long)tlen[t];
+            const bool walk_bound = tw[t] + lw >= share && tw[t] >= HEAVY_WALK_LEVELS * lw;
+            ((tw[t] >= thr || walk_bound) && tlen[t] > 0 ? front : back).push_back(t);
         }
         nheavy = (int)front.size();
         int pos = 0;
@@ -1240,6 +1364,7 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
     D.fd_heavy = nheavy;
     D.fd_heavy_ms = 0;
     D.fd_heavy_levels = 0;
+    D.fd_split_levels = 0;
     std::vector<FdhDev> hh(nheavy);
     if (nheavy > 0) {
         DevBuf<FdhDev> hst(1, s);
@@ -1258,6 +1383,12 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
             }
         } eg{evs};
         for (int i = 0; i < 2; i++) RC_CUDA(cudaEventCreateWithFlags(&evs[i], cudaEventDisableTiming));
+        // global counters of split levels, sized for the largest heavy task
+        int32_t ni_max = 1;
+        for (int h = 0; h < nheavy; h++) ni_max = std::max(ni_max, tlen[hq[h]]);
+        DevBuf<uint32_t> gcnt((size_t)FDH_SPLIT_NB * ni_max, s);
+        DevBuf<int32_t> gtl((size_t)FDH_SPLIT_NB * ni_max, s);
+        gcnt.zero();
         for (int h = 0; h < nheavy; h++) {
             const int32_t i = hq[h];
             const int32_t mb = tstart[i], ni = tlen[i];
@@ -1265,7 +1396,7 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
                        fd_beg.get(),       fd_len.get(), fd_adj.get(),   S.new2old,
                        D.init,             fsup.get() + mb, alive.get() + mb, wr.get() + mb,
                        plist.get() + mb,   blist.get() + mb, (unsigned long long *)d_tip,
-                       hst.get()};
+                       hst.get(),          gcnt.get(),   gtl.get()};
             const int gm = std::max(1, std::min(ceil_div(ni, 256), sms * 4));
             const int gi = std::max(1, std::min(ceil_div((int64_t)ni * 32, 256), sms * 16));
             k_fdh_reset<<<1, 1, 0, s>>>(hst.get(), ni);
@@ -1299,6 +1430,8 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
                     RC_LAUNCH();
                     k_fdh_cta<<<grid_h, FD_THREADS, smem_h, s>>>(ha);
                     RC_LAUNCH();
+                    k_fdh_sweep<<<sms * 4, 256, 0, s>>>(ha, grid_h);
+                    RC_LAUNCH();
                     k_fdh_next<<<1, 1, 0, s>>>(hst.get());
                     RC_LAUNCH();
                 }
@@ -1314,6 +1447,7 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
             RC_CUDA(cudaStreamSynchronize(s));
             D.fd_heavy_ms += (float)((hh[h].t1 - hh[h].t0) * 1e-6);
             D.fd_heavy_levels += (int64_t)hh[h].levels;
+            D.fd_split_levels += (int64_t)hh[h].splits;
         }
         RC_CUDA(cudaMemcpyAsync(qhead.get(), &nheavy, 4, cudaMemcpyHostToDevice, s));
     }

@@ -76,6 +76,7 @@ struct Decomp {
     int32_t fd_heavy = 0;        // subsets peeled by all CTAs
     float fd_heavy_ms = 0;
     int64_t fd_heavy_levels = 0;
+    int64_t fd_split_levels = 0; // heavy levels whose big walks were split over the CTAs
     int32_t fd_tasks = 0;        // tasks of the fine-grained step
     // first vertex of every packed graph when the side is a batch's
     // disjoint union (null otherwise)
