@@ -246,7 +246,7 @@ def measure_graph(R, name, args, dist=None, world=1, local=0, clocks=True, e2e=T
         g.tip_decompose(side, P=P, timing=timing, out=tip, stream=stream,
                         round_graphs=args.round_graphs, huc=args.huc,
                         huc_factor_1024=args.huc_factor_1024)
-        st = g.stats() if timing else None
+        st = g.stats()
         if timing and args.trace:
             trace[:] = g.trace()
         g.close()
@@ -255,7 +255,7 @@ def measure_graph(R, name, args, dist=None, world=1, local=0, clocks=True, e2e=T
     for _ in range(max(3, args.warmup)):
         step(False)
     barrier()
-    times = []
+    times, plain = [], []
     launches0 = R.receipt_kernel_launches()
 
     class _Null:
@@ -274,7 +274,7 @@ def measure_graph(R, name, args, dist=None, world=1, local=0, clocks=True, e2e=T
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            step(False)
+            plain.append(step(False))
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
@@ -309,7 +309,12 @@ def measure_graph(R, name, args, dist=None, world=1, local=0, clocks=True, e2e=T
         "walked_wedges_per_step": {"count": last["wedges_count"], "cd": sum(last["peel_wedges"]),
                                    "cd_without_dgm": last["wedges_cd"], "fd": last["wedges_fd"]},
         "phase_ms": {"count": st["ms_count"], "cd": st["ms_cd"], "fd": st["ms_fd"],
-                     "peel_tiers": st["ms_peel"]},
+                     "peel_tiers": st["ms_peel"],
+                     "cd_outside_tiers": st["ms_cd"] - sum(st["ms_peel"])},
+        # the timed (uninstrumented) steps' own phase split: rounds run
+        # device-driven, tiers on forked streams
+        "phase_ms_timed_steps": {k: statistics.mean(p[f"ms_{k}"] for p in plain)
+                                 for k in ("count", "cd", "fd")} if plain else None,
         "phase_wedges_per_s": {
             "count": last["wedges_count"] / (st["ms_count"] / 1e3) if st["ms_count"] else None,
             "cd": sum(last["peel_wedges"]) / (st["ms_cd"] / 1e3) if st["ms_cd"] else None,
@@ -342,7 +347,8 @@ def measure_graph(R, name, args, dist=None, world=1, local=0, clocks=True, e2e=T
         # end to end through the C ABI with host buffers: H2D of the edges,
         # build, decomposition, D2H of the tips, with the step's options
         e2e_opt = {k: tuned.get(k, 0) for k in ("warp_max_w", "slice_min_w", "dgm_frac_1024",
-                                                 "slice_ctas", "range_max_n", "slice_fetch")}
+                                                 "slice_ctas", "slice_fetch")}
+        e2e_opt["range_max_n"] = R._tuned_cap(tuned, P) if tuned else 0
         e2e_opt.update(huc=args.huc, huc_factor_1024=args.huc_factor_1024,
                        round_graphs=args.round_graphs)
         eu_h = torch.from_numpy(eu).pin_memory().numpy()
@@ -606,9 +612,11 @@ def run_experiments(args):
         tip = torch.empty(n_side, dtype=torch.int64, device=dev)
         ref = None
         # few subsets: P = 4 on the 10M-edge graph; on the 100M-edge graph a
-        # subset of P = 4 takes minutes to peel exactly (P = 25 instead)
+        # subset of P = 4 takes minutes to peel exactly (P = 25 instead). The
+        # slow small-P settings run last.
         few = 4 if name == SECONDARY else 25
-        ps = (4, 25, 50, 100, 150, 300, 600) if name == SECONDARY else (25, 50, 100, 150, 300, 600)
+        ps = (50, 100, 150, 300, 600, 25, 4) if name == SECONDARY else \
+            (100, 150, 200, 300, 600, 50, 25)
         settings = [("P", {"P": p}) for p in ps]
         settings += [("receipt", {"P": 150}),
                      ("receipt-paper-huc-factor", {"P": 150, "huc_factor_1024": 1024}),
@@ -648,8 +656,8 @@ def run_experiments(args):
         out[name] = {"workload": DESCR[name], "wedges_bup": wedges, "records": recs,
                      "note": "seconds: one step with per-phase CUDA events, after an "
                              "uninstrumented warm-up step of the same setting"}
-    with open(args.experiments, "w") as f:
-        json.dump(out, f, indent=1)
+        with open(args.experiments, "w") as f:  # after each workload
+            json.dump(out, f, indent=1)
     return 0
 
 

@@ -41,3 +41,16 @@ def test_coordinate_search_picks_the_fastest_setting():
     rec, times = autotune.search(lambda **o: None, 1_000_000, time_fn=cost)
     assert {k: rec[k] for k in best} == best and rec["ms"] == 1.0
     assert len(times) == len(calls)
+
+
+def test_tuned_range_cap_follows_P():
+    # the table's vertex cap was tuned with its own P: another P keeps
+    # cap * P, and the special values stay
+    import paper_2010_08695_gb300 as R
+    rec = {"P": 200, "range_max_n": 6666}
+    assert R._tuned_cap(rec, 200) == 6666
+    assert R._tuned_cap(rec, 25) == 53328
+    assert R._tuned_cap(rec, 400) == 3333
+    assert R._tuned_cap({"P": 200, "range_max_n": -1}, 25) == -1
+    assert R._tuned_cap({"P": 200, "range_max_n": 0}, 25) == 0
+    assert R._tuned_cap({"range_max_n": 500}, 25) == 500
