@@ -108,8 +108,8 @@ typedef struct {
      * also every task whose weight plus 2^15 per member exceeds the CTA
      * count's share of the total of those sums while its wedges are at
      * least 4 x 2^15 per member (walk-bound). A level of such a task with at
-     * most 8 members with big walks spreads each one's middle vertices over
-     * the CTAs. -1 = never. Speed only. */
+     * most 32 members with big walks spreads each one's walk over the CTAs
+     * in equal wedge shares. -1 = never. Speed only. */
     int64_t fd_heavy_w;
     /* How the synchronisation rounds of Algorithm 3 are launched.
      * 0 (default): device-driven; the rounds of a range run inside one

@@ -38,14 +38,14 @@ using FdEngine = DenseSliceT<FD_WORDS, TOUCH_LIST>;
 static_assert(TOUCH_CAP * 2 >= LOG_BUCKETS * 4, "histogram in the touched-word list");
 // walk-size flag: the vertex's degree is >= 65535 (counts may need 32 bits)
 constexpr unsigned long long WIDE_BIT = 1ull << 63;
-// heavy subsets: automatic threshold and levels enqueued per alive check
+// heavy subsets: automatic threshold
 constexpr unsigned long long HEAVY_MIN_W = 1ull << 23;
 constexpr unsigned long long HEAVY_SHARE = 8;
-constexpr int HEAVY_LEVELS_PER_CHECK = 4;
 // a level of a heavy task with at most this many members with big walks
-// splits each one's middle vertices over the CTAs (partial counts summed in
-// global counters) instead of giving each member one CTA
-constexpr int FDH_SPLIT_NB = 8;
+// (and at least two CTAs for each) splits each one's walk over the CTAs
+// (partial counts summed in global counters) instead of giving each member
+// one CTA
+constexpr int FDH_SPLIT_NB = 32;
 // a task whose walk wedges reach this many times LEVEL_WEDGES per member is
 // walk-bound (see the heavy rule)
 constexpr unsigned long long HEAVY_WALK_LEVELS = 4;
@@ -464,11 +464,43 @@ struct FdPartialOut {
     }
 };
 
+// Part of a member's walk: the runs of its edges [q0, q1) with the first run
+// taken from position `skip` on and the last one up to position `keep`
+// (split heavy levels cut a walk into equal wedge shares), optionally only
+// the ranks of one slice [base, end) of each.
+struct FdClipMids {
+    const int64_t *fd_beg;
+    const int32_t *fd_len;
+    const int32_t *fd_adj;
+    int64_t qa, ql;       // first and last edge
+    int32_t skip, keep;
+    int32_t base, end;
+    bool sliced;
+    __device__ __forceinline__ void seg(int64_t q, int64_t &beg, int32_t &len) const {
+        const int64_t b = fd_beg[q];
+        const int32_t s0 = q == qa ? skip : 0;
+        const int32_t e0 = q == ql ? keep : fd_len[q];
+        if (sliced) {
+            const int64_t lo = s0 + lower_bound_i32(fd_adj + b + s0, e0 - s0, base);
+            const int64_t hi = lo + lower_bound_i32(fd_adj + b + lo, e0 - lo, end);
+            beg = b + lo;
+            len = (int32_t)(hi - lo);
+        } else {
+            beg = b + s0;
+            len = e0 - s0;
+        }
+    }
+};
+
+// keep < 0: the last run whole (no cut).
 template <class Out>
 __device__ int64_t fd_update_cta(FdEngine &H, Chunk &ch, const int64_t *__restrict__ fd_beg,
                                  const int32_t *__restrict__ fd_len,
                                  const int32_t *__restrict__ fd_adj, int64_t q0, int64_t q1,
-                                 int32_t r, int32_t ni, int32_t kb, Out &out) {
+                                 int32_t r, int32_t ni, int32_t kb, Out &out, int32_t skip = 0,
+                                 int32_t keep = -1) {
+    const bool clip = skip != 0 || keep >= 0;
+    if (clip && keep < 0) keep = fd_len[q1 - 1];
     const bool wide = q1 - q0 >= 65535;
     const int32_t SWk = wide ? FD_WORDS : FD_KEYS;
     const int32_t C = (ni + SWk - 1) / SWk;
@@ -511,7 +543,11 @@ __device__ int64_t fd_update_cta(FdEngine &H, Chunk &ch, const int64_t *__restri
         H.set_width(w, wide);
         FdSliceVisit v{&H, base + kb, r + kb};
         int64_t walked;
-        if (j0 == j1) {
+        if (clip) {
+            FdClipMids MC{fd_beg, fd_len, fd_adj, q0,       q1 - 1,  skip,
+                          keep,   base + kb, base + kb + w, j0 != j1};
+            walked = cta_walk(MC, q0, q1, fd_adj, ch, v);
+        } else if (j0 == j1) {
             FdMids M{fd_beg, fd_len};
             walked = cta_walk(M, q0, q1, fd_adj, ch, v);
         } else {
@@ -875,6 +911,7 @@ struct FdhArgs {
     FdhDev *st;
     uint32_t *gcnt;            // split levels: FDH_SPLIT_NB x ni counters, zero between levels
     int32_t *gtl;              // split levels: FDH_SPLIT_NB x ni listed keys
+    const int64_t *wpre;       // side-s edges: exclusive prefix of the run lengths
 };
 
 // A level splits its big-walk members' middle vertices over the CTAs when it
@@ -1032,19 +1069,37 @@ __global__ void __launch_bounds__(FD_THREADS, 1) k_fdh_cta(FdhArgs a) {
     const int32_t nb = a.st->nb;
     unsigned long long wedges = 0;
     if (fdh_split(nb, gridDim.x)) {
-        // K CTAs per member, each over an equal share of its middle
-        // vertices; k_fdh_sweep applies the summed counts
+        // K CTAs per member, each over an equal share of its walk's wedges
+        // (runs cut at the share's ends); k_fdh_sweep applies the summed
+        // counts
         const int32_t K = gridDim.x / nb;
         for (int32_t it = blockIdx.x; it < nb * K; it += gridDim.x) {
             const int32_t i = it / K, k = it % K;
             const int32_t r = a.Lb[i];
             const int32_t x = a.mem[r];
-            const int64_t q0 = a.off_s[x], nm = a.off_s[x + 1] - q0;
-            const int64_t qa = q0 + nm * k / K, qb = q0 + nm * (k + 1) / K;
-            if (qa == qb) continue;
+            const int64_t q0 = a.off_s[x], q1 = a.off_s[x + 1];
+            const int64_t w0 = a.wpre[q0], W = a.wpre[q1] - w0;
+            const int64_t lo = w0 + W * k / K, hi = w0 + W * (k + 1) / K;
+            if (lo == hi) continue;
+            // edge whose run holds wedge position p: the last q in [q0, q1)
+            // with wpre[q] <= p (runs of length 0 are passed over)
+            auto run_of = [&](int64_t p) {
+                int64_t l = q0, h = q1 - 1;
+                while (l < h) {
+                    const int64_t md = (l + h + 1) >> 1;
+                    if (a.wpre[md] <= p)
+                        l = md;
+                    else
+                        h = md - 1;
+                }
+                return l;
+            };
+            const int64_t qa = run_of(lo), ql = run_of(hi - 1);
+            const int32_t skip = (int32_t)(lo - a.wpre[qa]);
+            const int32_t keep = (int32_t)(hi - a.wpre[ql]);
             FdPartialOut o{a.gcnt + (size_t)i * a.ni, a.gtl + (size_t)i * a.ni, &a.st->gnt[i]};
             wedges += (unsigned long long)fd_update_cta(H, ch, a.fd_beg, a.fd_len, a.fd_adj, qa,
-                                                        qb, r, a.ni, a.kb, o);
+                                                        ql + 1, r, a.ni, a.kb, o, skip, keep);
         }
     } else {
         for (int32_t i = blockIdx.x; i < nb; i += gridDim.x) {
@@ -1083,7 +1138,7 @@ __global__ void k_fdh_sweep(FdhArgs a, int32_t grid) {
 
 // Closes a level. Launched again after the subset is empty, it changes
 // nothing that is read later (the host enqueues levels ahead of its check).
-__global__ void k_fdh_next(FdhDev *st) {
+__device__ void fdh_close_level(FdhDev *st) {
     for (int i = 0; i < FDH_SPLIT_NB; i++) st->gnt[i] = 0;
     if (st->nalive == 0) return;
     const unsigned long long mu = st->mn > st->level ? st->mn : st->level;
@@ -1097,7 +1152,26 @@ __global__ void k_fdh_next(FdhDev *st) {
     if (st->nalive == 0) st->t1 = globaltimer_ns();
 }
 
+__global__ void k_fdh_next(FdhDev *st) { fdh_close_level(st); }
+
+// The same inside a graph's while-node: the loop goes on while members are
+// alive (at most ni levels: every level peels at least one member).
+__global__ void k_fdh_next_loop(FdhDev *st, int32_t ni, cudaGraphConditionalHandle cond) {
+    fdh_close_level(st);
+    cudaGraphSetConditional(cond, (st->nalive > 0 && st->levels < (unsigned long long)ni) ? 1u : 0u);
+}
+
 }  // namespace
+
+// A graph and its executable, destroyed together.
+struct GraphOwner {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t e = nullptr;
+    ~GraphOwner() {
+        if (e) cudaGraphExecDestroy(e);
+        if (g) cudaGraphDestroy(g);
+    }
+};
 
 // Levels of one heavy task one at a time, each deciding on the host between
 // its updates and a recount of the task's alive members (hybrid update
@@ -1186,7 +1260,7 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
     }
     // induced subgraphs
     DevBuf<int32_t> fd_adj(m, s), fd_len(m, s);
-    DevBuf<int64_t> fd_beg(m, s);
+    DevBuf<int64_t> fd_beg(m, s), wpre;
     DevBuf<unsigned long long> wr(n, s);
     DevBuf<unsigned long long> wsub(P, s);
     wsub.zero();
@@ -1214,13 +1288,15 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
                                                     hpos.get(), run_start.get(), nruns, S.off, S.adj,
                                                     D.sub, fd_beg.get(), fd_len.get(), wsub.get());
         RC_LAUNCH();
-        // walk sizes of all vertices: prefix sums of the run lengths
-        DevBuf<int64_t> l64(m + 1, s), pre(m + 1, s);
+        // walk sizes of all vertices: prefix sums of the run lengths (kept
+        // for the split levels of heavy tasks)
+        DevBuf<int64_t> l64(m + 1, s);
+        wpre.alloc(m + 1, s);
         k_i32_to_i64<<<ceil_div(m, 256), 256, 0, s>>>(fd_len.get(), m, l64.get());
         RC_LAUNCH();
         RC_CUDA(cudaMemsetAsync(l64.get() + m, 0, sizeof(int64_t), s));
-        scan_exclusive<int64_t>(l64.get(), pre.get(), m + 1, s);
-        k_fd_walk_sizes<<<ceil_div(n, 256), 256, 0, s>>>(S.off, n, pre.get(), D.sub, mstart.get(),
+        scan_exclusive<int64_t>(l64.get(), wpre.get(), m + 1, s);
+        k_fd_walk_sizes<<<ceil_div(n, 256), 256, 0, s>>>(S.off, n, wpre.get(), D.sub, mstart.get(),
                                                          rank.get(), wr.get());
         RC_LAUNCH();
     } else {
@@ -1373,16 +1449,6 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
         int occ_h = 0;
         RC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_h, k_fdh_cta, FD_THREADS, smem_h));
         const int grid_h = sms * std::max(occ_h, 1);
-        int32_t *pin = (int32_t *)pinned_scratch(64);
-        cudaEvent_t evs[2] = {};
-        struct EvGuard {
-            cudaEvent_t *e;
-            ~EvGuard() {
-                for (int i = 0; i < 2; i++)
-                    if (e[i]) cudaEventDestroy(e[i]);
-            }
-        } eg{evs};
-        for (int i = 0; i < 2; i++) RC_CUDA(cudaEventCreateWithFlags(&evs[i], cudaEventDisableTiming));
         // global counters of split levels, sized for the largest heavy task
         int32_t ni_max = 1;
         for (int h = 0; h < nheavy; h++) ni_max = std::max(ni_max, tlen[hq[h]]);
@@ -1396,7 +1462,7 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
                        fd_beg.get(),       fd_len.get(), fd_adj.get(),   S.new2old,
                        D.init,             fsup.get() + mb, alive.get() + mb, wr.get() + mb,
                        plist.get() + mb,   blist.get() + mb, (unsigned long long *)d_tip,
-                       hst.get(),          gcnt.get(),   gtl.get()};
+                       hst.get(),          gcnt.get(),   gtl.get(),      wpre.get()};
             const int gm = std::max(1, std::min(ceil_div(ni, 256), sms * 4));
             const int gi = std::max(1, std::min(ceil_div((int64_t)ni * 32, 256), sms * 16));
             k_fdh_reset<<<1, 1, 0, s>>>(hst.get(), ni);
@@ -1416,35 +1482,44 @@ void fd_run(Decomp &D, uint64_t *d_tip, cudaStream_t s) {
                 rcnt = hh[h].rcnt;
                 may_recount = rcnt > 0 && (double)tw[i] > D.huc_factor * (double)rcnt;
             }
-            if (may_recount) {
+            // the levels in one graph launch: a while-node repeats select,
+            // updates, sweep and close while members are alive
+            GraphOwner lg;
+            if (!may_recount) {
+                RC_CUDA(cudaGraphCreate(&lg.g, 0));
+                cudaGraphConditionalHandle cond;
+                RC_CUDA(cudaGraphConditionalHandleCreate(&cond, lg.g, 1, cudaGraphCondAssignDefault));
+                cudaGraphNodeParams np{};
+                np.type = cudaGraphNodeTypeConditional;
+                np.conditional.handle = cond;
+                np.conditional.type = cudaGraphCondTypeWhile;
+                np.conditional.size = 1;
+                cudaGraphNode_t wnode;
+                RC_CUDA(cudaGraphAddNode(&wnode, lg.g, nullptr, nullptr, 0, &np));
+                cudaGraph_t body = np.conditional.phGraph_out[0];
+                cudaStream_t cs = aux_stream();
+                RC_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                                      cudaStreamCaptureModeThreadLocal));
+                k_fdh_select<<<gm, 256, 0, cs>>>(ha);
+                RC_LAUNCH();
+                k_fdh_warp<<<sms * 8, 256, 0, cs>>>(ha);
+                RC_LAUNCH();
+                k_fdh_cta<<<grid_h, FD_THREADS, smem_h, cs>>>(ha);
+                RC_LAUNCH();
+                k_fdh_sweep<<<sms * 4, 256, 0, cs>>>(ha, grid_h);
+                RC_LAUNCH();
+                k_fdh_next_loop<<<1, 1, 0, cs>>>(hst.get(), ni, cond);
+                RC_LAUNCH();
+                RC_CUDA(cudaStreamEndCapture(cs, &body));
+                uncount_launches(5);  // counted per level below
+                RC_CUDA(cudaGraphInstantiate(&lg.e, lg.g, 0));
+                RC_CUDA(cudaGraphLaunch(lg.e, s));
+            } else {
                 fdh_levels_with_recount(D, ha, hst.get(), &hh[h], rcnt, grid_h, smem_h, gm, s);
-            } else
-            // levels are enqueued in batches; the alive count of batch k is
-            // checked while batch k + 1 runs (levels after the last change
-            // nothing)
-            for (int64_t batch = 0;; batch++) {
-                for (int l = 0; l < HEAVY_LEVELS_PER_CHECK; l++) {
-                    k_fdh_select<<<gm, 256, 0, s>>>(ha);
-                    RC_LAUNCH();
-                    k_fdh_warp<<<sms * 8, 256, 0, s>>>(ha);
-                    RC_LAUNCH();
-                    k_fdh_cta<<<grid_h, FD_THREADS, smem_h, s>>>(ha);
-                    RC_LAUNCH();
-                    k_fdh_sweep<<<sms * 4, 256, 0, s>>>(ha, grid_h);
-                    RC_LAUNCH();
-                    k_fdh_next<<<1, 1, 0, s>>>(hst.get());
-                    RC_LAUNCH();
-                }
-                const int slot = (int)(batch & 1);
-                RC_CUDA(cudaMemcpyAsync(pin + slot, &hst.get()->nalive, 4, cudaMemcpyDeviceToHost, s));
-                RC_CUDA(cudaEventRecord(evs[slot], s));
-                if (batch > 0) {
-                    RC_CUDA(cudaEventSynchronize(evs[slot ^ 1]));
-                    if (pin[slot ^ 1] == 0) break;
-                }
             }
             RC_CUDA(cudaMemcpyAsync(&hh[h], hst.get(), sizeof(FdhDev), cudaMemcpyDeviceToHost, s));
             RC_CUDA(cudaStreamSynchronize(s));
+            if (!may_recount) count_launches(5 * (uint64_t)hh[h].levels);
             D.fd_heavy_ms += (float)((hh[h].t1 - hh[h].t0) * 1e-6);
             D.fd_heavy_levels += (int64_t)hh[h].levels;
             D.fd_split_levels += (int64_t)hh[h].splits;

@@ -45,11 +45,20 @@ struct Request {
 };
 
 // Device bytes a request may hold while it runs (graph, build and
-// decomposition temporaries), an upper estimate.
-size_t estimate_bytes(int64_t m, int32_t nu, int32_t nv, int side) {
+// decomposition temporaries), an upper estimate. It includes what a recount
+// of Sec. 4.1 allocates when the rule picks one (the remaining subgraph's
+// lists, offsets and counts, the counting pass's temporaries and its
+// global-tier counters per CTA, a copy of the other side's lists: the sizes
+// the decomposition itself checks before recounting) and the fine-grained
+// step's global counters of split heavy levels (32 members x the side).
+size_t estimate_bytes(int64_t m, int32_t nu, int32_t nv, int side, int sms) {
     const int64_t ns = side ? nv : nu;
     size_t b = (size_t)160 * (size_t)m + (size_t)400 * (size_t)(nu + nv) + ((size_t)32 << 20);
     if (m >= 65535) b += (size_t)8 * 80 * (size_t)ns;  // hub slots of the global tier
+    const size_t n_max = (size_t)std::max(nu, nv);
+    b += (size_t)40 * (size_t)m + (size_t)48 * (size_t)(nu + nv) + (size_t)8 * (size_t)sms * n_max +
+         ((size_t)64 << 20);
+    b += (size_t)8 * 32 * (size_t)ns;
     return b;
 }
 
@@ -58,6 +67,7 @@ size_t estimate_bytes(int64_t m, int32_t nu, int32_t nv, int side) {
 struct receipt_server {
     receipt_server_config cfg{};
     int device = 0;
+    int sms = 1;  // the device's SM count (per-CTA counters of the estimate)
     size_t budget = 0;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -233,6 +243,12 @@ receipt_status receipt_server_create(const receipt_server_config *cfg, receipt_s
             delete sv;
             throw ReceiptError{RECEIPT_ERR_CUDA, "no CUDA device"};
         }
+        if (cudaDeviceGetAttribute(&sv->sms, cudaDevAttrMultiProcessorCount, sv->device) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            delete sv;
+            throw ReceiptError{RECEIPT_ERR_CUDA, "cudaDeviceGetAttribute failed"};
+        }
         size_t fr = 0, tot = 0;
         if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
             cudaGetLastError();
@@ -271,7 +287,7 @@ receipt_status receipt_server_submit(receipt_server *sv, const int32_t *h_eu, co
     r->nv = nv;
     r->side = (int)side;
     r->h_tip = h_tip;
-    r->est = estimate_bytes(m, nu, nv, (int)side);
+    r->est = estimate_bytes(m, nu, nv, (int)side, sv->sms);
     r->t_submit = now_ms();
     {
         std::lock_guard<std::mutex> lk(sv->mu);
