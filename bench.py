@@ -576,7 +576,7 @@ def run_single(args):
     g = R.Graph(eu, ev, nu, nv)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    tip = g.tip_decompose(side, P=args.P, timing=bool(args.trace))
+    tip = g.tip_decompose(side, P=args.P, timing=bool(args.trace), fd_heavy_w=args.fd_heavy_w)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     st = g.stats()
@@ -746,6 +746,9 @@ def main():
                     help="recount rule (Sec. 4.1): 0 cost rule, -1 never, 1 every range")
     ap.add_argument("--huc-factor-1024", type=int, default=0,
                     help="factor of the recount rule in 1/1024 units (0: 8192)")
+    ap.add_argument("--fd-heavy-w", type=int, default=0,
+                    help="--single: heavy-task threshold of the fine-grained step (0 automatic, "
+                         "-1 never)")
     ap.add_argument("--single", action="store_true",
                     help="one decomposition of the workload and nothing else (profiling runs)")
     ap.add_argument("--experiments", default=None,
