@@ -74,7 +74,12 @@ SERVE_PREFIX = 200
 # algorithmic byte of the captured launch (scaled to the average launch of
 # the step), keyed by kernel name; valid only while the peel kernels'
 # sources (PEEL_SOURCES) hash to the recorded digest.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # rounds 134-138 of the 100M-edge decomposition (the heaviest sliced
+    # round and the next four): 4.032 GB of DRAM traffic for 76.97 GB of
+    # algorithmic bytes
+    "k_cd_update_slice": {"src": "f2b774bbdaf08fc7", "dram_per_alg_byte": 0.05238},
+}
 
 PEEL_TIERS = ["k_cd_update_warp", "k_cd_update_cta", "k_cd_update_global", "k_cd_update_slice",
               "k_cd_update_dense"]
@@ -697,6 +702,7 @@ def run_ours(args):
             "roofline": main["roofline"], "e2e": main["e2e"],
             "gpu_launches": main["gpu_launches"], "clocks": main["clocks"]}
     for k in ("step_ms_all", "instrumented_step_ms", "walked_wedges_per_step", "phase_ms",
+              "phase_ms_timed_steps",
               "phase_wedges_per_s", "rounds_cd", "levels_fd", "subsets", "fd_slowest_task",
               "fd_heavy", "huc", "peel_tier_wedges", "peel_tier_anchors", "peel_tier_pairs",
               "peel_tier_mids"):
