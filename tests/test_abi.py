@@ -57,6 +57,18 @@ def test_options_default_and_last_error_without_gpu(lib):
     assert isinstance(lib.receipt_last_error(), bytes)
 
 
+def test_round_launch_modes_marshal_without_gpu(lib):
+    # Python's round_graphs: False -> 0 (device-driven rounds, the default),
+    # True -> 1 (one graph launch per round), -1 -> -1 (separate launches)
+    import paper_2010_08695_gb300 as R
+    assert R._options(round_graphs=False)[0].round_graphs == 0
+    assert R._options(round_graphs=True)[0].round_graphs == 1
+    assert R._options(round_graphs=-1)[0].round_graphs == -1
+    o = R.Options()
+    lib.receipt_options_default(ctypes.byref(o))
+    assert o.round_graphs == 0
+
+
 def test_null_arguments_are_rejected_without_gpu(lib):
     import paper_2010_08695_gb300 as R
     R.load()
